@@ -1,0 +1,232 @@
+/*
+ * gen.c -- seeded synthetic fingerprint workloads.
+ *
+ * Stands in for the continuous-data fingerprints of the paper's GeoNet and
+ * NCEDC stations (§8 "Dataset"), which are not available here.  A fingerprint
+ * is a binary vector of D bits with exactly K set bits (§5.1, "Binarize";
+ * top-K coefficients), stored as an ascending uint16 index list.
+ *
+ * This module is the ONE input source shared by the CUDA path and the oracle.
+ * It holds none of the search method's arithmetic: it only draws sets.
+ *
+ * Structure of a station's N windows (1 window = 1 s lag, §6.4 "Partition"):
+ *   1. every window starts as a uniform random K-subset of [0, D);
+ *   2. each periodic noise source p (period P_p windows) has a base set and a
+ *      random phase; every window phase + k*P_p becomes a noisy copy of it
+ *      (repeating non-seismic signals, §6.5 "Removing correlated noise");
+ *   3. each template tau (a repeating earthquake source, §1) has a base set and
+ *      U{rep_lo..rep_hi} repeats at uniform random windows, each a noisy copy.
+ *   Later steps overwrite earlier ones at the same window.
+ * A noisy copy with re-draw fraction x removes round(x*K) uniformly chosen set
+ * bits and adds as many uniform bits from D minus the remaining set, so
+ * exactly K bits stay set.
+ *
+ * Randomness is counter based (SplitMix64, Steele, Lea & Flood 2014): every
+ * draw is a pure function of (seed, stream, counter), so rows are generated
+ * independently and in parallel, identically on every machine.
+ */
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <unistd.h>
+
+#define SYN_GAMMA 0x9E3779B97F4A7C15ULL
+
+static uint64_t syn_mix(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* Stream key for (seed, domain, id); draws are syn_mix(key + (n+1)*GAMMA). */
+static uint64_t syn_stream(uint64_t seed, uint64_t domain, uint64_t id)
+{
+    return syn_mix(syn_mix(seed ^ (domain * 0xD1B54A32D192ED03ULL)) + (id + 1) * SYN_GAMMA);
+}
+
+typedef struct {
+    uint64_t key, n;
+} syn_rng;
+
+static uint64_t syn_next(syn_rng *g)
+{
+    g->n++;
+    return syn_mix(g->key + g->n * SYN_GAMMA);
+}
+
+/* Uniform integer in [0, m) by the multiply-high method. */
+static uint64_t syn_below(syn_rng *g, uint64_t m)
+{
+    return (uint64_t)(((unsigned __int128)syn_next(g) * m) >> 64);
+}
+
+enum { DOM_ROW = 1, DOM_PBASE = 2, DOM_PPHASE = 3, DOM_TBASE = 4, DOM_TPLACE = 5, DOM_NOISE = 6,
+       DOM_TOFF = 7 };
+
+#define OWNER_RANDOM 0u
+#define OWNER_PERIODIC (1u << 30)
+#define OWNER_TEMPLATE (2u << 30)
+
+/* Writes the ascending list of the bits set in bitmap `bm` (D bits) to out. */
+static uint32_t syn_emit(const uint64_t *bm, uint32_t D, uint16_t *out)
+{
+    uint32_t n = 0;
+    for (uint32_t w = 0; w < (D + 63) / 64; w++) {
+        uint64_t x = bm[w];
+        while (x) {
+            out[n++] = (uint16_t)(w * 64 + (uint32_t)__builtin_ctzll(x));
+            x &= x - 1;
+        }
+    }
+    return n;
+}
+
+/* Uniform random K-subset of [0, D), ascending. */
+static void syn_subset(syn_rng *g, uint32_t D, uint32_t K, uint64_t *bm, uint16_t *out)
+{
+    memset(bm, 0, sizeof(uint64_t) * ((D + 63) / 64));
+    uint32_t have = 0;
+    while (have < K) {
+        uint32_t x = (uint32_t)syn_below(g, D);
+        if (!(bm[x >> 6] >> (x & 63) & 1)) {
+            bm[x >> 6] |= 1ULL << (x & 63);
+            have++;
+        }
+    }
+    syn_emit(bm, D, out);
+}
+
+/* Noisy copy of the ascending K-set `base`: remove m = round(x*K) uniformly
+ * chosen members, then add m uniform bits of D outside the remaining set. */
+static void syn_copy(syn_rng *g, const uint16_t *base, uint32_t D, uint32_t K, double x,
+                     uint64_t *bm, uint32_t *perm, uint16_t *out)
+{
+    uint32_t m = (uint32_t)(x * K + 0.5);
+    if (m > K) m = K;
+    for (uint32_t k = 0; k < K; k++) perm[k] = k;
+    for (uint32_t k = 0; k < m; k++) { /* partial Fisher-Yates: perm[0..m) removed */
+        uint32_t s = k + (uint32_t)syn_below(g, K - k);
+        uint32_t tmp = perm[k];
+        perm[k] = perm[s];
+        perm[s] = tmp;
+    }
+    memset(bm, 0, sizeof(uint64_t) * ((D + 63) / 64));
+    for (uint32_t k = m; k < K; k++) bm[base[perm[k]] >> 6] |= 1ULL << (base[perm[k]] & 63);
+    /* the removed bits may come back: D minus the *remaining* set is eligible */
+    uint32_t added = 0;
+    while (added < m) {
+        uint32_t y = (uint32_t)syn_below(g, D);
+        if (!(bm[y >> 6] >> (y & 63) & 1)) {
+            bm[y >> 6] |= 1ULL << (y & 63);
+            added++;
+        }
+    }
+    syn_emit(bm, D, out);
+}
+
+typedef struct {
+    uint64_t N, w0, w1, seed;
+    uint32_t D, K, ld;
+    uint16_t *out;
+    const uint32_t *owner;
+    const uint16_t *pbase, *tbase;
+    double per_redraw, tpl_redraw;
+} syn_job;
+
+static void *syn_worker(void *arg)
+{
+    syn_job *j = arg;
+    uint64_t *bm = malloc(sizeof(uint64_t) * ((j->D + 63) / 64));
+    uint32_t *perm = malloc(sizeof(uint32_t) * (j->K ? j->K : 1));
+    for (uint64_t w = j->w0; w < j->w1; w++) {
+        uint16_t *row = j->out + w * (uint64_t)j->ld;
+        uint32_t own = j->owner[w];
+        uint32_t kind = own & (3u << 30), id = own & ((1u << 30) - 1);
+        if (kind == OWNER_RANDOM) {
+            syn_rng g = {syn_stream(j->seed, DOM_ROW, w), 0};
+            syn_subset(&g, j->D, j->K, bm, row);
+        } else {
+            syn_rng g = {syn_stream(j->seed, DOM_NOISE, w), 0};
+            if (kind == OWNER_PERIODIC)
+                syn_copy(&g, j->pbase + (uint64_t)id * j->K, j->D, j->K, j->per_redraw, bm, perm, row);
+            else
+                syn_copy(&g, j->tbase + (uint64_t)id * j->K, j->D, j->K, j->tpl_redraw, bm, perm, row);
+        }
+        for (uint32_t k = j->K; k < j->ld; k++) row[k] = 0xFFFF; /* row padding */
+    }
+    free(bm);
+    free(perm);
+    return NULL;
+}
+
+/*
+ * Fills out[N][ld] (ld >= K) and, when owner_out != NULL, owner_out[N] with
+ * each window's source: 0 random, (1<<30)|p periodic source p,
+ * (2<<30)|tau template tau.
+ *
+ * Templates draw their base sets and repeat counts from `tpl_seed` (shared
+ * by all stations of a network) and their repeat windows uniformly from
+ * [0, place_range); a station adds its own offset U{0..tpl_offset_max} per
+ * template (drawn from `seed`) and keeps the repeats that land inside [0, N).
+ * Periodic sources and everything else draw from `seed`.
+ * Returns the number of threads used, or -1 on bad arguments.
+ */
+int synth_generate(uint64_t N, uint32_t D, uint32_t K, uint16_t *out, uint32_t ld, uint64_t seed,
+                   uint32_t n_periodic, const uint64_t *periods, double per_redraw,
+                   uint32_t n_templates, uint32_t rep_lo, uint32_t rep_hi, double tpl_redraw,
+                   uint64_t tpl_seed, uint64_t place_range, uint32_t tpl_offset_max,
+                   int nthreads, uint32_t *owner_out)
+{
+    if (D == 0 || D > 65536 || K == 0 || K > D || ld < K || rep_hi < rep_lo) return -1;
+    if (place_range == 0) place_range = N;
+    uint32_t *owner = owner_out ? owner_out : malloc(sizeof(uint32_t) * (N ? N : 1));
+    memset(owner, 0, sizeof(uint32_t) * N);
+    uint64_t *bm = malloc(sizeof(uint64_t) * ((D + 63) / 64));
+
+    uint16_t *pbase = malloc(sizeof(uint16_t) * (uint64_t)K * (n_periodic ? n_periodic : 1));
+    for (uint32_t p = 0; p < n_periodic; p++) {
+        syn_rng g = {syn_stream(seed, DOM_PBASE, p), 0};
+        syn_subset(&g, D, K, bm, pbase + (uint64_t)p * K);
+        syn_rng h = {syn_stream(seed, DOM_PPHASE, p), 0};
+        uint64_t P = periods[p] ? periods[p] : 1;
+        for (uint64_t w = syn_below(&h, P); w < N; w += P) owner[w] = OWNER_PERIODIC | p;
+    }
+
+    uint16_t *tbase = malloc(sizeof(uint16_t) * (uint64_t)K * (n_templates ? n_templates : 1));
+    for (uint32_t t = 0; t < n_templates; t++) {
+        syn_rng g = {syn_stream(tpl_seed, DOM_TBASE, t), 0};
+        syn_subset(&g, D, K, bm, tbase + (uint64_t)t * K);
+        syn_rng pl = {syn_stream(tpl_seed, DOM_TPLACE, t), 0};
+        uint32_t reps = rep_lo + (uint32_t)syn_below(&pl, (uint64_t)(rep_hi - rep_lo) + 1);
+        syn_rng off = {syn_stream(seed, DOM_TOFF, t), 0};
+        uint64_t delta = syn_below(&off, (uint64_t)tpl_offset_max + 1);
+        for (uint32_t k = 0; k < reps; k++) {
+            uint64_t w = syn_below(&pl, place_range) + delta;
+            if (w < N) owner[w] = OWNER_TEMPLATE | t;
+        }
+    }
+    free(bm);
+
+    int T = nthreads;
+    if (T <= 0) {
+        long n = sysconf(_SC_NPROCESSORS_ONLN);
+        T = n > 0 ? (int)n : 1;
+    }
+    if ((uint64_t)T > N / 4096 + 1) T = (int)(N / 4096 + 1);
+    pthread_t *th = malloc(sizeof(pthread_t) * T);
+    syn_job *jobs = malloc(sizeof(syn_job) * T);
+    for (int k = 0; k < T; k++) {
+        jobs[k] = (syn_job){N,     N * k / T, N * (k + 1) / T, seed,      D,         K, ld,
+                            out,   owner,     pbase,           tbase,     per_redraw, tpl_redraw};
+        pthread_create(&th[k], NULL, syn_worker, &jobs[k]);
+    }
+    for (int k = 0; k < T; k++) pthread_join(th[k], NULL);
+    free(th);
+    free(jobs);
+    free(pbase);
+    free(tbase);
+    if (!owner_out) free(owner);
+    return T;
+}

@@ -1,0 +1,50 @@
+"""The shared synthetic input generator (CPU only)."""
+import numpy as np
+
+import synth
+
+
+def test_rows_are_sorted_k_subsets_and_reproducible():
+    w = synth.scaled("c1", 20_000)
+    a = synth.generate(w, threads=3)
+    b = synth.generate(w, threads=5)
+    assert np.array_equal(a, b)
+    assert a.shape == (20_000, 400)
+    assert np.all(np.diff(a.astype(np.int32), axis=1) > 0)
+    assert a.max() < w.D
+
+
+def test_padding_and_owner_structure():
+    w = synth.scaled("c1", 30_000)
+    idx, own = synth.generate(w, ld=408, owner=True)
+    assert np.all(idx[:, 400:] == 0xFFFF)
+    per = own[(own >= synth.OWNER_PERIODIC) & (own < synth.OWNER_TEMPLATE)] - synth.OWNER_PERIODIC
+    assert set(np.unique(per).tolist()) == {0, 1, 2}
+    # periodic copies recur every P windows unless a template overwrote them
+    for p, P in enumerate(w.periods):
+        pos = np.nonzero(own == synth.OWNER_PERIODIC + p)[0]
+        assert np.all(np.diff(pos) % P == 0)
+        assert len(pos) >= 0.9 * (w.N // P)
+
+
+def test_noisy_copies_keep_k_and_overlap():
+    w = synth.scaled("c1", 30_000)
+    idx, own = synth.generate(w, owner=True)
+    pos = np.nonzero(own == synth.OWNER_PERIODIC + 1)[0][:20]  # the 300 s source, 5 % re-draw
+    for x in pos[1:]:
+        inter = len(np.intersect1d(idx[pos[0]], idx[x]))
+        assert inter >= 400 - 2 * 20  # each copy re-draws 20 of 400 bits
+
+
+def test_shared_templates_across_stations():
+    a, oa = synth.generate(synth.scaled("c2", 40_000, station=0), owner=True)
+    b, ob = synth.generate(synth.scaled("c2", 40_000, station=3), owner=True)
+    ta = set((oa[oa >= synth.OWNER_TEMPLATE] - synth.OWNER_TEMPLATE).tolist())
+    tb = set((ob[ob >= synth.OWNER_TEMPLATE] - synth.OWNER_TEMPLATE).tolist())
+    assert len(ta & tb) > 0
+
+
+def test_request_schedule():
+    t, st, size = synth.requests(5000, 2000.0)
+    assert np.all(np.diff(t) >= 0) and abs(5000 / t[-1] - 2000) < 200
+    assert size.min() >= 60 and size.max() <= 3600 and st.max() < 12
