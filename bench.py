@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Throughput of the LSH fingerprint search on GB300: fingerprints/s, bit-exact.
+
+One step = the whole hot path on one station's fingerprints resident in HBM:
+Min-Max signatures -> per-table bucket keys -> radix-sorted hash tables ->
+occurrence filter -> pair enumeration + vote counting -> canonical (i, j,
+votes) list (fast_detect).  The workload is the paper-scale single station:
+3 months at 1 s lag (N = 7,776,000 windows), D = 8192, K = 400, Min-Max
+b = 100 x r = 4, v = 4, |i - j| <= 10 excluded, 0.5 % occurrence filter,
+synthetic (seeded) fingerprints with 2,000 repeating templates and three
+periodic noise sources.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank searches its own station
+(an independent problem, no data-path collective): weak scaling; the value is
+the fingerprints of all ranks over the slowest rank's time.
+``--impl reference`` times the CPU oracle (plain C, the definition written
+out) on a bounded sample of the same workload on this machine's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fingerprints/sec searched (bit-exact) + HBM roofline %; stream p50/p99 ms vs plain"
+UNIT = "fingerprints/s"
+
+
+def workload_config(w, n_gpus, extra=None):
+    cfg = {
+        "workload": f"{w.name}: {w.N:,} windows/station (1 s lag), D={w.D}, K={w.K}, "
+                    f"{'Min-Max' if w.kind else 'MinHash'} b={w.b} x r={w.r}, v={w.v}, excl={w.excl}, "
+                    f"occurrence filter {100.0 * w.occ_num / w.occ_den:g}% in > b/2 tables, "
+                    f"{w.n_templates} templates, periodic sources {list(w.periods)} s",
+        "stations": n_gpus,
+        "N_per_station": w.N,
+        "l2": "inputs larger than L2 (idx %.1f GB/station), no flush" % (w.N * w.K * 2 / 1e9),
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------------ clocks
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle leg
+
+def oracle_sample(w, n_sample: int):
+    """The oracle, as it stands, on the first n_sample windows of the workload."""
+    import numpy as np
+
+    import oracle
+    import synth
+    idx = synth.generate(_sample_workload(w, n_sample), ld=w.K)
+    p = w.params()
+    t0 = time.perf_counter()
+    keys, threads = oracle.keys(p, idx, return_threads=True)
+    d = oracle.drop(p, keys)
+    i, _, _ = oracle.search(p, keys, d)
+    dt = time.perf_counter() - t0
+    return dt, threads, len(i)
+
+
+def _sample_workload(w, n):
+    """The first n windows of workload w, exactly: every draw of the generator
+    is keyed by window index, and repeats placed beyond n are dropped."""
+    from dataclasses import replace
+    return replace(w, N=n, place_range=w.place_range or w.N)
+
+
+def reference_arm(args, rank, world):
+    import synth
+    if rank != 0:
+        return 0
+    w = synth.workload(args.workload)
+    n = args.ref_sample
+    sw = _sample_workload(w, n)
+    times, thr, M = [], 0, 0
+    for k in range(args.warmup + args.steps):
+        dt, thr, M = oracle_sample(sw, n)
+        if k >= args.warmup:
+            times.append(dt)
+    ms = 1000 * statistics.mean(times)
+    value = n / (ms / 1000)
+    sample = (f"first {n:,} windows of the {w.name} workload (its own filter threshold), whole path "
+              f"(keys on {thr} threads, filter, search single-threaded); {M:,} detections")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": workload_config(w, 1, {"sample_windows": n}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- GB300 leg
+
+STAGES = ("sig", "sort", "filter", "enum", "dense", "sparse", "output")
+
+
+def stage_bytes(w, N, st):
+    """Algorithmic bytes per stage and launch (measurement)."""
+    b = w.b
+    return {
+        "sig": N * (2 * w.K + 4 * b),            # read the index lists, write b keys
+        "sort": N * b * (4 + 8),                 # read keys, write (key, id)
+        "filter": N * b * 4 + N,                 # read sorted keys, write the drop mask
+        "enum": N * b * 8,                       # read (key, id) of every table
+        "dense": st["n_dense_pairs"] * 0 + 1,    # compare-bound; no HBM traffic to speak of
+        "sparse": st["n_emissions"] * (4 + 9),   # read j, read-modify-write a 9-byte slot
+        "output": st["n_detections"] * 9 * 2,    # write + read (i, j, votes)
+    }
+
+
+def gpu_arm(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1803_09835_gb300 import Searcher
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    w = synth.workload(args.workload, station=rank)
+    if args.n:
+        w = synth.scaled(args.workload, args.n, station=rank)
+    ld = ((w.K + 7) // 8) * 8
+    h_idx = torch.empty((w.N, ld), dtype=torch.uint16, pin_memory=True)
+    synth.generate(w, ld=ld, out=h_idx)
+    d_idx = h_idx.cuda()
+    s = Searcher(w.params())
+
+    def step():
+        r = s.detect(d_idx)
+        m = r.M
+        r.free()
+        return m, s.stats()
+
+    M = 0
+    for _ in range(args.warmup):
+        M, _ = step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    acc = {k: 0.0 for k in STAGES}
+    launches = 0
+    last = None
+    for _ in range(args.steps):
+        M, st = step()
+        for k in STAGES:
+            acc[k] += st["ms_" + k]
+        launches += st["n_launches"]
+        last = st
+    ev1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    n_total = w.N * world
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n_total / (ms / 1000)
+
+    # end to end through the host entry point: pinned input in, pinned result out
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    h_i = torch.empty(M, dtype=torch.int32, pin_memory=True)
+    h_j = torch.empty(M, dtype=torch.int32, pin_memory=True)
+    h_v = torch.empty(M, dtype=torch.uint8, pin_memory=True)
+    from paper_1803_09835_gb300 import fast_detect_host
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        m2 = fast_detect_host(s.ctx, h_idx, w.N, ld, h_i, h_j, h_v, M)
+    torch.cuda.synchronize()
+    e2e_ms = 1000 * (time.perf_counter() - t0) / e2e_steps
+    assert m2 == M
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # roofline of the dominant kernel
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    per = {k: acc[k] / args.steps for k in STAGES}
+    dom = max(("sig", "sort", "sparse", "enum", "output"), key=lambda k: per[k])
+    bytes_ = stage_bytes(w, w.N, last)[dom]
+    achieved = bytes_ / (per[dom] / 1000) / 1e9 if per[dom] > 0 else 0.0
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+            "algorithmic_bytes": bytes_, "ms": per[dom]}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": workload_config(w, world, {"detections_per_station": M}),
+            "e2e": {"value": n_total / (e2e_ms / 1000), "unit": UNIT, "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": w.N * ld * 2, "d2h_bytes_per_step": M * 9},
+            "gpu_launches": launches, "roofline": roof, "clocks": clk,
+            "stage_ms": per,
+            "counters": {k: last[k] for k in ("n_dropped", "n_emissions", "n_dense_pairs", "n_groups",
+                                              "n_detections", "map_slots", "query_parts", "sort_passes")}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, thr, Ms = oracle_sample(w, args.cpu_sample)
+        line["cpu_baseline"] = {"value": args.cpu_sample / dt, "unit": UNIT, "cores": thr, "kind": "oracle",
+                                "sample": f"first {args.cpu_sample:,} windows of the same workload, whole path "
+                                          f"(keys on {thr} threads, filter, search single-threaded), "
+                                          f"{dt:.1f} s, {Ms:,} detections"}
+    s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("gb300", "reference"), default="gb300")
+    ap.add_argument("--workload", default="c1")
+    ap.add_argument("--n", type=int, default=0, help="override N (windows per station) for quick runs")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=300_000)
+    ap.add_argument("--ref-sample", type=int, default=100_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    rc = gpu_arm(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,211 @@
+/*
+ * fast.h -- C-ABI of the GB300 LSH similarity search over binary waveform
+ * fingerprints (Rong et al., "Locality-Sensitive Hashing for Earthquake
+ * Detection: A Case Study of Scaling Data-Driven Science", §6).
+ *
+ * Problem (§6.1): given N binary fingerprints (one per time window, §5.1),
+ * find every pair (i, j), i < j, that shares a hash bucket in at least v of
+ * b independent hash tables, where each table keys a fingerprint by r
+ * MinHash (or Min-Max hash, §6.2) values.  Pairs of nearby windows
+ * (j - i <= excl) are excluded as self-matches (§7.1 "Station Level"), and
+ * fingerprints caught by the occurrence filter (§6.5) take part in no pair.
+ * Each detection is reported as (i, j, votes); in the paper's triplet form
+ * (§7.2) that is (dt = j - i, idx1 = i, sim = votes).
+ *
+ * Conventions for every call:
+ *   - Pointers named d_* are device pointers on the context's device; h_*
+ *     are host pointers (pinned memory is faster but not required).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; device inputs must stay valid until
+ *     the stream reaches the call's work.
+ *   - Every call returns fast_status and never aborts.  Invalid arguments are
+ *     reported as FAST_EINVAL before any work is enqueued; invalid data found
+ *     on the device (an index >= D) is reported by the call that synchronises
+ *     on it.  fast_last_error() gives a human-readable message.
+ *   - Objects returned through out-pointers (tables, results) are owned by the
+ *     caller and must be released with the matching *_free; they must not
+ *     outlive the context that made them.
+ *   - There is no CPU fallback: without a usable CUDA device every call fails
+ *     with FAST_ECUDA.
+ */
+#ifndef FAST_H
+#define FAST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FAST_OK = 0,
+    FAST_EINVAL = 1,    /* bad argument or bad input data                     */
+    FAST_ENOMEM = 2,    /* device allocation failed                            */
+    FAST_EBUDGET = 3,   /* the work does not fit the context's HBM budget      */
+    FAST_EMAPFULL = 4,  /* a device hash map ran past its probe limit          */
+    FAST_ETIMEOUT = 5,  /* a bounded wait ran out                              */
+    FAST_EPENDING = 6,  /* a streamed request is not finished yet              */
+    FAST_ECUDA = 7,     /* a CUDA runtime call failed                          */
+    FAST_EINTERNAL = 8  /* broken internal invariant (a bug)                   */
+} fast_status;
+
+typedef enum {
+    FAST_MINHASH = 0, /* §6.1: r minima per table, F = b*r functions                  */
+    FAST_MINMAX = 1   /* §6.2: min and max per function, F = b*ceil(r/2) functions    */
+} fast_hash_kind;
+
+/*
+ * Search parameters.  Paper notation (§6.3): t = b tables, k = r values per
+ * table, m = v matches.
+ *   D, K      fingerprint dimension and set bits per fingerprint (§5.1);
+ *             1 <= K <= D <= 65536.
+ *   b, r      tables and values per table; 1 <= b <= 255, 1 <= r <= 16.
+ *   kind      fast_hash_kind.
+ *   seed      hash seed: the F hash functions h_f(x) = high32(a_f*x + b_f)
+ *             take a_f = sm64(seed, 2f) | 1 and b_f = sm64(seed, 2f+1), where
+ *             sm64(s, n) is the n-th SplitMix64 output of seed s; the bucket
+ *             key of table t folds its r values w into z = sm64(seed, 2F+t)
+ *             by z = mix64(z ^ w) and keeps high32(z) (Algorithm 1,
+ *             hash_combine, with the hash family fixed by this library).
+ *   v         report a pair when it shares a bucket in >= v tables; 1 <= v <= b.
+ *   excl      report a pair only when j - i > excl.
+ *   occ_num, occ_den
+ *             occurrence filter (§6.5), static form: a bucket is heavy when
+ *             occ_den * size > occ_num * N; a fingerprint in heavy buckets in
+ *             more than b/2 tables is dropped.  occ_num = 0 turns it off.
+ *   table_group
+ *             tables sorted and held at once (0 = all b); votes are merged
+ *             across groups (§6.4 "Partition": identical results).
+ *   query_part
+ *             query partitions of the vote map (0 = automatic); identical
+ *             results for any value (§6.4).
+ */
+typedef struct {
+    uint32_t D, K, b, r;
+    uint32_t kind;
+    uint64_t seed;
+    uint32_t v, excl;
+    uint32_t occ_num, occ_den;
+    uint32_t table_group;
+    uint32_t query_part;
+} fast_params;
+
+typedef struct fast_ctx fast_ctx;
+typedef struct fast_tables fast_tables;
+typedef struct fast_result fast_result;
+
+/*
+ * Per-stage device times (ms, CUDA events on the call's stream) and counters
+ * of the most recent fast_detect / fast_search on a context.
+ */
+typedef struct {
+    float ms_sig, ms_sort, ms_filter, ms_enum, ms_dense, ms_sparse, ms_output, ms_total;
+    uint64_t n_fingerprints;  /* N                                                  */
+    uint64_t n_dropped;       /* fingerprints removed by the occurrence filter      */
+    uint64_t n_emissions;     /* sparse bucket pairs counted in the vote map         */
+    uint64_t n_dense_pairs;   /* pairs compared directly inside dense groups         */
+    uint64_t n_groups;        /* dense groups (components of large buckets)          */
+    uint64_t n_detections;    /* M                                                   */
+    uint64_t map_slots;       /* vote-map capacity (slots) of the last partition     */
+    uint64_t n_launches;      /* CUDA kernels launched by the call                   */
+    uint32_t query_parts;     /* query partitions actually used                      */
+    uint32_t sort_passes;     /* radix passes per table sort                         */
+} fast_stats;
+
+/*
+ * Creates a context on the current CUDA device: validates `p`, draws the
+ * hash parameters and builds the per-function rank tables used by fast_sig.
+ * hbm_budget_bytes bounds the device memory the context and the objects it
+ * returns may hold at once (0 = no bound).  *out is NULL on failure.
+ */
+fast_status fast_create(const fast_params *p, uint64_t hbm_budget_bytes, fast_ctx **out);
+
+/* Releases the context and its workspace.  NULL is a no-op. */
+void fast_destroy(fast_ctx *ctx);
+
+/* Message of the last failure on `ctx` (never NULL; "" after success). */
+const char *fast_last_error(const fast_ctx *ctx);
+
+/*
+ * Signature generation (§6.1 "Hash signature generation", §6.2 Min-Max hash,
+ * Algorithm 1).  d_idx: N rows of ld >= K uint16 set-bit indices (row i at
+ * d_idx + i*ld; order within a row does not matter; entries K..ld-1 are
+ * ignored).  Writes d_sig[t*N + i] = bucket key of fingerprint i in table t
+ * (table-major, b*N uint32, caller-allocated).  An index >= D makes the call
+ * fail with FAST_EINVAL when it synchronises (fast_sig synchronises `stream`).
+ */
+fast_status fast_sig(fast_ctx *ctx, const uint16_t *d_idx, uint64_t N, uint32_t ld, uint32_t *d_sig,
+                     void *stream);
+
+/*
+ * Hash-table construction (§6.1 "Hash table construction") and the
+ * occurrence filter (§6.5).  Reads d_sig (b*N, table-major, as written by
+ * fast_sig) and builds, per table, the (key, id) pairs stably sorted by key
+ * -- each bucket a run of equal keys with ids ascending -- plus the drop mask.
+ * N <= 2^28 - 1.  The tables live in device memory owned by *out.  d_sig
+ * is not copied: it must stay valid and unchanged until fast_search on these
+ * tables has returned (the search compares keys of fingerprint pairs).
+ */
+fast_status fast_build_tables(fast_ctx *ctx, const uint32_t *d_sig, uint64_t N, fast_tables **out,
+                              void *stream);
+
+/*
+ * Device views of a table set: d_skey / d_sid are b*N uint32 (table t at
+ * offset t*N), d_drop is N uint8 (1 = dropped by the occurrence filter).
+ * Any out-pointer may be NULL.
+ */
+fast_status fast_tables_view(const fast_tables *tb, uint64_t *N, uint32_t *b, const uint32_t **d_skey,
+                             const uint32_t **d_sid, const uint8_t **d_drop);
+
+void fast_tables_free(fast_tables *tb);
+
+/*
+ * Search (§6.1 "Search", §6.3 detection threshold, §6.4 partitioned search,
+ * §7.2 output triplets): every pair (i, j), i < j, neither dropped,
+ * j - i > excl, sharing a bucket in votes >= v tables, sorted by (i, j).
+ * `tb` must come from `ctx`.  Synchronises `stream`.
+ */
+fast_status fast_search(fast_ctx *ctx, const fast_tables *tb, fast_result **out, void *stream);
+
+/*
+ * The whole path, idx resident in HBM: fast_sig + fast_build_tables +
+ * fast_search in one call, intermediates held in the context's workspace.
+ */
+fast_status fast_detect(fast_ctx *ctx, const uint16_t *d_idx, uint64_t N, uint32_t ld, fast_result **out,
+                        void *stream);
+
+/*
+ * The whole path from and to host memory: copies h_idx (N rows of ld uint16)
+ * to the device, runs fast_detect, and copies at most `cap` detections back
+ * to h_i / h_j / h_votes.  *M receives the total number of detections (which
+ * may exceed cap; then only the first cap, in (i, j) order, are copied).
+ */
+fast_status fast_detect_host(fast_ctx *ctx, const uint16_t *h_idx, uint64_t N, uint32_t ld, uint64_t *M,
+                             uint32_t *h_i, uint32_t *h_j, uint8_t *h_votes, uint64_t cap, void *stream);
+
+/*
+ * Device views of a result: *M detections as three arrays (structure of
+ * arrays), sorted by (i asc, j asc).  Any out-pointer may be NULL.
+ */
+fast_status fast_result_view(const fast_result *res, uint64_t *M, const uint32_t **d_i, const uint32_t **d_j,
+                             const uint8_t **d_votes);
+
+void fast_result_free(fast_result *res);
+
+/* Stage times and counters of the last search on `ctx`. */
+fast_status fast_get_stats(const fast_ctx *ctx, fast_stats *out);
+
+/*
+ * Tuning knobs; none changes any result.
+ *   "large_min"  live bucket size from which buckets are summed by direct key
+ *                comparison inside groups instead of the vote map (0 = auto)
+ *   "map_load"   target load factor of the vote map, in (0.05, 0.95)
+ *   "timing"     1 = record per-stage CUDA events (default), 0 = off
+ */
+fast_status fast_set_option(fast_ctx *ctx, const char *name, double value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FAST_H */

@@ -1,0 +1,129 @@
+"""GB300-native LSH similarity search over binary waveform fingerprints.
+
+The hot path of FAST-style earthquake detection (Rong et al., §6): MinHash /
+Min-Max signatures, banding into per-table bucket keys, device radix sort into
+hash tables, the occurrence filter, pair enumeration with near-time exclusion
+and vote counting, thresholded to a canonical (i, j, votes) detection list.
+
+All of it runs in the hand-written sm_103a kernels of ``libfast.so`` behind the
+C-ABI of ``include/fast.h``; ``_lib`` binds those entry points under their C
+names, and :class:`Searcher` is a convenience wrapper over them.  PyTorch only
+provides device memory and streams.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _lib
+from ._lib import (FAST_MINHASH, FAST_MINMAX, FastError, fast_build_tables, fast_create, fast_destroy, fast_detect,
+                   fast_detect_host, fast_get_stats, fast_result_free, fast_result_view, fast_search, fast_set_option,
+                   fast_sig, fast_tables_free, fast_tables_view)
+
+__all__ = ["Searcher", "Result", "Tables", "FastError", "FAST_MINHASH", "FAST_MINMAX", "fast_create", "fast_destroy",
+           "fast_sig", "fast_build_tables", "fast_tables_view", "fast_tables_free", "fast_search", "fast_detect",
+           "fast_detect_host", "fast_result_view", "fast_result_free", "fast_get_stats", "fast_set_option"]
+
+
+class Result:
+    """A detection list held in device memory by the library."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self.M, self.i, self.j, self.votes = fast_result_view(handle, owner=self)
+
+    def numpy(self):
+        """(i, j, votes) as numpy uint32 / uint32 / uint8 arrays."""
+        return (self.i.cpu().numpy().view(np.uint32), self.j.cpu().numpy().view(np.uint32),
+                self.votes.cpu().numpy())
+
+    def free(self):
+        if self.handle:
+            fast_result_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Tables:
+    """Per-table sorted (key, id) arrays and the drop mask, in device memory."""
+
+    def __init__(self, handle, sig):
+        self.handle = handle
+        self.sig = sig  # the keys must outlive the tables (fast_search reads them)
+        self.skey, self.sid, self.drop = fast_tables_view(handle, owner=self)
+
+    def free(self):
+        if self.handle:
+            fast_tables_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Searcher:
+    """One search context: parameters, hash functions, device workspace."""
+
+    def __init__(self, params: dict, hbm_budget_bytes: int = 0, **options):
+        import torch
+        if not torch.cuda.is_available():
+            raise FastError(_lib.FAST_ECUDA, "no CUDA device: this library has no CPU fallback")
+        self.params = dict(params)
+        self.ctx = fast_create(self.params, hbm_budget_bytes)
+        for k, v in options.items():
+            fast_set_option(self.ctx, k, v)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            fast_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, name: str, value: float):
+        fast_set_option(self.ctx, name, value)
+
+    def sig(self, idx, out=None, stream=None):
+        """Bucket keys [b, N] (int32 view of uint32) of the fingerprints idx [N, ld]."""
+        import torch
+        N, ld = idx.shape
+        if out is None:
+            out = torch.empty((self.params["b"], N), dtype=torch.int32, device=idx.device)
+        fast_sig(self.ctx, idx, N, ld, out, stream)
+        return out
+
+    def build_tables(self, sig, stream=None) -> Tables:
+        return Tables(fast_build_tables(self.ctx, sig, sig.shape[1], stream), sig)
+
+    def search(self, tables: Tables, stream=None) -> Result:
+        return Result(fast_search(self.ctx, tables.handle, stream))
+
+    def detect(self, idx, stream=None) -> Result:
+        N, ld = idx.shape
+        return Result(fast_detect(self.ctx, idx, N, ld, stream))
+
+    def detect_host(self, idx: np.ndarray, cap: int | None = None, stream=None):
+        """Whole path from host memory: returns (M, i, j, votes) numpy arrays."""
+        N, ld = idx.shape
+        if cap is None:
+            cap = 1 << 20
+        i = np.empty(cap, np.uint32)
+        j = np.empty(cap, np.uint32)
+        v = np.empty(cap, np.uint8)
+        M = fast_detect_host(self.ctx, idx, N, ld, i, j, v, cap, stream)
+        m = min(M, cap)
+        return M, i[:m], j[:m], v[:m]
+
+    def stats(self) -> dict:
+        return fast_get_stats(self.ctx)

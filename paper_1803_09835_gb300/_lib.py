@@ -1,0 +1,232 @@
+"""ctypes binding of libfast.so (include/fast.h).  Argument marshalling only.
+
+Every function here has the name of the C entry point it calls and takes
+torch tensors (device memory) or numpy arrays (host memory) in place of raw
+pointers.  All work runs in the library's CUDA kernels; if the library is
+missing or no GPU is present the calls raise -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfast.so")
+HEADER = os.path.join(HERE, "..", "include", "fast.h")
+
+STATUS = {0: "FAST_OK", 1: "FAST_EINVAL", 2: "FAST_ENOMEM", 3: "FAST_EBUDGET", 4: "FAST_EMAPFULL",
+          5: "FAST_ETIMEOUT", 6: "FAST_EPENDING", 7: "FAST_ECUDA", 8: "FAST_EINTERNAL"}
+FAST_OK, FAST_EINVAL, FAST_ENOMEM, FAST_EBUDGET, FAST_EMAPFULL, FAST_ETIMEOUT, FAST_EPENDING, FAST_ECUDA, \
+    FAST_EINTERNAL = range(9)
+FAST_MINHASH, FAST_MINMAX = 0, 1
+
+
+class FastError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class fast_params(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_uint32), ("K", ctypes.c_uint32), ("b", ctypes.c_uint32), ("r", ctypes.c_uint32),
+                ("kind", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("v", ctypes.c_uint32),
+                ("excl", ctypes.c_uint32), ("occ_num", ctypes.c_uint32), ("occ_den", ctypes.c_uint32),
+                ("table_group", ctypes.c_uint32), ("query_part", ctypes.c_uint32)]
+
+
+class fast_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in ("ms_sig", "ms_sort", "ms_filter", "ms_enum", "ms_dense", "ms_sparse",
+                                              "ms_output", "ms_total")] + \
+               [(n, ctypes.c_uint64) for n in ("n_fingerprints", "n_dropped", "n_emissions", "n_dense_pairs",
+                                               "n_groups", "n_detections", "map_slots", "n_launches")] + \
+               [("query_parts", ctypes.c_uint32), ("sort_passes", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load():
+    """Loads libfast.so (built by ``__graft_entry__.build()``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first (__graft_entry__.build()); "
+                          "there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, u64, u32, st = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    pp = ctypes.POINTER
+    sigs = {
+        "fast_create": (st, [pp(fast_params), u64, pp(vp)]),
+        "fast_destroy": (None, [vp]),
+        "fast_last_error": (ctypes.c_char_p, [vp]),
+        "fast_sig": (st, [vp, vp, u64, u32, vp, vp]),
+        "fast_build_tables": (st, [vp, vp, u64, pp(vp), vp]),
+        "fast_tables_view": (st, [vp, pp(u64), pp(u32), pp(vp), pp(vp), pp(vp)]),
+        "fast_tables_free": (None, [vp]),
+        "fast_search": (st, [vp, vp, pp(vp), vp]),
+        "fast_detect": (st, [vp, vp, u64, u32, pp(vp), vp]),
+        "fast_detect_host": (st, [vp, vp, u64, u32, pp(u64), vp, vp, vp, u64, vp]),
+        "fast_result_view": (st, [vp, pp(u64), pp(vp), pp(vp), pp(vp)]),
+        "fast_result_free": (None, [vp]),
+        "fast_get_stats": (st, [vp, pp(fast_stats)]),
+        "fast_set_option": (st, [vp, ctypes.c_char_p, ctypes.c_double]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype, fn.argtypes = res, args
+    _lib = lib
+    return lib
+
+
+def _check(ctx, status: int):
+    if status != FAST_OK:
+        msg = load().fast_last_error(ctx).decode() if ctx else ""
+        raise FastError(status, msg)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dptr(t, dtype=None):
+    import torch
+    if t is None:
+        return None
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    if dtype is not None:
+        assert t.dtype == dtype, f"expected {dtype}, got {t.dtype}"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    assert a.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class _DevArray:
+    """Zero-copy view of library-owned device memory (__cuda_array_interface__)."""
+
+    def __init__(self, ptr, n, typestr, owner):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr or 0, False),
+                                         "version": 3, "strides": None}
+        self._owner = owner
+
+
+def _view(ptr, n, typestr, owner):
+    import torch
+    if n == 0:
+        dt = {"<i4": torch.int32, "|u1": torch.uint8}[typestr]
+        return torch.empty(0, dtype=dt, device="cuda")
+    return torch.as_tensor(_DevArray(ptr, n, typestr, owner), device="cuda")
+
+
+def params_struct(params: dict) -> fast_params:
+    p = fast_params()
+    for k, _ in fast_params._fields_:
+        setattr(p, k, int(params.get(k, 0)))
+    return p
+
+
+# --------------------------------------------------------------- C names
+
+def fast_create(params: dict, hbm_budget_bytes: int = 0) -> ctypes.c_void_p:
+    lib = load()
+    out = ctypes.c_void_p()
+    _check(None, lib.fast_create(ctypes.byref(params_struct(params)), hbm_budget_bytes, ctypes.byref(out)))
+    return out
+
+
+def fast_destroy(ctx):
+    load().fast_destroy(ctx)
+
+
+def fast_sig(ctx, d_idx, N: int, ld: int, d_sig, stream=None):
+    import torch
+    _check(ctx, load().fast_sig(ctx, _dptr(d_idx), N, ld, _dptr(d_sig), _stream(stream)))
+
+
+def fast_build_tables(ctx, d_sig, N: int, stream=None):
+    out = ctypes.c_void_p()
+    _check(ctx, load().fast_build_tables(ctx, _dptr(d_sig), N, ctypes.byref(out), _stream(stream)))
+    return out
+
+
+def fast_tables_view(tb, owner=None):
+    """(skey [b*N] int32 view, sid [b*N] int32 view, drop [N] uint8 view)."""
+    N, b = ctypes.c_uint64(), ctypes.c_uint32()
+    k, s, d = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(None, load().fast_tables_view(tb, ctypes.byref(N), ctypes.byref(b), ctypes.byref(k), ctypes.byref(s),
+                                         ctypes.byref(d)))
+    n = N.value * b.value
+    return (_view(k.value, n, "<i4", owner), _view(s.value, n, "<i4", owner), _view(d.value, N.value, "|u1", owner))
+
+
+def fast_tables_free(tb):
+    load().fast_tables_free(tb)
+
+
+def fast_search(ctx, tb, stream=None):
+    out = ctypes.c_void_p()
+    _check(ctx, load().fast_search(ctx, tb, ctypes.byref(out), _stream(stream)))
+    return out
+
+
+def fast_detect(ctx, d_idx, N: int, ld: int, stream=None):
+    out = ctypes.c_void_p()
+    _check(ctx, load().fast_detect(ctx, _dptr(d_idx), N, ld, ctypes.byref(out), _stream(stream)))
+    return out
+
+
+def fast_detect_host(ctx, h_idx, N: int, ld: int, h_i, h_j, h_votes, cap: int, stream=None) -> int:
+    M = ctypes.c_uint64()
+    _check(ctx, load().fast_detect_host(ctx, _hptr(h_idx), N, ld, ctypes.byref(M),
+                                        _hptr(h_i) if cap else None, _hptr(h_j) if cap else None,
+                                        _hptr(h_votes) if cap else None, cap, _stream(stream)))
+    return M.value
+
+
+def fast_result_view(res, owner=None):
+    """(M, i [M] int32 view, j [M] int32 view, votes [M] uint8 view)."""
+    M = ctypes.c_uint64()
+    i, j, v = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(None, load().fast_result_view(res, ctypes.byref(M), ctypes.byref(i), ctypes.byref(j), ctypes.byref(v)))
+    m = M.value
+    return m, _view(i.value, m, "<i4", owner), _view(j.value, m, "<i4", owner), _view(v.value, m, "|u1", owner)
+
+
+def fast_result_free(res):
+    load().fast_result_free(res)
+
+
+def fast_get_stats(ctx) -> dict:
+    s = fast_stats()
+    _check(ctx, load().fast_get_stats(ctx, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def fast_set_option(ctx, name: str, value: float):
+    _check(ctx, load().fast_set_option(ctx, name.encode(), float(value)))
+
+
+def header_functions() -> list[str]:
+    """Names of the entry points declared in include/*.h."""
+    import glob
+    import re
+    names = []
+    for h in sorted(glob.glob(os.path.join(HERE, "..", "include", "*.h"))):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names += re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?[\s\*])(fast_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def fast_last_error(ctx) -> str:
+    return load().fast_last_error(ctx).decode()

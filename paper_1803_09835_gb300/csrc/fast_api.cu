@@ -1,0 +1,360 @@
+// fast_api.cu -- the C-ABI entry points (include/fast.h), the context's
+// stream-ordered memory pool with its HBM budget, error plumbing and stage
+// timers.  Every step of the search runs in the kernels of k_sig.cu,
+// k_sort.cu and k_search.cu; this file only validates, allocates and
+// sequences them.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "fast_internal.cuh"
+
+using namespace fastgb;
+
+namespace fastgb {
+
+fast_status set_error(fast_ctx *c, fast_status st, const std::string &msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+fast_status cuda_fail(fast_ctx *c, cudaError_t e, const char *where) {
+    cudaGetLastError();  // clear a sticky-free error so the context stays usable
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return set_error(c, e == cudaErrorMemoryAllocation ? FAST_ENOMEM : FAST_ECUDA, m);
+}
+
+fast_status dalloc(fast_ctx *c, void **p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (c->budget && c->live + bytes > c->budget)
+        return set_error(c, FAST_EBUDGET,
+                         "HBM budget exceeded: " + std::to_string(c->live + bytes) + " > " + std::to_string(c->budget));
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, c->pool, s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(c, e, "device allocation");
+    }
+    c->live += bytes;
+    c->peak = std::max(c->peak, c->live);
+    return FAST_OK;
+}
+
+void dfree(fast_ctx *c, void *p, size_t bytes, cudaStream_t s) {
+    if (!p) return;
+    if (bytes == 0) bytes = 16;
+    cudaFreeAsync(p, s);
+    c->live -= std::min<uint64_t>(c->live, bytes);
+}
+
+fast_status sync_check(fast_ctx *c, cudaStream_t s, const char *where) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(c, e, where);
+    uint32_t flags = 0;
+    e = cudaMemcpy(&flags, c->d_err, 4, cudaMemcpyDeviceToHost);
+    if (e) return cuda_fail(c, e, where);
+    if (!flags) return FAST_OK;
+    cudaMemset(c->d_err, 0, 4);
+    std::string w(where);
+    if (flags & ERR_BAD_INDEX) return set_error(c, FAST_EINVAL, w + ": fingerprint index >= D");
+    if (flags & ERR_WALK) return set_error(c, FAST_EINVAL, w + ": fingerprint with no valid index");
+    if (flags & ERR_MAP_FULL) return set_error(c, FAST_EMAPFULL, w + ": vote map probe limit reached");
+    if (flags & ERR_OVERFLOW) return set_error(c, FAST_EINTERNAL, w + ": device list capacity exceeded");
+    return set_error(c, FAST_EINTERNAL, w + ": device error flag " + std::to_string(flags));
+}
+
+static uint32_t g_marked = 0;  // slots recorded in the current call (per process; calls are not reentrant per ctx)
+
+void stage_mark(fast_ctx *c, int slot, cudaStream_t s) {
+    if (!c->timing) return;
+    cudaEventRecord(c->ev[slot], s);
+    g_marked |= 1u << slot;
+}
+
+float stage_ms(fast_ctx *c, int a, int b) {
+    if (!c->timing || !(g_marked >> a & 1) || !(g_marked >> b & 1)) return 0.f;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[a], c->ev[b]) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.f;
+    }
+    return ms;
+}
+
+}  // namespace fastgb
+
+static fast_status validate(const fast_params *p, std::string &why) {
+    if (!p) return why = "params is NULL", FAST_EINVAL;
+    if (p->D < 1 || p->D > 65536) return why = "D must be in [1, 65536]", FAST_EINVAL;
+    if (p->K < 1 || p->K > p->D) return why = "K must be in [1, D]", FAST_EINVAL;
+    if (p->b < 1 || p->b > 255) return why = "b must be in [1, 255]", FAST_EINVAL;
+    if (p->r < 1 || p->r > 16) return why = "r must be in [1, 16]", FAST_EINVAL;
+    if (p->kind != FAST_MINHASH && p->kind != FAST_MINMAX) return why = "unknown hash kind", FAST_EINVAL;
+    if (p->v < 1 || p->v > p->b) return why = "v must be in [1, b]", FAST_EINVAL;
+    if (p->occ_num > 0 && p->occ_den == 0) return why = "occ_den must be > 0 when the filter is on", FAST_EINVAL;
+    if (p->query_part > 64) return why = "query_part must be <= 64", FAST_EINVAL;
+    return FAST_OK;
+}
+
+static void stats_times(fast_ctx *c, bool whole) {
+    fast_stats &s = c->stats;
+    s.ms_sig = whole ? stage_ms(c, 0, 1) : 0.f;
+    s.ms_sort = whole ? stage_ms(c, 1, 2) : 0.f;
+    s.ms_filter = whole ? stage_ms(c, 2, 9) : 0.f;
+    s.ms_enum = stage_ms(c, 3, 4);
+    s.ms_dense = stage_ms(c, 4, 5) + stage_ms(c, 5, 6);
+    s.ms_sparse = stage_ms(c, 6, 7);
+    s.ms_output = stage_ms(c, 7, 8);
+    s.ms_total = whole ? stage_ms(c, 0, 8) : stage_ms(c, 3, 8);
+}
+
+extern "C" {
+
+fast_status fast_create(const fast_params *p, uint64_t hbm_budget_bytes, fast_ctx **out) {
+    if (!out) return FAST_EINVAL;
+    *out = nullptr;
+    std::string why;
+    if (validate(p, why)) return FAST_EINVAL;
+    int dev = 0, n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return FAST_ECUDA;
+    }
+    cudaGetDevice(&dev);
+    fast_ctx *c = new fast_ctx();
+    c->p = *p;
+    c->device = dev;
+    c->budget = hbm_budget_bytes;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaError_t e = cudaMemPoolCreate(&c->pool, &props);
+    if (e) {
+        fast_status st = cuda_fail(c, e, "cudaMemPoolCreate");
+        delete c;
+        return st;
+    }
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    if ((e = cudaMalloc(&c->d_err, 4)) || (e = cudaMemset(c->d_err, 0, 4)) ||
+        (e = cudaMalloc(&c->d_scal, sizeof(uint64_t) * kScal)) ||
+        (e = cudaMallocHost(&c->h_scal, sizeof(uint64_t) * kScal))) {
+        fast_status st = cuda_fail(c, e, "fast_create");
+        fast_destroy(c);
+        return st;
+    }
+    for (auto &ev : c->ev) cudaEventCreate(&ev);
+    fast_status st = sig_setup(c);
+    if (st) {
+        fast_destroy(c);
+        return st;
+    }
+    *out = c;
+    return FAST_OK;
+}
+
+void fast_destroy(fast_ctx *c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    cudaFree(c->d_a);
+    cudaFree(c->d_b);
+    cudaFree(c->d_zinit);
+    cudaFree(c->d_walk);
+    cudaFree(c->d_err);
+    cudaFree(c->d_scal);
+    if (c->h_scal) cudaFreeHost(c->h_scal);
+    for (auto &ev : c->ev)
+        if (ev) cudaEventDestroy(ev);
+    if (c->pool) cudaMemPoolDestroy(c->pool);
+    cudaGetLastError();
+    delete c;
+}
+
+const char *fast_last_error(const fast_ctx *c) { return c ? c->err.c_str() : "no context"; }
+
+fast_status fast_sig(fast_ctx *c, const uint16_t *d_idx, uint64_t N, uint32_t ld, uint32_t *d_sig, void *stream) {
+    if (!c) return FAST_EINVAL;
+    c->err.clear();
+    if ((N && (!d_idx || !d_sig)) || ld < c->p.K) return set_error(c, FAST_EINVAL, "fast_sig: bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    c->stats.n_launches = 0;
+    fast_status st = sig_launch(c, d_idx, N, ld, d_sig, s);
+    if (st) return st;
+    return sync_check(c, s, "fast_sig");
+}
+
+static fast_status build_tables(fast_ctx *c, const uint32_t *d_sig, uint64_t N, fast_tables **out, cudaStream_t s) {
+    *out = nullptr;
+    if (N > (1ull << 28) - 1) return set_error(c, FAST_EINVAL, "N must be < 2^28");
+    if (N && !d_sig) return set_error(c, FAST_EINVAL, "d_sig is NULL");
+    const uint32_t nb = c->p.b;
+    fast_tables *tb = new fast_tables();
+    tb->ctx = c;
+    tb->N = N;
+    tb->b = nb;
+    tb->d_sig = d_sig;
+    tb->stream = s;
+    const size_t n = (size_t)nb * N;
+    uint32_t *ka = nullptr, *va = nullptr;
+    fast_status st;
+    if ((st = dalloc_t(c, &tb->d_skey, n, s)) || (st = dalloc_t(c, &tb->d_sid, n, s)) ||
+        (st = dalloc_t(c, &tb->d_drop, N ? N : 1, s)) || (st = dalloc_t(c, &ka, n, s)) ||
+        (st = dalloc_t(c, &va, n, s))) {
+        dfree(c, ka, n * 4, s);
+        dfree(c, va, n * 4, s);
+        fast_tables_free(tb);
+        return st;
+    }
+    uint32_t *ko = nullptr, *vo = nullptr;
+    st = sort_u32(c, nb, N, d_sig, nullptr, ka, va, tb->d_skey, tb->d_sid, 0, 32, &ko, &vo, s, &c->stats.sort_passes);
+    if (!st && N && ko != tb->d_skey) {  // odd number of passes: result sits in the scratch pair
+        cudaMemcpyAsync(tb->d_skey, ko, n * 4, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(tb->d_sid, vo, n * 4, cudaMemcpyDeviceToDevice, s);
+    }
+    dfree(c, ka, n * 4, s);
+    dfree(c, va, n * 4, s);
+    stage_mark(c, 2, s);
+    if (!st) st = filter_launch(c, tb, s);
+    stage_mark(c, 9, s);
+    if (st) {
+        fast_tables_free(tb);
+        return st;
+    }
+    *out = tb;
+    return FAST_OK;
+}
+
+fast_status fast_build_tables(fast_ctx *c, const uint32_t *d_sig, uint64_t N, fast_tables **out, void *stream) {
+    if (!c || !out) return FAST_EINVAL;
+    c->err.clear();
+    c->stats.n_launches = 0;
+    return build_tables(c, d_sig, N, out, (cudaStream_t)stream);
+}
+
+fast_status fast_tables_view(const fast_tables *tb, uint64_t *N, uint32_t *b, const uint32_t **d_skey,
+                             const uint32_t **d_sid, const uint8_t **d_drop) {
+    if (!tb) return FAST_EINVAL;
+    if (N) *N = tb->N;
+    if (b) *b = tb->b;
+    if (d_skey) *d_skey = tb->d_skey;
+    if (d_sid) *d_sid = tb->d_sid;
+    if (d_drop) *d_drop = tb->d_drop;
+    return FAST_OK;
+}
+
+void fast_tables_free(fast_tables *tb) {
+    if (!tb) return;
+    fast_ctx *c = tb->ctx;
+    const size_t n = (size_t)tb->b * tb->N;
+    dfree(c, tb->d_skey, n * 4, tb->stream);
+    dfree(c, tb->d_sid, n * 4, tb->stream);
+    dfree(c, tb->d_drop, tb->N ? tb->N : 1, tb->stream);
+    delete tb;
+}
+
+fast_status fast_search(fast_ctx *c, const fast_tables *tb, fast_result **out, void *stream) {
+    if (!c || !tb || !out || tb->ctx != c) return FAST_EINVAL;
+    c->err.clear();
+    *out = nullptr;
+    g_marked = 0;
+    c->stats.n_launches = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    fast_status st = search_run(c, tb, tb->d_sig, out, s);
+    if (!st) stats_times(c, false);
+    return st;
+}
+
+fast_status fast_detect(fast_ctx *c, const uint16_t *d_idx, uint64_t N, uint32_t ld, fast_result **out,
+                        void *stream) {
+    if (!c || !out) return FAST_EINVAL;
+    c->err.clear();
+    *out = nullptr;
+    if ((N && !d_idx) || ld < c->p.K) return set_error(c, FAST_EINVAL, "fast_detect: bad arguments");
+    if (N > (1ull << 28) - 1) return set_error(c, FAST_EINVAL, "N must be < 2^28");
+    cudaStream_t s = (cudaStream_t)stream;
+    g_marked = 0;
+    c->stats.n_launches = 0;
+    stage_mark(c, 0, s);
+    uint32_t *sig = nullptr;
+    const size_t n = (size_t)c->p.b * N;
+    fast_status st = dalloc_t(c, &sig, n ? n : 1, s);
+    if (st) return st;
+    st = sig_launch(c, d_idx, N, ld, sig, s);
+    stage_mark(c, 1, s);
+    fast_tables *tb = nullptr;
+    if (!st) st = build_tables(c, sig, N, &tb, s);  // synchronises: reports bad indices too
+    if (!st) st = search_run(c, tb, sig, out, s);
+    fast_tables_free(tb);
+    dfree(c, sig, n * 4, s);
+    if (!st) stats_times(c, true);
+    c->stats.n_fingerprints = N;
+    return st;
+}
+
+fast_status fast_detect_host(fast_ctx *c, const uint16_t *h_idx, uint64_t N, uint32_t ld, uint64_t *M,
+                             uint32_t *h_i, uint32_t *h_j, uint8_t *h_votes, uint64_t cap, void *stream) {
+    if (!c || !M || (N && !h_idx) || (cap && (!h_i || !h_j || !h_votes))) return FAST_EINVAL;
+    c->err.clear();
+    cudaStream_t s = (cudaStream_t)stream;
+    uint16_t *d_idx = nullptr;
+    const size_t bytes = (size_t)N * ld * 2;
+    fast_status st = dalloc(c, (void **)&d_idx, bytes, s);
+    if (st) return st;
+    if (N) cudaMemcpyAsync(d_idx, h_idx, bytes, cudaMemcpyHostToDevice, s);
+    fast_result *res = nullptr;
+    st = fast_detect(c, d_idx, N, ld, &res, stream);
+    dfree(c, d_idx, bytes, s);
+    if (st) return st;
+    *M = res->M;
+    const uint64_t m = std::min<uint64_t>(cap, res->M);
+    if (m) {
+        cudaMemcpyAsync(h_i, res->d_i, m * 4, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(h_j, res->d_j, m * 4, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(h_votes, res->d_votes, m, cudaMemcpyDeviceToHost, s);
+    }
+    st = sync_check(c, s, "fast_detect_host copy-out");
+    fast_result_free(res);
+    return st;
+}
+
+fast_status fast_result_view(const fast_result *r, uint64_t *M, const uint32_t **d_i, const uint32_t **d_j,
+                             const uint8_t **d_votes) {
+    if (!r) return FAST_EINVAL;
+    if (M) *M = r->M;
+    if (d_i) *d_i = r->d_i;
+    if (d_j) *d_j = r->d_j;
+    if (d_votes) *d_votes = r->d_votes;
+    return FAST_OK;
+}
+
+void fast_result_free(fast_result *r) {
+    if (!r) return;
+    fast_ctx *c = r->ctx;
+    const uint64_t m = r->M ? r->M : 1;
+    dfree(c, r->d_i, m * 4, r->stream);
+    dfree(c, r->d_j, m * 4, r->stream);
+    dfree(c, r->d_votes, m, r->stream);
+    delete r;
+}
+
+fast_status fast_get_stats(const fast_ctx *c, fast_stats *out) {
+    if (!c || !out) return FAST_EINVAL;
+    *out = c->stats;
+    return FAST_OK;
+}
+
+fast_status fast_set_option(fast_ctx *c, const char *name, double value) {
+    if (!c || !name) return FAST_EINVAL;
+    if (!strcmp(name, "large_min")) c->large_min = (uint32_t)std::max(0.0, value);
+    else if (!strcmp(name, "map_load")) {
+        if (!(value > 0.05 && value < 0.95)) return set_error(c, FAST_EINVAL, "map_load must be in (0.05, 0.95)");
+        c->map_load = (float)value;
+    } else if (!strcmp(name, "timing")) c->timing = value != 0;
+    else return set_error(c, FAST_EINVAL, std::string("unknown option ") + name);
+    return FAST_OK;
+}
+
+}  // extern "C"

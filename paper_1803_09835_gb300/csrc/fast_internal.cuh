@@ -1,0 +1,169 @@
+// fast_internal.cuh -- shared definitions of the GB300 search library.
+//
+// Device side: SplitMix64 mixing used by the hash parameters and by
+// hash_combine (Algorithm 1), device error flags, launch helpers.
+// Host side: the context (parameters, per-function rank tables, memory pool,
+// stage timers) and the stream-ordered allocator with the HBM budget.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fast.h"
+
+namespace fastgb {
+
+// ----------------------------------------------------------------- device
+
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
+// SplitMix64 finaliser (Steele, Lea & Flood 2014).
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// n-th SplitMix64 output for `seed`.
+__host__ __device__ __forceinline__ uint64_t sm64(uint64_t seed, uint64_t n) {
+    return mix64(seed + (n + 1) * kGamma);
+}
+
+// h(x) = high 32 bits of a*x + b (mod 2^64): one 32x32->64 multiply-add of
+// the low half of a plus a 32-bit multiply-add of the high half.
+__device__ __forceinline__ uint32_t hash_ab(uint32_t a_lo, uint32_t a_hi, uint64_t b, uint32_t x) {
+    uint64_t t = (uint64_t)a_lo * x + b;
+    return (uint32_t)(t >> 32) + a_hi * x;
+}
+
+// Device error flags, OR-ed into ctx->d_err.
+enum : uint32_t {
+    ERR_BAD_INDEX = 1u << 0,   // fingerprint index >= D
+    ERR_MAP_FULL = 1u << 1,    // vote map probe limit
+    ERR_OVERFLOW = 1u << 2,    // an output / list capacity was exceeded
+    ERR_WALK = 1u << 3,        // signature walk ran off the end (bad input)
+    ERR_INTERNAL = 1u << 4,
+};
+
+__device__ __forceinline__ void set_err(uint32_t *err, uint32_t bit) { atomicOr(err, bit); }
+
+// ------------------------------------------------------------------- host
+
+struct StageTimer;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace fastgb
+
+struct fast_ctx {
+    fast_params p{};
+    int device = 0;
+    int num_sms = 0;
+    uint32_t F = 0;        // hash functions
+    uint32_t W = 0;        // walks: F (MinHash) or 2F (Min-Max)
+    bool use_walk = false;
+    uint32_t Dpad = 0;     // walk sequence length (multiple of 8)
+    // device constants
+    uint64_t *d_a = nullptr;      // [F]
+    uint64_t *d_b = nullptr;      // [F]
+    uint64_t *d_zinit = nullptr;  // [b] combine start values
+    uint16_t *d_walk = nullptr;   // [W][Dpad] x in ascending (min walks) / descending (max walks) h order
+    uint32_t *d_err = nullptr;    // device error flags
+    uint64_t *d_scal = nullptr;   // small device scalars (counters), kScal entries
+    uint64_t *h_scal = nullptr;   // pinned mirror
+    // memory
+    cudaMemPool_t pool = nullptr;
+    uint64_t budget = 0;   // 0 = unbounded
+    uint64_t live = 0;     // bytes currently allocated through the pool
+    uint64_t peak = 0;
+    // tuning
+    uint32_t large_min = 0;     // live bucket size from which a bucket goes to the dense path (0 = auto)
+    float map_load = 0.5f;      // vote-map load factor target
+    // instrumentation
+    fast_stats stats{};
+    cudaEvent_t ev[16] = {};
+    bool timing = true;
+    std::string err;
+};
+
+struct fast_tables {
+    fast_ctx *ctx = nullptr;
+    uint64_t N = 0;
+    uint32_t b = 0;
+    const uint32_t *d_sig = nullptr;  // [b][N] keys the tables were built from (caller-owned)
+    uint32_t *d_skey = nullptr;  // [b][N]
+    uint32_t *d_sid = nullptr;   // [b][N]
+    uint8_t *d_drop = nullptr;   // [N]
+    uint64_t n_dropped = 0;
+    cudaStream_t stream = nullptr;
+};
+
+struct fast_result {
+    fast_ctx *ctx = nullptr;
+    uint64_t M = 0;
+    uint32_t *d_i = nullptr;
+    uint32_t *d_j = nullptr;
+    uint8_t *d_votes = nullptr;
+    cudaStream_t stream = nullptr;
+};
+
+#define FAST_LAUNCHED(c) ((c)->stats.n_launches++)
+
+namespace fastgb {
+
+constexpr int kScal = 128;
+
+// Stream-ordered allocation from the context's pool, checked against the budget.
+fast_status dalloc(fast_ctx *c, void **p, size_t bytes, cudaStream_t s);
+void dfree(fast_ctx *c, void *p, size_t bytes, cudaStream_t s);
+
+template <typename T>
+inline fast_status dalloc_t(fast_ctx *c, T **p, size_t count, cudaStream_t s) {
+    return dalloc(c, reinterpret_cast<void **>(p), count * sizeof(T), s);
+}
+
+fast_status set_error(fast_ctx *c, fast_status st, const std::string &msg);
+fast_status cuda_fail(fast_ctx *c, cudaError_t e, const char *where);
+
+// Synchronises `s` and converts device error flags into a status.
+fast_status sync_check(fast_ctx *c, cudaStream_t s, const char *where);
+
+inline unsigned ceil_div(uint64_t a, uint64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// ------------------------------------------------------------ kernel launchers
+// k_sig.cu
+fast_status sig_setup(fast_ctx *c);
+fast_status sig_launch(fast_ctx *c, const uint16_t *d_idx, uint64_t N, uint32_t ld, uint32_t *d_sig,
+                       cudaStream_t s);
+
+// k_sort.cu: stable LSD radix sort of `nseg` equal segments of length `len`.
+// Keys in/out, optional 32-bit values (vals_in == nullptr -> values are the
+// element index within its segment).  Sorts on bits [bit0, bit1).  Result is
+// left in (keys_out, vals_out); keys_tmp/vals_tmp are scratch of equal size.
+struct SortScratch {
+    uint32_t *counts = nullptr;   // [nseg][256][nchunks]
+    uint64_t *offsets = nullptr;  // [nseg][256][nchunks]
+    size_t cap_entries = 0;
+};
+fast_status sort_u32(fast_ctx *c, uint32_t nseg, uint64_t len, const uint32_t *keys_in, const uint32_t *vals_in,
+                     uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, uint32_t bit0,
+                     uint32_t bit1, uint32_t **keys_out, uint32_t **vals_out, cudaStream_t s, uint32_t *passes);
+fast_status sort_u64(fast_ctx *c, uint64_t len, uint64_t *keys_a, uint64_t *keys_b, uint32_t bit0, uint32_t bit1,
+                     uint64_t **keys_out, cudaStream_t s);
+
+// k_search.cu
+fast_status filter_launch(fast_ctx *c, fast_tables *tb, cudaStream_t s);
+fast_status search_run(fast_ctx *c, const fast_tables *tb, const uint32_t *d_sig, fast_result **out,
+                       cudaStream_t s);
+
+// timing helpers (fast_api.cu)
+void stage_mark(fast_ctx *c, int slot, cudaStream_t s);
+float stage_ms(fast_ctx *c, int a, int b);
+
+}  // namespace fastgb

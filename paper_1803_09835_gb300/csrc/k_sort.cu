@@ -1,0 +1,255 @@
+// k_sort.cu -- stable LSD radix sort used to build the hash tables
+// (§6.1 "Hash table construction": each table maps a signature to the list
+// of fingerprints sharing it) and to order the detection list.
+//
+// One launch sorts `nseg` equal-length segments (all b tables at once).
+// Each 8-bit pass is reduce-then-scan, with no inter-CTA waits:
+//   k_hist    per (segment, chunk) digit counts        -- reads keys
+//   k_scan    per segment exclusive scan, digit-major  -- tiny
+//   k_scatter per chunk: stable rank of every key inside the chunk (warp
+//             match_any + per-warp counters), staging in shared memory in
+//             digit order, then coalesced runs written to the digit's
+//             global position.
+// Stability makes the ids of a bucket come out ascending, i.e. the canonical
+// bucket listing (key ascending, id ascending).
+#include <algorithm>
+
+#include "fast_internal.cuh"
+
+namespace fastgb {
+
+namespace {
+
+constexpr int kRadix = 256;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 8;
+constexpr int kSub = kThreads * kItems;  // 2048 keys per sub-tile
+constexpr int kSubPerChunk = 4;
+constexpr int kChunk = kSub * kSubPerChunk;  // 8192 keys per chunk
+
+template <typename KT>
+__device__ __forceinline__ uint32_t digit_of(KT k, uint32_t shift) {
+    return (uint32_t)(k >> shift) & (kRadix - 1);
+}
+
+template <typename KT>
+__global__ void __launch_bounds__(kThreads) k_hist(const KT *__restrict__ keys, uint64_t len, uint32_t nchunks,
+                                                   uint32_t shift, uint32_t *__restrict__ counts) {
+    __shared__ uint32_t h[kWarps][kRadix];
+    const uint32_t seg = blockIdx.y, chunk = blockIdx.x;
+    for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const KT *k = keys + (uint64_t)seg * len;
+    const uint64_t lo = (uint64_t)chunk * kChunk, hi = std::min<uint64_t>(lo + kChunk, len);
+    const int warp = threadIdx.x >> 5;
+    for (uint64_t e = lo + threadIdx.x; e < hi; e += kThreads) atomicAdd(&h[warp][digit_of(k[e], shift)], 1u);
+    __syncthreads();
+    uint32_t d = threadIdx.x, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; w++) tot += h[w][d];
+    counts[((uint64_t)seg * kRadix + d) * nchunks + chunk] = tot;
+}
+
+// Exclusive scan over one segment's [digit][chunk] counts.
+__global__ void __launch_bounds__(1024) k_scan(const uint32_t *__restrict__ counts, uint64_t *__restrict__ offsets,
+                                               uint32_t nchunks) {
+    __shared__ uint64_t wsum[32];
+    const uint64_t n = (uint64_t)kRadix * nchunks;
+    const uint32_t *c = counts + (uint64_t)blockIdx.x * n;
+    uint64_t *o = offsets + (uint64_t)blockIdx.x * n;
+    const uint64_t per = (n + blockDim.x - 1) / blockDim.x;
+    const uint64_t lo = std::min<uint64_t>(n, per * threadIdx.x), hi = std::min<uint64_t>(n, lo + per);
+    uint64_t s = 0;
+    for (uint64_t i = lo; i < hi; i++) s += c[i];
+    // block exclusive scan of s
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t x = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint64_t y = __shfl_up_sync(~0u, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t v = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint64_t y = __shfl_up_sync(~0u, v, d);
+            if (lane >= d) v += y;
+        }
+        wsum[lane] = v;
+    }
+    __syncthreads();
+    uint64_t run = x - s + (warp > 0 ? wsum[warp - 1] : 0);
+    for (uint64_t i = lo; i < hi; i++) {
+        o[i] = run;
+        run += c[i];
+    }
+}
+
+template <typename KT, bool HAS_VAL, bool IOTA>
+__global__ void __launch_bounds__(kThreads) k_scatter(const KT *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                                      KT *__restrict__ kout, uint32_t *__restrict__ vout, uint64_t len,
+                                                      uint32_t nchunks, uint32_t shift,
+                                                      const uint64_t *__restrict__ offsets) {
+    __shared__ uint64_t run[kRadix];
+    __shared__ uint32_t wcnt[kWarps][kRadix];
+    __shared__ uint32_t tot[kRadix], dstart[kRadix], wscan[kWarps];
+    __shared__ KT sk[kSub];
+    __shared__ uint32_t sv[HAS_VAL ? kSub : 1];
+
+    const uint32_t seg = blockIdx.y, chunk = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1;
+    const KT *ki = kin + (uint64_t)seg * len;
+    const uint32_t *vi = HAS_VAL && !IOTA ? vin + (uint64_t)seg * len : nullptr;
+    KT *ko = kout + (uint64_t)seg * len;
+    uint32_t *vo = HAS_VAL ? vout + (uint64_t)seg * len : nullptr;
+    run[threadIdx.x] = offsets[((uint64_t)seg * kRadix + threadIdx.x) * nchunks + chunk];
+
+    for (int sub = 0; sub < kSubPerChunk; sub++) {
+        const uint64_t sbase = (uint64_t)chunk * kChunk + (uint64_t)sub * kSub;
+        if (sbase >= len) break;
+        const uint32_t nvalid = (uint32_t)std::min<uint64_t>(kSub, len - sbase);
+#pragma unroll
+        for (int w = 0; w < kWarps; w++) wcnt[w][threadIdx.x] = 0;
+        __syncthreads();
+
+        KT key[kItems];
+        uint32_t val[kItems], dig[kItems], rnk[kItems];
+#pragma unroll
+        for (int j = 0; j < kItems; j++) {
+            const uint32_t e = warp * (kItems * 32) + j * 32 + lane;
+            const bool valid = e < nvalid;
+            key[j] = valid ? ki[sbase + e] : (KT)0;
+            if (HAS_VAL) val[j] = valid ? (IOTA ? (uint32_t)(sbase + e) : vi[sbase + e]) : 0u;
+            dig[j] = valid ? digit_of(key[j], shift) : (uint32_t)kRadix;
+            const uint32_t peers = __match_any_sync(~0u, dig[j]);
+            const uint32_t before = peers & lt_mask;
+            uint32_t basec = 0;
+            if (valid) basec = wcnt[warp][dig[j]];
+            __syncwarp();
+            if (valid && before == 0) wcnt[warp][dig[j]] = basec + __popc(peers);
+            __syncwarp();
+            rnk[j] = basec + __popc(before);
+        }
+        __syncthreads();
+        {   // per digit: exclusive prefix over warps, sub-tile totals
+            const uint32_t d = threadIdx.x;
+            uint32_t r = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; w++) {
+                uint32_t c = wcnt[w][d];
+                wcnt[w][d] = r;
+                r += c;
+            }
+            tot[d] = r;
+            // exclusive scan of tot over the 256 digits
+            uint32_t x = r;
+#pragma unroll
+            for (int s = 1; s < 32; s <<= 1) {
+                uint32_t y = __shfl_up_sync(~0u, x, s);
+                if (lane >= s) x += y;
+            }
+            if (lane == 31) wscan[warp] = x;
+            __syncthreads();
+            uint32_t add = 0;
+            for (int w = 0; w < warp; w++) add += wscan[w];
+            dstart[d] = x - r + add;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kItems; j++) {
+            if (dig[j] < (uint32_t)kRadix) {
+                uint32_t pos = dstart[dig[j]] + wcnt[warp][dig[j]] + rnk[j];
+                sk[pos] = key[j];
+                if (HAS_VAL) sv[pos] = val[j];
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < nvalid; i += kThreads) {
+            KT k = sk[i];
+            uint32_t d = digit_of(k, shift);
+            uint64_t o = run[d] + (i - dstart[d]);
+            ko[o] = k;
+            if (HAS_VAL) vo[o] = sv[i];
+        }
+        __syncthreads();
+        run[threadIdx.x] += tot[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+template <typename KT, bool HAS_VAL>
+fast_status sort_impl(fast_ctx *c, uint32_t nseg, uint64_t len, const KT *keys_in, const uint32_t *vals_in,
+                      KT *ka, uint32_t *va, KT *kb, uint32_t *vb, uint32_t bit0, uint32_t bit1, KT **kout,
+                      uint32_t **vout, cudaStream_t s, uint32_t *passes_out) {
+    const uint32_t npass = (bit1 - bit0 + 7) / 8;
+    if (passes_out) *passes_out = npass;
+    if (len == 0 || nseg == 0 || npass == 0) {
+        *kout = const_cast<KT *>(keys_in);
+        if (vout) *vout = const_cast<uint32_t *>(vals_in);
+        return FAST_OK;
+    }
+    const uint64_t nch64 = (len + kChunk - 1) / kChunk;
+    if (nch64 > 0x7fffffffull) return set_error(c, FAST_EINVAL, "sort: segment too long");
+    const uint32_t nchunks = (uint32_t)nch64;
+    const size_t entries = (size_t)nseg * kRadix * nchunks;
+    uint32_t *counts = nullptr;
+    uint64_t *offs = nullptr;
+    fast_status st;
+    if ((st = dalloc_t(c, &counts, entries, s))) return st;
+    if ((st = dalloc_t(c, &offs, entries, s))) {
+        dfree(c, counts, entries * 4, s);
+        return st;
+    }
+    const KT *src_k = keys_in;
+    const uint32_t *src_v = vals_in;
+    dim3 grid(nchunks, nseg);
+    for (uint32_t pass = 0; pass < npass; pass++) {
+        const uint32_t shift = bit0 + 8 * pass;
+        KT *dk = (pass & 1) ? kb : ka;
+        uint32_t *dv = (pass & 1) ? vb : va;
+        k_hist<KT><<<grid, kThreads, 0, s>>>(src_k, len, nchunks, shift, counts), FAST_LAUNCHED(c);
+        k_scan<<<nseg, 1024, 0, s>>>(counts, offs, nchunks), FAST_LAUNCHED(c);
+        if (HAS_VAL && pass == 0 && src_v == nullptr)
+            k_scatter<KT, true, true><<<grid, kThreads, 0, s>>>(src_k, nullptr, dk, dv, len, nchunks, shift, offs), FAST_LAUNCHED(c);
+        else if (HAS_VAL)
+            k_scatter<KT, true, false><<<grid, kThreads, 0, s>>>(src_k, src_v, dk, dv, len, nchunks, shift, offs), FAST_LAUNCHED(c);
+        else
+            k_scatter<KT, false, false><<<grid, kThreads, 0, s>>>(src_k, nullptr, dk, nullptr, len, nchunks, shift,
+                                                                 offs), FAST_LAUNCHED(c);
+        src_k = dk;
+        src_v = dv;
+    }
+    dfree(c, counts, entries * 4, s);
+    dfree(c, offs, entries * 8, s);
+    cudaError_t e = cudaGetLastError();
+    if (e) return cuda_fail(c, e, "radix sort");
+    *kout = const_cast<KT *>(src_k);
+    if (vout) *vout = const_cast<uint32_t *>(src_v);
+    return FAST_OK;
+}
+
+}  // namespace
+
+fast_status sort_u32(fast_ctx *c, uint32_t nseg, uint64_t len, const uint32_t *keys_in, const uint32_t *vals_in,
+                     uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, uint32_t bit0,
+                     uint32_t bit1, uint32_t **keys_out, uint32_t **vals_out, cudaStream_t s, uint32_t *passes) {
+    return sort_impl<uint32_t, true>(c, nseg, len, keys_in, vals_in, keys_a, vals_a, keys_b, vals_b, bit0, bit1,
+                                     keys_out, vals_out, s, passes);
+}
+
+fast_status sort_u64(fast_ctx *c, uint64_t len, uint64_t *keys_a, uint64_t *keys_b, uint32_t bit0, uint32_t bit1,
+                     uint64_t **keys_out, cudaStream_t s) {
+    // keys start in keys_a; passes alternate b, a, b, ...
+    uint64_t *out = nullptr;
+    fast_status st = sort_impl<uint64_t, false>(c, 1, len, keys_a, nullptr, keys_b, nullptr, keys_a, nullptr, bit0,
+                                                bit1, &out, nullptr, s, nullptr);
+    *keys_out = out;
+    return st;
+}
+
+}  // namespace fastgb

@@ -1,0 +1,275 @@
+"""CUDA path vs the CPU oracle, bit-exact (all integer work).
+
+Every comparison is element by element on the same seeded synthetic inputs:
+signatures [b, N], the canonical table listings (key, id) per table, the drop
+mask, and the final (i, j, votes) list sorted by (i, j).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1803_09835_gb300 import _build
+    _build.build()
+    assert torch.cuda.is_available()
+
+
+def _pad(K):
+    return ((K + 7) // 8) * 8
+
+
+def _searcher(p, **opts):
+    from paper_1803_09835_gb300 import Searcher
+    return Searcher(p, **opts)
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def _oracle_run(p, idx, K):
+    keys = oracle.keys(p, np.ascontiguousarray(idx[:, :K]))
+    d = oracle.drop(p, keys)
+    return keys, d, oracle.search(p, keys, d)
+
+
+def _assert_lists(got, want):
+    gi, gj, gv = got
+    wi, wj, wv = want
+    assert len(gi) == len(wi), (len(gi), len(wi))
+    assert np.array_equal(gi, wi) and np.array_equal(gj, wj) and np.array_equal(gv, wv)
+
+
+SIG_CASES = [
+    ("c0", dict(), 8192, None),                       # MinHash 16x4, D=2048, K=100, unaligned rows
+    ("c0", dict(), 8192, 104),                         # padded rows -> 128-bit loads
+    ("c1", dict(), 5000 + 13, 400),                    # Min-Max 100x4, ragged last tile
+    ("c1", dict(r=3, b=30), 777, 408),                 # odd r: last function gives its min only
+    ("c1", dict(K=40, b=12), 1000, 40),                # K^2 < D: direct-evaluation kernel
+    ("c0", dict(kind=1, r=6, b=10), 33, 104),          # Min-Max on C0 shape, 2 tiles
+]
+
+
+@pytest.mark.parametrize("name,over,n,ld", SIG_CASES)
+def test_signatures_bit_exact(name, over, n, ld):
+    w = synth.scaled(name, n, **over)
+    ld = ld or w.K
+    idx = synth.generate(w, ld=ld)
+    p = w.params()
+    s = _searcher(p)
+    sig = s.sig(torch.from_numpy(idx).cuda())
+    want = oracle.keys(p, np.ascontiguousarray(idx[:, :w.K]))
+    assert np.array_equal(_u32(sig), want)
+    s.close()
+
+
+def test_tables_and_filter_bit_exact():
+    w = synth.scaled("c1", 60_000)
+    idx = synth.generate(w, ld=400)
+    p = w.params()
+    s = _searcher(p)
+    sig = s.sig(torch.from_numpy(idx).cuda())
+    tb = s.build_tables(sig)
+    keys = oracle.keys(p, idx)
+    skey, sid, drop = _u32(tb.skey).reshape(p["b"], -1), _u32(tb.sid).reshape(p["b"], -1), tb.drop.cpu().numpy()
+    for t in range(p["b"]):
+        ok, oi = oracle.table(keys[t])
+        assert np.array_equal(skey[t], ok) and np.array_equal(sid[t], oi), f"table {t}"
+    want_drop = oracle.drop(p, keys)
+    assert want_drop.sum() > 0
+    assert np.array_equal(drop, want_drop)
+    res = s.search(tb)
+    _assert_lists(res.numpy(), oracle.search(p, keys, want_drop))
+    tb.free()
+    s.close()
+
+
+DETECT_CASES = [
+    ("c0", 8192, dict(), dict()),
+    ("c0", 8192, dict(v=1, excl=0), dict(large_min=6)),
+    ("c1", 60_000, dict(), dict()),
+    ("c1", 60_000, dict(), dict(large_min=16)),               # dense groups on every large bucket
+    ("c1", 60_000, dict(query_part=3), dict(map_load=0.8)),   # partitioned vote map
+    ("c1", 40_000, dict(occ_num=0), dict(large_min=64)),      # no filter: the 60 s source stays
+    ("c1", 20_000, dict(kind=0, r=2, b=40, v=3), dict()),     # MinHash on the C1 shape
+]
+
+
+@pytest.mark.parametrize("name,n,over,opts", DETECT_CASES)
+def test_detections_bit_exact(name, n, over, opts):
+    over = dict(over)
+    qp = over.pop("query_part", 0)
+    w = synth.scaled(name, n, **over)
+    idx = synth.generate(w, ld=_pad(w.K))
+    p = dict(w.params(), query_part=qp)
+    s = _searcher(p, **opts)
+    res = s.detect(torch.from_numpy(idx).cuda())
+    got = res.numpy()
+    _, _, want = _oracle_run(p, idx, w.K)
+    assert len(want[0]) > 0
+    _assert_lists(got, want)
+    st = s.stats()
+    assert st["n_detections"] == len(want[0])
+    res.free()
+    s.close()
+
+
+def test_dense_and_sparse_paths_agree():
+    w = synth.scaled("c1", 50_000, occ_num=0)
+    idx = torch.from_numpy(synth.generate(w, ld=400)).cuda()
+    out = []
+    for lm in (0, 10, 100, 10**9):
+        s = _searcher(w.params(), large_min=lm)
+        r = s.detect(idx)
+        out.append((r.numpy(), s.stats()))
+        r.free()
+        s.close()
+    for o, st in out[1:]:
+        _assert_lists(o, out[0][0])
+    assert out[1][1]["n_groups"] > 0 and out[3][1]["n_groups"] == 0
+
+
+def test_host_entry_point_matches_device():
+    w = synth.scaled("c1", 30_000)
+    idx = synth.generate(w, ld=400)
+    s = _searcher(w.params())
+    r = s.detect(torch.from_numpy(idx).cuda())
+    dev = r.numpy()
+    M, i, j, v = s.detect_host(idx, cap=len(dev[0]) + 5)
+    assert M == len(dev[0])
+    _assert_lists((i, j, v), dev)
+    M2, i2, _, _ = s.detect_host(idx, cap=7)  # truncated copy keeps the first cap in order
+    assert M2 == M and np.array_equal(i2, dev[0][:7])
+    r.free()
+    s.close()
+
+
+# ------------------------------------------------------------ edge cases
+
+def _params(**kw):
+    p = dict(D=2048, K=100, b=16, r=4, kind=0, seed=7, v=2, excl=0, occ_num=0, occ_den=1000)
+    p.update(kw)
+    return p
+
+
+def test_empty_and_tiny_inputs():
+    p = _params()
+    s = _searcher(p)
+    for n in (0, 1):
+        r = s.detect(torch.zeros((n, 104), dtype=torch.int16, device="cuda").view(torch.uint16)
+                     if n == 0 else torch.from_numpy(np.arange(104, dtype=np.uint16)[None]).cuda())
+        assert r.M == 0
+        r.free()
+    two = np.stack([np.arange(100, dtype=np.uint16)] * 2)
+    r = s.detect(torch.from_numpy(two).cuda())
+    i, j, v = r.numpy()
+    assert list(zip(i, j, v)) == [(0, 1, 16)]
+    r.free()
+    s.close()
+
+
+@pytest.mark.parametrize("lm", [0, 4, 10**9])
+def test_identical_fingerprints_one_giant_bucket(lm):
+    p = _params(excl=3, v=16)
+    n = 700
+    idx = np.tile(np.arange(0, 2000, 20, dtype=np.uint16), (n, 1))
+    s = _searcher(p, large_min=lm)
+    r = s.detect(torch.from_numpy(idx).cuda())
+    i, j, v = r.numpy()
+    keys = oracle.keys(p, idx)
+    want = oracle.search(p, keys, None)
+    _assert_lists((i, j, v), want)
+    assert len(i) == sum(n - 1 - a - 3 for a in range(n - 4))
+    r.free()
+    s.close()
+
+
+def test_filter_that_drops_everything():
+    w = synth.scaled("c1", 5000, occ_num=1, occ_den=10 * 5000)
+    idx = synth.generate(w, ld=400)
+    s = _searcher(w.params())
+    r = s.detect(torch.from_numpy(idx).cuda())
+    assert r.M == 0 and s.stats()["n_dropped"] == 5000
+    r.free()
+    s.close()
+
+
+def test_bad_index_is_reported_and_context_survives():
+    from paper_1803_09835_gb300 import FastError, _lib
+    p = _params()
+    s = _searcher(p)
+    idx = np.tile(np.arange(100, dtype=np.uint16), (64, 1))
+    idx[5, 7] = 2048  # == D
+    with pytest.raises(FastError) as e:
+        s.detect(torch.from_numpy(idx).cuda())
+    assert e.value.status == _lib.FAST_EINVAL
+    idx[5, 7] = 2047
+    r = s.detect(torch.from_numpy(idx).cuda())
+    assert r.M > 0
+    r.free()
+    s.close()
+
+
+@pytest.mark.parametrize("bad", [dict(b=0), dict(b=256), dict(v=17), dict(r=0), dict(K=3000), dict(kind=2),
+                                 dict(occ_num=1, occ_den=0), dict(D=70000)])
+def test_invalid_parameters(bad):
+    from paper_1803_09835_gb300 import FastError
+    with pytest.raises(FastError):
+        _searcher(_params(**bad))
+
+
+def test_hbm_budget_is_enforced():
+    from paper_1803_09835_gb300 import FastError, _lib
+    from paper_1803_09835_gb300 import Searcher
+    w = synth.scaled("c1", 20_000)
+    idx = torch.from_numpy(synth.generate(w, ld=400)).cuda()
+    s = Searcher(w.params(), hbm_budget_bytes=1 << 20)
+    with pytest.raises(FastError) as e:
+        s.detect(idx)
+    assert e.value.status == _lib.FAST_EBUDGET
+    s.close()
+
+
+# ------------------------------------------------------ full-size workload
+
+@pytest.mark.slow
+def test_c1_full_size_sampled_rows():
+    """The 3-month, 7.776M-window workload in the benchmark's configuration;
+    the oracle recomputes every key and checks sampled rows and entries."""
+    w = synth.workload("c1")
+    idx = synth.generate(w, ld=400)
+    p = w.params()
+    s = _searcher(p)
+    r = s.detect(torch.from_numpy(idx).cuda())
+    gi, gj, gv = r.numpy()
+    st = s.stats()
+    r.free()
+    s.close()
+    torch.cuda.empty_cache()
+    # structural properties of the whole list
+    assert len(gi) > 10**8
+    assert np.all(gi < gj) and np.all(gj.astype(np.int64) - gi > p["excl"]) and np.all(gv >= p["v"])
+    key = (gi.astype(np.uint64) << np.uint64(32)) | gj
+    assert np.all(key[1:] > key[:-1])
+    keys = oracle.keys(p, idx)
+    drop = oracle.drop(p, keys)
+    assert st["n_dropped"] == int(drop.sum())
+    assert not drop[gi].any() and not drop[gj].any()
+    rng = np.random.default_rng(0)
+    # sampled rows: some with detections (noise / template copies), some random
+    rows = np.concatenate([rng.choice(np.unique(gi[::9973]), 12, replace=False), rng.integers(0, w.N, 8)])
+    starts = np.searchsorted(gi, rows)
+    ends = np.searchsorted(gi, rows, side="right")
+    for row, a, b in zip(rows, starts, ends):
+        wj, wv = oracle.search_row(p, keys, drop, int(row))
+        assert np.array_equal(gj[a:b], wj) and np.array_equal(gv[a:b], wv), f"row {row}"
+    # sampled entries: votes from the definition
+    for x in rng.integers(0, len(gi), 3000):
+        assert oracle.pair_votes(p, keys, int(gi[x]), int(gj[x])) == gv[x]
