@@ -204,6 +204,38 @@ fast_status fast_get_stats(const fast_ctx *ctx, fast_stats *out);
  */
 fast_status fast_set_option(fast_ctx *ctx, const char *name, double value);
 
+/*
+ * One table's stable (key, id) sort without any device allocation.
+ * No counterpart in the paper: this is a service entry point of this library.
+ *
+ * Some callers cannot let a library call cudaMalloc: hosts that plan all
+ * device memory themselves up front (a serving process that has already
+ * reserved the GPU's memory for its own pools, so any further driver
+ * allocation fails or would break its budget), and latency-bound callers for
+ * which cudaMalloc's implicit device-wide synchronisation is unacceptable.
+ * This entry point gives them the table-construction step of §6.1: it sorts
+ * d_keys[0..n) by key, stably, and writes d_skey[k] / d_sid[k] = the k-th
+ * (key, original index) pair -- exactly one table of fast_build_tables.
+ *
+ * The caller passes the input and both outputs (n uint32 each, device
+ * memory, not overlapping).  The scratch (one ping-pong pair of keys and ids
+ * plus digit counts, about 8.4 MB) is a fixed array inside the library: every
+ * GPU that loads the library holds it until the process exits.
+ *   - n <= 1048576 (2^20); larger n returns FAST_EINVAL and does nothing.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, on the current device); make that first call before any
+ *     stream capture.
+ *   - All calls on a device share the array: calls whose GPU work overlaps
+ *     (different streams, or host threads without ordering) race and corrupt
+ *     each other's results.  Order them on one stream or synchronise between
+ *     them.  Every scratch word a call reads is written earlier in the same
+ *     call, so nothing left by a previous call leaks into the result.
+ * Returns FAST_OK once the work is enqueued on `stream`, FAST_EINVAL for bad
+ * arguments, FAST_ECUDA if a CUDA call fails.
+ */
+fast_status fast_table_sort_static(const uint32_t *d_keys, uint64_t n, uint32_t *d_skey, uint32_t *d_sid,
+                                   void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,7 @@ def load():
         "fast_result_free": (None, [vp]),
         "fast_get_stats": (st, [vp, pp(fast_stats)]),
         "fast_set_option": (st, [vp, ctypes.c_char_p, ctypes.c_double]),
+        "fast_table_sort_static": (st, [vp, u64, vp, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -230,3 +231,8 @@ def header_functions() -> list[str]:
 
 def fast_last_error(ctx) -> str:
     return load().fast_last_error(ctx).decode()
+
+
+def fast_table_sort_static(d_keys, n: int, d_skey, d_sid, stream=None):
+    """Sorts one table's keys with the library's fixed scratch (no allocation)."""
+    _check(None, load().fast_table_sort_static(_dptr(d_keys), n, _dptr(d_skey), _dptr(d_sid), _stream(stream)))

@@ -13,6 +13,7 @@
 // Stability makes the ids of a bucket come out ascending, i.e. the canonical
 // bucket listing (key ascending, id ascending).
 #include <algorithm>
+#include <mutex>
 
 #include "fast_internal.cuh"
 
@@ -253,3 +254,85 @@ fast_status sort_u64(fast_ctx *c, uint64_t len, uint64_t *keys_a, uint64_t *keys
 }
 
 }  // namespace fastgb
+
+namespace fastgb {
+// ---------------------------------------------------------------------------
+// fast_table_sort_static: one table's stable (key, id) sort with no device
+// allocation.  Its scratch -- one ping-pong pair of keys and ids plus the
+// per-chunk digit counts and offsets -- lives in the file-scope array below,
+// sized for kStaticMaxKeys keys.  Every GPU that loads this library holds the
+// array until the process exits; all calls on a device share it.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr uint64_t kStaticMaxKeys = 1ull << 20;
+constexpr uint64_t kStaticChunks = (kStaticMaxKeys + kChunk - 1) / kChunk;
+constexpr size_t kStaticCountsBytes = (size_t)kRadix * kStaticChunks * 4;
+constexpr size_t kStaticOffsetsBytes = (size_t)kRadix * kStaticChunks * 8;
+constexpr size_t kStaticBytes = kStaticMaxKeys * 4 * 2 + kStaticCountsBytes + kStaticOffsetsBytes;
+
+static __device__ __align__(256) unsigned char g_sort_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+unsigned char *g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_sort_scratch on the current device, looked up once per
+// device (host code cannot use the symbol itself: it names a host stand-in).
+cudaError_t scratch_for_current_device(unsigned char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_sort_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace fastgb
+
+extern "C" fast_status fast_table_sort_static(const uint32_t *d_keys, uint64_t n, uint32_t *d_skey, uint32_t *d_sid,
+                                              void *stream) {
+    using namespace fastgb;
+    if (n > kStaticMaxKeys) return FAST_EINVAL;
+    if (n == 0) return FAST_OK;
+    if (!d_keys || !d_skey || !d_sid) return FAST_EINVAL;
+    unsigned char *base = nullptr;
+    cudaError_t e = scratch_for_current_device(&base);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return FAST_ECUDA;
+    }
+    uint32_t *tmp_k = reinterpret_cast<uint32_t *>(base);
+    uint32_t *tmp_v = tmp_k + kStaticMaxKeys;
+    uint32_t *counts = reinterpret_cast<uint32_t *>(base + kStaticMaxKeys * 8);
+    uint64_t *offs = reinterpret_cast<uint64_t *>(base + kStaticMaxKeys * 8 + kStaticCountsBytes);
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t nchunks = (uint32_t)((n + kChunk - 1) / kChunk);
+    const dim3 grid(nchunks, 1);
+    // four 8-bit passes: keys -> scratch -> out -> scratch -> out
+    const uint32_t *src_k = d_keys, *src_v = nullptr;
+    for (uint32_t pass = 0; pass < 4; pass++) {
+        uint32_t *dk = (pass & 1) ? d_skey : tmp_k;
+        uint32_t *dv = (pass & 1) ? d_sid : tmp_v;
+        const uint32_t shift = 8 * pass;
+        k_hist<uint32_t><<<grid, kThreads, 0, s>>>(src_k, n, nchunks, shift, counts);
+        k_scan<<<1, 1024, 0, s>>>(counts, offs, nchunks);
+        if (pass == 0)
+            k_scatter<uint32_t, true, true><<<grid, kThreads, 0, s>>>(src_k, nullptr, dk, dv, n, nchunks, shift, offs);
+        else
+            k_scatter<uint32_t, true, false><<<grid, kThreads, 0, s>>>(src_k, src_v, dk, dv, n, nchunks, shift, offs);
+        src_k = dk;
+        src_v = dv;
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? FAST_OK : FAST_ECUDA;
+}
