@@ -108,6 +108,9 @@ typedef struct {
     uint64_t n_detections;    /* M                                                   */
     uint64_t map_slots;       /* vote-map capacity (slots) of the last partition     */
     uint64_t n_launches;      /* CUDA kernels launched by the call                   */
+    uint64_t n_long_rows;     /* rows too long for the first vote tier (> 358 candidates) */
+    uint64_t n_huge_rows;     /* rows voted by a whole CTA (> 1433 candidates)       */
+    uint64_t max_row;         /* most candidates of one row among the CTA-voted rows */
     uint32_t query_parts;     /* query partitions actually used                      */
     uint32_t sort_passes;     /* radix passes per table sort                         */
 } fast_stats;
@@ -201,6 +204,9 @@ fast_status fast_get_stats(const fast_ctx *ctx, fast_stats *out);
  *                comparison inside groups instead of the vote map (0 = auto)
  *   "map_load"   target load factor of the vote map, in (0.05, 0.95)
  *   "timing"     1 = record per-stage CUDA events (default), 0 = off
+ *   "vote_map"   1 = sum sparse votes in one global open-addressing map of
+ *                packed (i, j) -> votes and order the list by a radix sort;
+ *                0 = count them row by row (default)
  */
 fast_status fast_set_option(fast_ctx *ctx, const char *name, double value);
 

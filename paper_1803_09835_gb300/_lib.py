@@ -38,7 +38,7 @@ class fast_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_float) for n in ("ms_sig", "ms_sort", "ms_filter", "ms_enum", "ms_dense", "ms_sparse",
                                               "ms_output", "ms_total")] + \
                [(n, ctypes.c_uint64) for n in ("n_fingerprints", "n_dropped", "n_emissions", "n_dense_pairs",
-                                               "n_groups", "n_detections", "map_slots", "n_launches")] + \
+                                               "n_groups", "n_detections", "map_slots", "n_launches", "n_long_rows", "n_huge_rows", "max_row")] + \
                [("query_parts", ctypes.c_uint32), ("sort_passes", ctypes.c_uint32)]
 
     def as_dict(self):

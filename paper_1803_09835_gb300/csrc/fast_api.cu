@@ -103,9 +103,9 @@ static void stats_times(fast_ctx *c, bool whole) {
     s.ms_sort = whole ? stage_ms(c, 1, 2) : 0.f;
     s.ms_filter = whole ? stage_ms(c, 2, 9) : 0.f;
     s.ms_enum = stage_ms(c, 3, 4);
-    s.ms_dense = stage_ms(c, 4, 5) + stage_ms(c, 5, 6);
-    s.ms_sparse = stage_ms(c, 6, 7);
-    s.ms_output = stage_ms(c, 7, 8);
+    s.ms_dense = stage_ms(c, 4, 5);
+    s.ms_sparse = stage_ms(c, 5, 6);
+    s.ms_output = stage_ms(c, 6, 8);
     s.ms_total = whole ? stage_ms(c, 0, 8) : stage_ms(c, 3, 8);
 }
 
@@ -353,6 +353,7 @@ fast_status fast_set_option(fast_ctx *c, const char *name, double value) {
         if (!(value > 0.05 && value < 0.95)) return set_error(c, FAST_EINVAL, "map_load must be in (0.05, 0.95)");
         c->map_load = (float)value;
     } else if (!strcmp(name, "timing")) c->timing = value != 0;
+    else if (!strcmp(name, "vote_map")) c->vote_map = value != 0;
     else return set_error(c, FAST_EINVAL, std::string("unknown option ") + name);
     return FAST_OK;
 }

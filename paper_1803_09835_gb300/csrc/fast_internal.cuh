@@ -85,6 +85,7 @@ struct fast_ctx {
     // tuning
     uint32_t large_min = 0;     // live bucket size from which a bucket goes to the dense path (0 = auto)
     float map_load = 0.5f;      // vote-map load factor target
+    bool vote_map = false;      // sum sparse votes in one global hash map instead of per row
     // instrumentation
     fast_stats stats{};
     cudaEvent_t ev[16] = {};
@@ -156,6 +157,11 @@ fast_status sort_u32(fast_ctx *c, uint32_t nseg, uint64_t len, const uint32_t *k
                      uint32_t bit1, uint32_t **keys_out, uint32_t **vals_out, cudaStream_t s, uint32_t *passes);
 fast_status sort_u64(fast_ctx *c, uint64_t len, uint64_t *keys_a, uint64_t *keys_b, uint32_t bit0, uint32_t bit1,
                      uint64_t **keys_out, cudaStream_t s);
+
+// k_scan.cu: out[seg][k] = sum of in[seg][0..k), nseg segments of n counts;
+// totals[seg] (optional, device) receives each segment's sum.
+fast_status scan_excl(fast_ctx *c, const uint32_t *in, uint64_t *out, uint64_t n, uint32_t nseg, uint64_t *totals,
+                      cudaStream_t s);
 
 // k_search.cu
 fast_status filter_launch(fast_ctx *c, fast_tables *tb, cudaStream_t s);

@@ -534,6 +534,631 @@ __global__ void k_unpack(const unsigned long long *__restrict__ in, uint64_t M, 
     }
 }
 
+// ------------------------------------------------- row-partitioned votes
+
+__device__ __forceinline__ uint32_t row_hash(uint32_t j) { return (uint32_t)(mix64(j) >> 32); }
+
+// Hash insert of one occurrence of j (key j+1, 0 = empty); counts are bytes
+// packed four to a word (votes never exceed b <= 255).
+__device__ __forceinline__ bool gadd8(uint32_t *K, uint32_t *C32, uint32_t slots, uint32_t j) {
+    const uint32_t want = j + 1;
+    uint32_t h = row_hash(j) & (slots - 1);
+    for (uint32_t probe = 0; probe < slots; probe++) {
+        uint32_t kk = K[h];
+        if (kk == 0) {
+            kk = atomicCAS(K + h, 0u, want);
+            if (kk == 0) kk = want;
+        }
+        if (kk == want) {
+            atomicAdd(C32 + (h >> 2), 1u << (8 * (h & 3)));
+            return true;
+        }
+        h = (h + 1) & (slots - 1);
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint32_t cnt8(const uint32_t *C32, uint32_t h) { return (C32[h >> 2] >> (8 * (h & 3))) & 0xFF; }
+
+// Kept entries of one row, written in j order: each kept entry's rank is the
+// number of kept entries with a smaller j (j is unique within a row).
+__device__ __forceinline__ void row_write_sorted(const uint32_t *kj, const uint32_t *kv, uint32_t nk, uint32_t lane,
+                                                 uint32_t nlanes, uint32_t *sp_j, uint8_t *sp_v, uint64_t base) {
+    for (uint32_t x = lane; x < nk; x += nlanes) {
+        const uint32_t jx = kj[x];
+        uint32_t rank = 0;
+        for (uint32_t y = 0; y < nk; y++) rank += kj[y] < jx;
+        sp_j[base + rank] = jx;
+        sp_v[base + rank] = (uint8_t)kv[x];
+    }
+}
+
+__device__ __forceinline__ void row_write_sorted8(const uint32_t *kj, const uint8_t *kv, uint32_t nk, uint32_t lane,
+                                                  uint32_t nlanes, uint32_t *sp_j, uint8_t *sp_v, uint64_t base) {
+    for (uint32_t x = lane; x < nk; x += nlanes) {
+        const uint32_t jx = kj[x];
+        uint32_t rank = 0;
+        for (uint32_t y = 0; y < nk; y++) rank += kj[y] < jx;
+        sp_j[base + rank] = jx;
+        sp_v[base + rank] = kv[x];
+    }
+}
+
+constexpr uint32_t kRowBlockSlots = 16384;  // shared-memory hash of the one-CTA-per-row path
+
+// ------------------------------------------------- group-partitioned votes
+//
+// Rows (pairs keyed by their lower id i) are cut into groups of 2^gshift
+// consecutive ids.  Bucket-major passes over the sorted tables count each
+// group's pairs, then append every pair to its group's region as one packed
+// entry (i's offset in the group, j); with one open sector per group the
+// write frontier stays in L2.  A CTA per group then sorts its entries by row
+// in shared memory and counts each row's duplicates of j in a hash: the
+// number of tables in which i and j share a bucket (§6.1 "Search").
+
+template <typename PT>
+__device__ __forceinline__ PT pack_entry(uint32_t local, uint32_t j, uint32_t nbits) {
+    return ((PT)local << nbits) | (PT)j;
+}
+
+// Small buckets (at most kSmall entries, dropped ones included): one thread
+// per table position x pairs x with every later entry of its bucket.
+template <int MODE, typename PT>
+__global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, uint32_t nbits,
+                                                   uint32_t *__restrict__ gcnt, const uint64_t *__restrict__ goff,
+                                                   uint32_t *__restrict__ gcur, PT *__restrict__ ent) {
+    const uint32_t t = blockIdx.y;
+    const uint64_t N = a.N;
+    const uint32_t *k = a.skey + (uint64_t)t * N;
+    const uint32_t *s = a.sid + (uint64_t)t * N;
+    const uint32_t lmask = (1u << gshift) - 1;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = k[x];
+        uint64_t s0 = x;
+        while (s0 > 0 && x - s0 < kSmall && k[s0 - 1] == key) s0--;
+        if (x - s0 >= kSmall) continue;  // at least kSmall + 1 entries: a big bucket
+        uint64_t e = x + 1;
+        while (e < N && e - s0 <= kSmall && k[e] == key) e++;
+        if (e - s0 > kSmall || e - x == 1) continue;
+        const uint32_t i = s[x];
+        if (a.drop[i]) continue;
+        uint32_t c = 0;
+        for (uint64_t y = x + 1; y < e; y++) {
+            const uint32_t j = s[y];
+            c += !a.drop[j] && pair_live(a, i, j);
+        }
+        if (!c) continue;
+        const uint32_t g = i >> gshift;
+        if (MODE == 0) {
+            atomicAdd(gcnt + g, c);
+        } else {
+            uint64_t o = goff[g] + atomicAdd(gcur + g, c);
+            for (uint64_t y = x + 1; y < e; y++) {
+                const uint32_t j = s[y];
+                if (!a.drop[j] && pair_live(a, i, j)) ent[o++] = pack_entry<PT>(i & lmask, j, nbits);
+            }
+        }
+    }
+}
+
+// Medium buckets (more than kSmall entries, fewer than large_min live): one
+// CTA per bucket, live members compacted in shared memory when they fit.
+template <int MODE, typename PT>
+__global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, const uint4 *__restrict__ medium,
+                                                    const unsigned long long *__restrict__ nmedium, uint32_t gshift,
+                                                    uint32_t nbits, uint32_t *__restrict__ gcnt,
+                                                    const uint64_t *__restrict__ goff, uint32_t *__restrict__ gcur,
+                                                    PT *__restrict__ ent) {
+    __shared__ uint32_t s_m[kMedSmem];
+    __shared__ uint32_t wsum[32];
+    const uint64_t n = *nmedium;
+    const uint32_t lmask = (1u << gshift) - 1;
+    for (uint64_t bi = blockIdx.x; bi < n; bi += gridDim.x) {
+        const uint4 e = medium[bi];
+        const uint32_t *s = a.sid + (uint64_t)e.x * a.N;
+        const bool in_smem = e.w <= kMedSmem;
+        uint32_t nl = 0;
+        if (in_smem) {
+            for (uint32_t q0 = e.y; q0 < e.z; q0 += blockDim.x) {
+                const uint32_t q = q0 + threadIdx.x;
+                uint32_t id = 0, live = 0;
+                if (q < e.z) {
+                    id = s[q];
+                    live = !a.drop[id];
+                }
+                uint32_t tot;
+                const uint32_t pos = block_excl_scan(live, wsum, &tot);
+                if (live && nl + pos < kMedSmem) s_m[nl + pos] = id;
+                nl += tot;
+            }
+            nl = min(nl, kMedSmem);
+            __syncthreads();
+        }
+        const uint32_t lo = in_smem ? 0 : e.y, hi = in_smem ? nl : e.z;
+        for (uint32_t x = lo + threadIdx.x; x < hi; x += blockDim.x) {
+            const uint32_t i = in_smem ? s_m[x] : s[x];
+            if (!in_smem && a.drop[i]) continue;
+            uint32_t c = 0;
+            for (uint32_t y = x + 1; y < hi; y++) {
+                const uint32_t j = in_smem ? s_m[y] : s[y];
+                c += (in_smem || !a.drop[j]) && pair_live(a, i, j);
+            }
+            if (!c) continue;
+            const uint32_t g = i >> gshift;
+            if (MODE == 0) {
+                atomicAdd(gcnt + g, c);
+            } else {
+                uint64_t o = goff[g] + atomicAdd(gcur + g, c);
+                for (uint32_t y = x + 1; y < hi; y++) {
+                    const uint32_t j = in_smem ? s_m[y] : s[y];
+                    if ((in_smem || !a.drop[j]) && pair_live(a, i, j)) ent[o++] = pack_entry<PT>(i & lmask, j, nbits);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+struct VoteArgs {
+    const uint64_t *goff;
+    uint64_t ngroups, N;
+    uint32_t gshift, nbits, v;
+    uint32_t *sp_cnt;
+    uint64_t *sp_start;
+    uint32_t *sp_j;
+    uint8_t *sp_v;
+    uint64_t sp_cap;
+    unsigned long long *sp_cursor;
+    uint2 *long_rows;  // (row, candidate bound) for rows voted one CTA each
+    unsigned long long *n_long;
+    uint64_t long_cap;
+};
+
+// Hash insert for the row votes (key j+1, 0 = empty), 32-bit counts.
+__device__ __forceinline__ bool vadd(uint32_t *K, uint32_t *C, uint32_t slots, uint32_t j) {
+    const uint32_t want = j + 1;
+    uint32_t h = row_hash(j) & (slots - 1);
+    for (uint32_t probe = 0; probe < slots; probe++) {
+        uint32_t kk = K[h];
+        if (kk == 0) {
+            kk = atomicCAS(K + h, 0u, want);
+            if (kk == 0) kk = want;
+        }
+        if (kk == want) {
+            atomicAdd(C + h, 1u);
+            return true;
+        }
+        h = (h + 1) & (slots - 1);
+    }
+    return false;
+}
+
+constexpr uint32_t kVCap = 4096;       // pairs of a group counted in shared memory (larger groups: per row)
+constexpr uint32_t kVTarget = 1536;    // expected pairs per group
+
+template <typename PT>
+size_t group_vote_smem() {
+    return (size_t)2 * kVCap * sizeof(PT) + (size_t)2 * kVCap / 4 * 4;
+}
+
+template <typename PT>
+__device__ __forceinline__ uint32_t ghash(PT key) {
+    return (uint32_t)(mix64((uint64_t)key) >> 32);
+}
+
+// One CTA per group: every entry (local row, j) of the group counted in one
+// shared-memory hash of >= 2n slots; entries seen at least v times are the
+// group's detections, ordered by (local row, j) -- i.e. by (i, j) -- by rank.
+template <typename PT>
+__global__ void __launch_bounds__(256) k_group_vote(VoteArgs A, const PT *__restrict__ ent) {
+    extern __shared__ unsigned long long vsm_raw[];
+    PT *K = reinterpret_cast<PT *>(vsm_raw);                             // [<= 2 kVCap] keys (entry + 1)
+    uint32_t *C = reinterpret_cast<uint32_t *>(K + 2 * kVCap);           // [<= 2 kVCap / 4] byte counts
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t s_nk;
+    __shared__ unsigned long long s_b0;
+    const PT jmask = ((PT)1 << A.nbits) - 1;
+    for (uint64_t g = blockIdx.x; g < A.ngroups; g += gridDim.x) {
+        const uint64_t e0 = A.goff[g], n = A.goff[g + 1] - e0;
+        if (n < A.v) continue;  // block-uniform
+        const uint64_t row0 = g << A.gshift;
+        if (n > kVCap) {  // every row of the group is voted one CTA each
+            for (uint32_t r = threadIdx.x; r < (1u << A.gshift); r += blockDim.x) {
+                if (row0 + r >= A.N) break;
+                unsigned long long q = atomicAdd(A.n_long, 1ull);
+                if (q < A.long_cap) A.long_rows[q] = make_uint2((uint32_t)(row0 + r), (uint32_t)n);
+            }
+            continue;
+        }
+        uint32_t slots = 64;
+        while (slots < 2 * n) slots <<= 1;
+        for (uint32_t x = threadIdx.x; x < slots; x += blockDim.x) K[x] = 0;
+        for (uint32_t x = threadIdx.x; x < slots / 4; x += blockDim.x) C[x] = 0;
+        __syncthreads();
+        for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) {
+            const PT want = ent[e0 + x] + 1;
+            uint32_t h = ghash(want) & (slots - 1);
+            for (uint32_t probe = 0; probe < slots; probe++) {
+                PT kk = K[h];
+                if (kk == 0) {
+                    kk = atomicCAS(K + h, (PT)0, want);
+                    if (kk == 0) kk = want;
+                }
+                if (kk == want) {
+                    atomicAdd(C + (h >> 2), 1u << (8 * (h & 3)));
+                    break;
+                }
+                h = (h + 1) & (slots - 1);
+            }
+        }
+        __syncthreads();
+        // kept entries compacted to the front: key into K, votes into count bytes
+        if (threadIdx.x == 0) s_nk = 0;
+        __syncthreads();
+        for (uint32_t base = 0; base < slots; base += blockDim.x) {
+            const uint32_t x = base + threadIdx.x;
+            PT kk = 0;
+            uint32_t cc = 0;
+            if (x < slots) {
+                kk = K[x];
+                cc = (C[x >> 2] >> (8 * (x & 3))) & 0xFF;
+            }
+            const uint32_t keep = kk != 0 && cc >= A.v;
+            uint32_t tot;
+            const uint32_t pos = s_nk + block_excl_scan(keep, wsum, &tot);
+            __syncthreads();
+            if (keep) {  // pos <= x: never overwrites an unread slot
+                K[pos] = kk - 1;
+                reinterpret_cast<uint8_t *>(C)[pos] = (uint8_t)cc;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) s_nk += tot;
+            __syncthreads();
+        }
+        const uint32_t nk = s_nk;
+        if (!nk) continue;  // block-uniform
+        if (threadIdx.x == 0) s_b0 = atomicAdd(A.sp_cursor, (unsigned long long)nk);
+        __syncthreads();
+        const uint64_t b0 = s_b0;
+        const uint8_t *V = reinterpret_cast<const uint8_t *>(C);
+        for (uint32_t x = threadIdx.x; x < nk; x += blockDim.x) {
+            const PT kx = K[x];
+            uint32_t rank = 0, first = 1;
+            for (uint32_t y = 0; y < nk; y++) {
+                rank += K[y] < kx;
+                first &= (uint32_t)((K[y] >> A.nbits) != (kx >> A.nbits) || K[y] >= kx);
+            }
+            const uint64_t i = row0 + (uint32_t)(kx >> A.nbits);
+            if (b0 + nk <= A.sp_cap) {
+                A.sp_j[b0 + rank] = (uint32_t)(kx & jmask);
+                A.sp_v[b0 + rank] = V[x];
+            }
+            atomicAdd(A.sp_cnt + i, 1u);
+            if (first) A.sp_start[i] = b0 + rank;  // the row's smallest j
+        }
+        __syncthreads();
+    }
+}
+
+// Long rows: one CTA per row, the row's entries filtered out of its group's
+// region; hash of pow2 >= 2n slots in shared memory (up to kRowBlockSlots)
+// or in global scratch at gscratch + gofs[r].
+template <typename PT>
+__global__ void __launch_bounds__(512) k_long_vote(VoteArgs A, const PT *__restrict__ ent,
+                                                   const uint2 *__restrict__ rows, uint64_t nrows,
+                                                   uint32_t *__restrict__ gscratch, const uint64_t *__restrict__ gofs) {
+    extern __shared__ uint32_t sm_row[];
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t s_nk;
+    __shared__ unsigned long long s_b0;
+    const PT jmask = ((PT)1 << A.nbits) - 1;
+    for (uint64_t rr = blockIdx.x; rr < nrows; rr += gridDim.x) {
+        const uint32_t i = rows[rr].x;
+        const uint64_t bound = rows[rr].y;
+        uint32_t slots = 32;
+        while (slots < 2 * bound) slots <<= 1;
+        uint32_t *K = sm_row, *C;
+        if (slots <= kRowBlockSlots) {
+            C = sm_row + slots;
+        } else {
+            K = gscratch + gofs[rr];
+            C = K + slots;
+        }
+        for (uint32_t x = threadIdx.x; x < slots; x += blockDim.x) K[x] = 0, C[x] = 0;
+        __syncthreads();
+        const uint64_t g = i >> A.gshift;
+        const uint32_t local = i & ((1u << A.gshift) - 1);
+        for (uint64_t e = A.goff[g] + threadIdx.x; e < A.goff[g + 1]; e += blockDim.x) {
+            const PT en = ent[e];
+            if ((uint32_t)(en >> A.nbits) == local) vadd(K, C, slots, (uint32_t)(en & jmask));
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_nk = 0;
+        __syncthreads();
+        for (uint32_t base = 0; base < slots; base += blockDim.x) {
+            const uint32_t x = base + threadIdx.x;
+            uint32_t cc = 0, kk = 0;
+            if (x < slots) {
+                cc = C[x];
+                kk = K[x];
+            }
+            const uint32_t keep = kk != 0 && cc >= A.v;
+            uint32_t tot;
+            const uint32_t pos = s_nk + block_excl_scan(keep, wsum, &tot);
+            if (keep) {
+                K[pos] = kk - 1;
+                C[pos] = cc;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) s_nk += tot;
+            __syncthreads();
+        }
+        const uint32_t nk = s_nk;
+        if (nk) {
+            if (threadIdx.x == 0) {
+                s_b0 = atomicAdd(A.sp_cursor, (unsigned long long)nk);
+                A.sp_cnt[i] = nk;
+                A.sp_start[i] = s_b0;
+            }
+            __syncthreads();
+            if (s_b0 + nk <= A.sp_cap) row_write_sorted(K, C, nk, threadIdx.x, blockDim.x, A.sp_j, A.sp_v, s_b0);
+        }
+        __syncthreads();
+    }
+}
+
+// Dense groups, count pass for the row layout: detections per row, one
+// atomic per (row, tile).
+__global__ void __launch_bounds__(256) k_dense_rowcount(const DenseTile *__restrict__ tiles, uint64_t ntiles,
+                                                        const uint32_t *__restrict__ GT, const uint32_t *__restrict__ ids,
+                                                        uint64_t nm, uint32_t nb, uint32_t v, uint32_t excl,
+                                                        uint32_t *__restrict__ dense_cnt) {
+    extern __shared__ uint32_t sd[];
+    uint32_t *sA = sd, *sB = sd + (size_t)nb * kDT;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    for (uint64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const DenseTile T = tiles[ti];
+        const uint32_t a0 = T.g0 + T.ta * kDT, b0 = T.g0 + T.tb * kDT;
+        const uint32_t na = min((uint32_t)kDT, T.n - T.ta * kDT), nbb = min((uint32_t)kDT, T.n - T.tb * kDT);
+        __syncthreads();
+        for (uint32_t x = threadIdx.x; x < nb * kDT; x += blockDim.x) {
+            const uint32_t t = x / kDT, c = x % kDT;
+            sA[x] = c < na ? GT[(uint64_t)t * nm + a0 + c] : 0xFFFFFFFFu;
+            sB[x] = c < nbb ? GT[(uint64_t)t * nm + b0 + c] : 0xFFFFFFFEu;
+        }
+        __syncthreads();
+        uint32_t acc[4][4] = {};
+        for (uint32_t t = 0; t < nb; t++) {
+            const uint4 av = *reinterpret_cast<const uint4 *>(sA + t * kDT + ty * 4);
+            const uint4 bv = *reinterpret_cast<const uint4 *>(sB + t * kDT + tx * 4);
+            const uint32_t A4[4] = {av.x, av.y, av.z, av.w}, B4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+#pragma unroll
+                for (int w = 0; w < 4; w++) acc[u][w] += A4[u] == B4[w];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t ga = T.ta * kDT + ty * 4 + u;
+            uint32_t c = 0;
+            const uint32_t i = ga < T.n ? ids[T.g0 + ga] : 0;
+#pragma unroll
+            for (int w = 0; w < 4; w++) {
+                const uint32_t gb = T.tb * kDT + tx * 4 + w;
+                if (ga < T.n && gb < T.n && ga < gb && acc[u][w] >= v && ids[T.g0 + gb] - i > excl) ++c;
+            }
+#pragma unroll
+            for (int d = 8; d; d >>= 1) c += __shfl_down_sync(~0u, c, d, 16);
+            if (tx == 0 && c) atomicAdd(dense_cnt + i, c);
+        }
+    }
+}
+
+// Dense groups, emit pass: one CTA per strip (group, row tile ta), column
+// tiles taken in increasing order so every row's detections are written in
+// increasing j at row_off[i] + (running count).
+struct DenseStrip {
+    uint32_t g0, n, ta, pad;
+};
+
+__global__ void __launch_bounds__(256) k_dense_rows(const DenseStrip *__restrict__ strips, uint64_t nstrips,
+                                                    const uint32_t *__restrict__ GT, const uint32_t *__restrict__ ids,
+                                                    uint64_t nm, uint32_t nb, uint32_t v, uint32_t excl,
+                                                    const uint64_t *__restrict__ row_off, uint32_t *__restrict__ oi,
+                                                    uint32_t *__restrict__ oj, uint8_t *__restrict__ ov) {
+    extern __shared__ uint32_t sd[];
+    __shared__ uint32_t s_cur[kDT];
+    uint32_t *sA = sd, *sB = sd + (size_t)nb * kDT;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint64_t si = blockIdx.x; si < nstrips; si += gridDim.x) {
+        const DenseStrip S = strips[si];
+        const uint32_t nt = (S.n + kDT - 1) / kDT;
+        const uint32_t a0 = S.g0 + S.ta * kDT;
+        const uint32_t na = min((uint32_t)kDT, S.n - S.ta * kDT);
+        __syncthreads();
+        for (uint32_t x = threadIdx.x; x < nb * kDT; x += blockDim.x) {
+            const uint32_t t = x / kDT, c = x % kDT;
+            sA[x] = c < na ? GT[(uint64_t)t * nm + a0 + c] : 0xFFFFFFFFu;
+        }
+        if (threadIdx.x < kDT) s_cur[threadIdx.x] = 0;
+        uint32_t rid[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t ga = S.ta * kDT + ty * 4 + u;
+            rid[u] = ga < S.n ? ids[S.g0 + ga] : 0;
+        }
+        for (uint32_t tb = S.ta; tb < nt; tb++) {
+            const uint32_t b0 = S.g0 + tb * kDT;
+            const uint32_t nbb = min((uint32_t)kDT, S.n - tb * kDT);
+            __syncthreads();
+            for (uint32_t x = threadIdx.x; x < nb * kDT; x += blockDim.x) {
+                const uint32_t t = x / kDT, c = x % kDT;
+                sB[x] = c < nbb ? GT[(uint64_t)t * nm + b0 + c] : 0xFFFFFFFEu;
+            }
+            __syncthreads();
+            uint32_t acc[4][4] = {};
+            for (uint32_t t = 0; t < nb; t++) {
+                const uint4 av = *reinterpret_cast<const uint4 *>(sA + t * kDT + ty * 4);
+                const uint4 bv = *reinterpret_cast<const uint4 *>(sB + t * kDT + tx * 4);
+                const uint32_t A4[4] = {av.x, av.y, av.z, av.w}, B4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+#pragma unroll
+                    for (int w = 0; w < 4; w++) acc[u][w] += A4[u] == B4[w];
+            }
+            uint32_t jid[4];
+#pragma unroll
+            for (int w = 0; w < 4; w++) {
+                const uint32_t gb = tb * kDT + tx * 4 + w;
+                jid[w] = gb < S.n ? ids[S.g0 + gb] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const uint32_t ga = S.ta * kDT + ty * 4 + u;
+                uint32_t keep = 0;
+#pragma unroll
+                for (int w = 0; w < 4; w++) {
+                    const uint32_t gb = tb * kDT + tx * 4 + w;
+                    if (ga < S.n && gb < S.n && ga < gb && acc[u][w] >= v && jid[w] - rid[u] > excl) keep |= 1u << w;
+                }
+                const uint32_t c = __popc(keep);
+                // inclusive scan over the 16 lanes of this row (same ty)
+                uint32_t inc = c;
+#pragma unroll
+                for (int d = 1; d < 16; d <<= 1) {
+                    uint32_t y = __shfl_up_sync(~0u, inc, d, 16);
+                    if ((lane & 15) >= (uint32_t)d) inc += y;
+                }
+                const uint32_t r = ty * 4 + u;
+                if (c) {
+                    uint64_t o = row_off[rid[u]] + s_cur[r] + (inc - c);
+#pragma unroll
+                    for (int w = 0; w < 4; w++)
+                        if (keep >> w & 1) {
+                            oi[o] = rid[u];
+                            oj[o] = jid[w];
+                            ov[o] = (uint8_t)acc[u][w];
+                            ++o;
+                        }
+                }
+                const uint32_t row_tot = __shfl_sync(~0u, inc, (lane & 16) | 15);
+                __syncthreads();
+                if (tx == 0) s_cur[r] += row_tot;
+            }
+        }
+    }
+}
+
+// Sparse detections placed after the row's dense ones; rows holding both
+// kinds are listed for a merge.
+__global__ void k_sparse_place(uint64_t N, const uint32_t *__restrict__ sp_cnt, const uint64_t *__restrict__ sp_start,
+                               const uint32_t *__restrict__ sp_j, const uint8_t *__restrict__ sp_v,
+                               const uint32_t *__restrict__ dense_cnt, const uint64_t *__restrict__ row_off,
+                               uint32_t *__restrict__ oi, uint32_t *__restrict__ oj, uint8_t *__restrict__ ov,
+                               uint32_t *__restrict__ merge_rows, uint64_t *__restrict__ merge_ofs,
+                               unsigned long long *__restrict__ n_merge, unsigned long long *__restrict__ merge_tot) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t n = sp_cnt[i];
+        if (!n) continue;
+        const uint32_t d = dense_cnt ? dense_cnt[i] : 0;
+        const uint64_t o = row_off[i] + d, s = sp_start[i];
+        for (uint32_t k = 0; k < n; k++) {
+            oi[o + k] = (uint32_t)i;
+            oj[o + k] = sp_j[s + k];
+            ov[o + k] = sp_v[s + k];
+        }
+        if (d) {
+            const unsigned long long q = atomicAdd(n_merge, 1ull);
+            merge_rows[q] = (uint32_t)i;
+            merge_ofs[q] = atomicAdd(merge_tot, (unsigned long long)(d + n));
+        }
+    }
+}
+
+// Rows with dense and sparse detections: the two sorted runs are merged by
+// rank (each entry's position = its index in its run + entries of the other
+// run with a smaller j), through scratch, one CTA per row.
+__global__ void k_row_merge(const uint32_t *__restrict__ rows, uint64_t nrows, const uint32_t *__restrict__ dense_cnt,
+                            const uint32_t *__restrict__ sp_cnt, const uint64_t *__restrict__ row_off,
+                            uint32_t *__restrict__ oj, uint8_t *__restrict__ ov, uint32_t *__restrict__ tj,
+                            uint8_t *__restrict__ tv, const uint64_t *__restrict__ tofs) {
+    for (uint64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const uint32_t i = rows[r];
+        const uint64_t o = row_off[i];
+        const uint32_t d = dense_cnt[i], sn = sp_cnt[i];
+        const uint32_t *J = oj + o;
+        uint32_t *TJ = tj + tofs[r];
+        uint8_t *TV = tv + tofs[r];
+        for (uint32_t x = threadIdx.x; x < d + sn; x += blockDim.x) {
+            const uint32_t jx = J[x];
+            uint32_t lo, hi, other;
+            if (x < d) lo = d, hi = d + sn, other = x;
+            else lo = 0, hi = d, other = x - d;
+            // entries of the other run with j < jx (binary search)
+            uint32_t a = lo, b = hi;
+            while (a < b) {
+                uint32_t m = (a + b) / 2;
+                if (J[m] < jx) a = m + 1;
+                else b = m;
+            }
+            const uint32_t pos = other + (a - lo);
+            TJ[pos] = jx;
+            TV[pos] = ov[o + x];
+        }
+        __syncthreads();
+        for (uint32_t x = threadIdx.x; x < d + sn; x += blockDim.x) {
+            oj[o + x] = TJ[x];
+            ov[o + x] = TV[x];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_add_u32(const uint32_t *__restrict__ a, const uint32_t *__restrict__ b, uint32_t *__restrict__ out,
+                          uint64_t n) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x)
+        out[x] = a[x] + b[x];
+}
+
+// Big buckets only (no pair work): the rows path counts pairs separately.
+__global__ void __launch_bounds__(256) k_find_big(EnumArgs a, uint4 *__restrict__ big,
+                                                  unsigned long long *__restrict__ nbig, uint64_t big_cap,
+                                                  unsigned long long *__restrict__ small_pairs, uint32_t *err) {
+    const uint32_t t = blockIdx.y;
+    const uint64_t N = a.N;
+    const uint32_t *k = a.skey + (uint64_t)t * N;
+    unsigned long long pairs = 0;
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = k[p];
+        if (p > 0 && k[p - 1] == key) continue;
+        uint64_t e = p + 1;
+        while (e < N && e - p <= kSmall && k[e] == key) e++;
+        if (e - p <= kSmall) {  // small bucket: its pairs bound the sparse work
+            pairs += (e - p) * (e - p - 1) / 2;
+            continue;
+        }
+        uint64_t lo = p + kSmall, step = 1, hi;
+        for (;;) {
+            hi = lo + step;
+            if (hi >= N || k[hi] != key) break;
+            lo = hi;
+            step <<= 1;
+        }
+        if (hi > N) hi = N;
+        while (hi - lo > 1) {
+            uint64_t mid = lo + (hi - lo) / 2;
+            if (k[mid] == key) lo = mid;
+            else hi = mid;
+        }
+        unsigned long long slot = atomicAdd(nbig, 1ull);
+        if (slot < big_cap) big[slot] = make_uint4(t, (uint32_t)p, (uint32_t)hi, 0);
+        else set_err(err, ERR_OVERFLOW);
+    }
+    for (int o = 16; o; o >>= 1) pairs += __shfl_down_sync(~0u, pairs, o);
+    if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(small_pairs, pairs);
+}
+
 uint32_t bits_for(uint64_t N) {
     uint32_t nb = 1;
     while (nb < 32 && (1ull << nb) < N) nb++;
@@ -541,7 +1166,8 @@ uint32_t bits_for(uint64_t N) {
 }
 
 struct Scal {  // device scalar slots (ctx->d_scal)
-    enum { NBIG, NLARGE, NMEDIUM, NHEAVY, NDROP, NMEMB, CUR_DENSE, CUR_SPARSE, CHANGED, PART0 };
+    enum { NBIG, NLARGE, NMEDIUM, NHEAVY, NDROP, NMEMB, CUR_DENSE, CUR_SPARSE, CHANGED, NLONG, NMERGE, NMERGE_TOT,
+           NCAND, NMID, SMALLPAIRS, PART0 };
 };
 
 }  // namespace
@@ -587,8 +1213,10 @@ static fast_status read_scal(fast_ctx *c, cudaStream_t s, const char *where) {
     return sync_check(c, s, where);
 }
 
-fast_status search_run(fast_ctx *c, const fast_tables *tb, const uint32_t *d_sig, fast_result **out,
-                       cudaStream_t s) {
+// Global-map search: sparse pairs summed in one open-addressing hash map of
+// packed (i, j) -> votes per query partition, output ordered by a radix sort.
+static fast_status search_map(fast_ctx *c, const fast_tables *tb, const uint32_t *d_sig, fast_result **out,
+                              cudaStream_t s) {
     const fast_params &p = c->p;
     const uint64_t N = tb->N;
     const uint32_t nb = p.b;
@@ -713,7 +1341,6 @@ fast_status search_run(fast_ctx *c, const fast_tables *tb, const uint32_t *d_sig
         if ((st = read_scal(c, s, "dense count"))) return fail(st);
         M_dense = c->h_scal[Scal::CUR_DENSE];
     }
-    stage_mark(c, 5, s);
 
     // ---- sparse vote map, one query partition at a time
     uint64_t M_cap = M_dense;
@@ -728,7 +1355,7 @@ fast_status search_run(fast_ctx *c, const fast_tables *tb, const uint32_t *d_sig
         k_dense<1><<<dg, 256, dsm, s>>>(d_tiles, tiles.size(), GT, ids, nm, nb, p.v, p.excl, nbits, outk,
                                         scal + Scal::CUR_DENSE, M_cap, c->d_err), FAST_LAUNCHED(c);
     }
-    stage_mark(c, 6, s);
+    stage_mark(c, 5, s);
     ea.label = label;
     uint64_t max_part = *std::max_element(part_ub.begin(), part_ub.end());
     const uint64_t map_cap = std::max<uint64_t>(1024, (uint64_t)((double)max_part / c->map_load) + 1);
@@ -757,7 +1384,7 @@ fast_status search_run(fast_ctx *c, const fast_tables *tb, const uint32_t *d_sig
     c->stats.map_slots = map_cap;
     if ((st = read_scal(c, s, "sparse votes"))) return fail(st);
     const uint64_t M_sparse = c->h_scal[Scal::CUR_SPARSE];
-    stage_mark(c, 7, s);
+    stage_mark(c, 6, s);
 
     // ---- canonical order and unpack
     const uint64_t M = M_dense + M_sparse;
@@ -792,6 +1419,333 @@ fast_status search_run(fast_ctx *c, const fast_tables *tb, const uint32_t *d_sig
     c->stats.query_parts = nparts;
     *out = res;
     return FAST_OK;
+}
+
+
+// Sparse pairs of small and medium buckets: count per group, scan, append,
+// vote per row.  PT is the packed entry type (local row, j).
+template <typename PT, typename Alloc>
+static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *medium, uint64_t nmedium,
+                                 uint32_t gshift, uint32_t nbits, uint32_t *sp_cnt, uint64_t *sp_start,
+                                 uint32_t **sp_j_out, uint8_t **sp_v_out, uint2 *long_rows, uint64_t &S_out,
+                                 Alloc &alloc, cudaStream_t s) {
+    const fast_params &p = c->p;
+    const uint64_t N = ea.N;
+    unsigned long long *scal = reinterpret_cast<unsigned long long *>(c->d_scal);
+    fast_status st;
+    const uint64_t ng = (N + (1ull << gshift) - 1) >> gshift;
+    uint32_t *gcnt = nullptr, *gcur = nullptr;
+    uint64_t *goff = nullptr;
+    PT *ent = nullptr;
+    if ((st = alloc(&gcnt, ng)) || (st = alloc(&gcur, ng)) || (st = alloc(&goff, ng + 1))) return st;
+    cudaMemsetAsync(gcnt, 0, ng * 4, s);
+    cudaMemsetAsync(gcur, 0, ng * 4, s);
+    const dim3 eg(std::max(1u, std::min<unsigned>(ceil_div(N, 256), 2048)), p.b);
+    const unsigned mg = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(nmedium, c->num_sms * 8));
+    k_pairs_grp<0, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, gcnt, nullptr, nullptr, nullptr), FAST_LAUNCHED(c);
+    if (nmedium)
+        k_medium_grp<0, PT><<<mg, 256, 0, s>>>(ea, medium, scal + Scal::NMEDIUM, gshift, nbits, gcnt, nullptr, nullptr,
+                                               nullptr), FAST_LAUNCHED(c);
+    if ((st = scan_excl(c, gcnt, goff, ng, 1, goff + ng, s))) return st;
+    uint64_t S = 0;
+    cudaMemcpyAsync(&S, goff + ng, 8, cudaMemcpyDeviceToHost, s);
+    if ((st = sync_check(c, s, "pair count"))) return st;
+    S_out = S;
+    if ((st = alloc(&ent, S))) return st;
+    k_pairs_grp<1, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, nullptr, goff, gcur, ent), FAST_LAUNCHED(c);
+    if (nmedium)
+        k_medium_grp<1, PT><<<mg, 256, 0, s>>>(ea, medium, scal + Scal::NMEDIUM, gshift, nbits, nullptr, goff, gcur,
+                                               ent), FAST_LAUNCHED(c);
+
+    const size_t vsm = group_vote_smem<PT>();
+    cudaFuncSetAttribute(k_group_vote<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
+    int vper = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&vper, k_group_vote<PT>, 256, vsm);
+    uint64_t sp_cap = std::max<uint64_t>(N, 1 << 20);
+    VoteArgs va{goff, ng, N, gshift, nbits, p.v, sp_cnt, sp_start, nullptr, nullptr, 0, scal + Scal::CUR_SPARSE,
+                long_rows, scal + Scal::NLONG, N};
+    for (int attempt = 0; attempt < 2; attempt++) {
+        uint32_t *sp_j = nullptr;
+        uint8_t *sp_v = nullptr;
+        if ((st = alloc(&sp_j, sp_cap)) || (st = alloc(&sp_v, sp_cap))) return st;
+        *sp_j_out = sp_j;
+        *sp_v_out = sp_v;
+        va.sp_j = sp_j;
+        va.sp_v = sp_v;
+        va.sp_cap = sp_cap;
+        cudaMemsetAsync(sp_cnt, 0, N * 4, s);
+        cudaMemsetAsync(scal + Scal::CUR_SPARSE, 0, 8, s);
+        cudaMemsetAsync(scal + Scal::NLONG, 0, 8, s);
+        k_group_vote<PT><<<(unsigned)std::max<uint64_t>(
+                               1, std::min<uint64_t>(ng, (uint64_t)c->num_sms * std::max(vper, 1))),
+                           256, vsm, s>>>(va, ent), FAST_LAUNCHED(c);
+        if ((st = read_scal(c, s, "row votes"))) return st;
+        const uint64_t nlong = c->h_scal[Scal::NLONG];
+        if (nlong > N) return set_error(c, FAST_EINTERNAL, "long-row list overflow");
+        c->stats.n_long_rows = nlong;
+        c->stats.n_huge_rows = 0;
+        if (nlong) {
+            std::vector<uint2> hl(nlong);
+            cudaMemcpyAsync(hl.data(), long_rows, nlong * sizeof(uint2), cudaMemcpyDeviceToHost, s);
+            if ((st = sync_check(c, s, "long rows"))) return st;
+            std::vector<uint64_t> gofs(nlong);
+            uint64_t gtot = 0;
+            for (uint64_t r = 0; r < nlong; r++) {
+                uint64_t slots = 32;
+                while (slots < 2ull * hl[r].y) slots <<= 1;
+                c->stats.max_row = std::max<uint64_t>(c->stats.max_row, hl[r].y);
+                gofs[r] = gtot;
+                if (slots > kRowBlockSlots) {
+                    gtot += 2 * slots;
+                    c->stats.n_huge_rows++;
+                }
+            }
+            uint32_t *gscr = nullptr;
+            uint64_t *d_gofs = nullptr;
+            if ((st = alloc(&gscr, gtot)) || (st = alloc(&d_gofs, nlong))) return st;
+            cudaMemcpyAsync(d_gofs, gofs.data(), nlong * 8, cudaMemcpyHostToDevice, s);
+            const size_t rsm = (size_t)2 * kRowBlockSlots * 4;
+            cudaFuncSetAttribute(k_long_vote<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+            k_long_vote<PT><<<(unsigned)std::min<uint64_t>(nlong, c->num_sms * 2), 512, rsm, s>>>(va, ent, long_rows,
+                                                                                                 nlong, gscr, d_gofs),
+                FAST_LAUNCHED(c);
+            if ((st = read_scal(c, s, "long rows"))) return st;
+        }
+        const uint64_t used = c->h_scal[Scal::CUR_SPARSE];
+        if (used <= sp_cap) return FAST_OK;
+        if (attempt == 1) break;
+        sp_cap = used;  // exact size for the second pass
+    }
+    return set_error(c, FAST_EINTERNAL, "sparse list overflow");
+}
+
+// Row-partitioned search: dense groups, per-row sparse votes, row-ordered
+// output with no global sort.
+static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_t *d_sig, fast_result **out,
+                               cudaStream_t s) {
+    const fast_params &p = c->p;
+    const uint64_t N = tb->N;
+    const uint32_t nb = p.b;
+    fast_status st = FAST_OK;
+    unsigned long long *scal = reinterpret_cast<unsigned long long *>(c->d_scal);
+    std::vector<std::pair<void *, size_t>> owned;
+    auto alloc = [&](auto **ptr, size_t count) -> fast_status {
+        using T = std::remove_reference_t<decltype(**ptr)>;
+        fast_status r = dalloc_t(c, ptr, count ? count : 1, s);
+        if (!r) owned.push_back({(void *)*ptr, (count ? count : 1) * sizeof(T)});
+        return r;
+    };
+    auto release = [&]() {
+        for (auto &o : owned) dfree(c, o.first, o.second, s);
+        owned.clear();
+    };
+    auto fail = [&](fast_status r) {
+        release();
+        return r;
+    };
+    c->stats.n_fingerprints = N;
+    c->stats.n_dropped = tb->n_dropped;
+    c->stats.n_long_rows = c->stats.n_huge_rows = c->stats.max_row = 0;
+    uint32_t large_min = c->large_min;
+    if (!large_min) {
+        double ptop = std::pow((double)p.K / p.D, (double)p.r);
+        large_min = (uint32_t)std::max(512.0, std::min(1e9, 8.0 * N * ptop));
+    }
+    const unsigned blocksN = std::max(1u, std::min<unsigned>(ceil_div(N, 256), c->num_sms * 8));
+
+    // ---- big buckets
+    stage_mark(c, 3, s);
+    cudaMemsetAsync(scal, 0, sizeof(uint64_t) * kScal, s);
+    const uint64_t big_cap = (uint64_t)nb * (N / (kSmall + 1) + 1);
+    uint4 *big = nullptr, *large = nullptr, *medium = nullptr;
+    if ((st = alloc(&big, big_cap))) return fail(st);
+    EnumArgs ea{tb->d_skey, tb->d_sid, tb->d_drop, nullptr, N, p.excl, 0, (uint32_t)N, 1};
+    const dim3 eg(std::max(1u, std::min<unsigned>(ceil_div(N, 256), 2048)), nb);
+    k_find_big<<<eg, 256, 0, s>>>(ea, big, scal + Scal::NBIG, big_cap, scal + Scal::SMALLPAIRS, c->d_err),
+        FAST_LAUNCHED(c);
+    if ((st = read_scal(c, s, "bucket scan"))) return fail(st);
+    const uint64_t nbig = c->h_scal[Scal::NBIG];
+    if ((st = alloc(&large, nbig)) || (st = alloc(&medium, nbig))) return fail(st);
+    k_big_classify<<<std::max<uint64_t>(1, std::min<uint64_t>(nbig, c->num_sms * 8)), 256, 0, s>>>(
+        ea, big, scal + Scal::NBIG, big_cap, large_min, large, scal + Scal::NLARGE, medium, scal + Scal::NMEDIUM,
+        scal + Scal::PART0), FAST_LAUNCHED(c);
+    if ((st = read_scal(c, s, "bucket classify"))) return fail(st);
+    const uint64_t nlarge = c->h_scal[Scal::NLARGE], nmedium = c->h_scal[Scal::NMEDIUM];
+    stage_mark(c, 4, s);
+
+    // ---- dense groups: labels, members, keys, tile schedule, per-row counts
+    uint32_t *label = nullptr, *GT = nullptr, *ids = nullptr, *dense_cnt = nullptr;
+    uint64_t nm = 0, dense_pairs = 0, ngroups = 0;
+    std::vector<DenseTile> tiles;
+    std::vector<DenseStrip> strips;
+    DenseTile *d_tiles = nullptr;
+    DenseStrip *d_strips = nullptr;
+    const size_t dsm = (size_t)2 * nb * kDT * 4;
+    if ((st = alloc(&label, N)) || (st = alloc(&dense_cnt, N))) return fail(st);
+    cudaMemsetAsync(label, 0xFF, N * 4, s);
+    cudaMemsetAsync(dense_cnt, 0, N * 4, s);
+    if (nlarge) {
+        const unsigned lg = (unsigned)std::min<uint64_t>(nlarge, c->num_sms * 8);
+        k_label_init<<<lg, 256, 0, s>>>(large, nlarge, tb->d_sid, tb->d_drop, N, label), FAST_LAUNCHED(c);
+        int it = 0;
+        for (; it < 256; it++) {
+            cudaMemsetAsync(scal + Scal::CHANGED, 0, 8, s);
+            k_label_prop<<<lg, 256, 0, s>>>(large, nlarge, tb->d_sid, tb->d_drop, N, label,
+                                            reinterpret_cast<uint32_t *>(scal + Scal::CHANGED)), FAST_LAUNCHED(c);
+            if ((st = read_scal(c, s, "group labels"))) return fail(st);
+            if (!c->h_scal[Scal::CHANGED]) break;
+        }
+        if (it == 256) return fail(set_error(c, FAST_EINTERNAL, "group labels did not converge"));
+        cudaMemsetAsync(scal + Scal::NMEMB, 0, 8, s);
+        unsigned long long *memb = nullptr, *memb2 = nullptr;
+        if ((st = alloc(&memb, N))) return fail(st);
+        k_collect_members<<<blocksN, 256, 0, s>>>(label, N, memb, scal + Scal::NMEMB), FAST_LAUNCHED(c);
+        if ((st = read_scal(c, s, "group members"))) return fail(st);
+        nm = c->h_scal[Scal::NMEMB];
+        if ((st = alloc(&memb2, nm))) return fail(st);
+        uint64_t *sorted = nullptr;
+        if ((st = sort_u64(c, nm, reinterpret_cast<uint64_t *>(memb), reinterpret_cast<uint64_t *>(memb2), 0,
+                           32 + bits_for(N), &sorted, s)))
+            return fail(st);
+        std::vector<uint64_t> hm(nm);
+        cudaMemcpyAsync(hm.data(), sorted, nm * 8, cudaMemcpyDeviceToHost, s);
+        if ((st = sync_check(c, s, "group members copy"))) return fail(st);
+        if ((st = alloc(&GT, (size_t)nm * nb)) || (st = alloc(&ids, nm))) return fail(st);
+        k_gather_keys<<<std::max(1u, std::min<unsigned>(ceil_div(nm, 128), c->num_sms * 8)), 128, 0, s>>>(
+            reinterpret_cast<unsigned long long *>(sorted), nm, d_sig, N, nb, GT, ids), FAST_LAUNCHED(c);
+        uint64_t g0 = 0;
+        while (g0 < nm) {
+            uint64_t g1 = g0 + 1;
+            while (g1 < nm && (hm[g1] >> 32) == (hm[g0] >> 32)) g1++;
+            const uint32_t n = (uint32_t)(g1 - g0);
+            ngroups++;
+            dense_pairs += (uint64_t)n * (n - 1) / 2;
+            const uint32_t nt = (n + kDT - 1) / kDT;
+            for (uint32_t a = 0; a < nt; a++) {
+                strips.push_back({(uint32_t)g0, n, a, 0});
+                for (uint32_t b = a; b < nt; b++) tiles.push_back({(uint32_t)g0, n, a, b});
+            }
+            g0 = g1;
+        }
+        // longest strips first: they bound the emit pass
+        std::stable_sort(strips.begin(), strips.end(), [](const DenseStrip &x, const DenseStrip &y) {
+            return (x.n + kDT - 1) / kDT - x.ta > (y.n + kDT - 1) / kDT - y.ta;
+        });
+        if ((st = alloc(&d_tiles, tiles.size())) || (st = alloc(&d_strips, strips.size()))) return fail(st);
+        cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(DenseTile), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_strips, strips.data(), strips.size() * sizeof(DenseStrip), cudaMemcpyHostToDevice, s);
+        cudaFuncSetAttribute(k_dense_rowcount, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+        cudaFuncSetAttribute(k_dense_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+        const unsigned dg = (unsigned)std::min<uint64_t>(tiles.size(), (uint64_t)c->num_sms * 4);
+        k_dense_rowcount<<<dg, 256, dsm, s>>>(d_tiles, tiles.size(), GT, ids, nm, nb, p.v, p.excl, dense_cnt),
+            FAST_LAUNCHED(c);
+    }
+    stage_mark(c, 5, s);
+
+    // ---- sparse pairs: group-partitioned emission, per-row votes
+    ea.label = label;
+    uint32_t *sp_cnt = nullptr, *sp_j = nullptr;
+    uint64_t *sp_start = nullptr;
+    uint8_t *sp_v = nullptr;
+    uint2 *long_rows = nullptr;
+    if ((st = alloc(&sp_cnt, N)) || (st = alloc(&sp_start, N)) || (st = alloc(&long_rows, N))) return fail(st);
+    uint64_t S = 0;
+    {
+        const uint64_t S_ub = c->h_scal[Scal::SMALLPAIRS] + c->h_scal[Scal::PART0];
+        const double avg = (double)S_ub / (double)N;
+        const uint32_t nbits = bits_for(N);
+        uint32_t gshift = 0;
+        while (gshift < 12 && (double)(2ull << gshift) * avg <= kVTarget) gshift++;
+        const fast_status r = gshift + nbits <= 32
+                                  ? sparse_groups<uint32_t>(c, ea, medium, nmedium, gshift, nbits, sp_cnt, sp_start,
+                                                            &sp_j, &sp_v, long_rows, S, alloc, s)
+                                  : sparse_groups<unsigned long long>(c, ea, medium, nmedium, gshift, nbits, sp_cnt,
+                                                                      sp_start, &sp_j, &sp_v, long_rows, S, alloc, s);
+        if (r) return fail(r);
+    }
+    stage_mark(c, 6, s);
+
+    // ---- row offsets and the canonical list
+    uint32_t *row_tot = nullptr;
+    uint64_t *row_off = nullptr;
+    if ((st = alloc(&row_tot, N)) || (st = alloc(&row_off, N + 1))) return fail(st);
+    k_add_u32<<<blocksN, 256, 0, s>>>(dense_cnt, sp_cnt, row_tot, N), FAST_LAUNCHED(c);
+    if ((st = scan_excl(c, row_tot, row_off, N, 1, row_off + N, s))) return fail(st);
+    uint64_t M = 0;
+    cudaMemcpyAsync(&M, row_off + N, 8, cudaMemcpyDeviceToHost, s);
+    if ((st = sync_check(c, s, "row offsets"))) return fail(st);
+    stage_mark(c, 7, s);
+    fast_result *res = new fast_result();
+    res->ctx = c;
+    res->stream = s;
+    res->M = M;
+    if ((st = dalloc_t(c, &res->d_i, M ? M : 1, s)) || (st = dalloc_t(c, &res->d_j, M ? M : 1, s)) ||
+        (st = dalloc_t(c, &res->d_votes, M ? M : 1, s))) {
+        fast_result_free(res);
+        return fail(st);
+    }
+    if (!strips.empty())
+        k_dense_rows<<<(unsigned)std::min<uint64_t>(strips.size(), (uint64_t)c->num_sms * 4), 256, dsm, s>>>(
+            d_strips, strips.size(), GT, ids, nm, nb, p.v, p.excl, row_off, res->d_i, res->d_j, res->d_votes),
+            FAST_LAUNCHED(c);
+    uint32_t *merge_rows = reinterpret_cast<uint32_t *>(long_rows);  // reuse: the long-row list is consumed
+    uint64_t *mofs = nullptr;
+    if ((st = alloc(&mofs, N))) {
+        fast_result_free(res);
+        return fail(st);
+    }
+    cudaMemsetAsync(scal + Scal::NMERGE, 0, 16, s);
+    k_sparse_place<<<blocksN, 256, 0, s>>>(N, sp_cnt, sp_start, sp_j, sp_v, dense_cnt, row_off, res->d_i, res->d_j,
+                                           res->d_votes, merge_rows, mofs, scal + Scal::NMERGE,
+                                           scal + Scal::NMERGE_TOT), FAST_LAUNCHED(c);
+    if ((st = read_scal(c, s, "sparse placement"))) {
+        fast_result_free(res);
+        return fail(st);
+    }
+    const uint64_t nmerge = c->h_scal[Scal::NMERGE], mtot = c->h_scal[Scal::NMERGE_TOT];
+    if (nmerge) {
+        uint32_t *tj = nullptr;
+        uint8_t *tv = nullptr;
+        if ((st = alloc(&tj, mtot)) || (st = alloc(&tv, mtot))) {
+            fast_result_free(res);
+            return fail(st);
+        }
+        k_row_merge<<<(unsigned)std::min<uint64_t>(nmerge, c->num_sms * 8), 256, 0, s>>>(
+            merge_rows, nmerge, dense_cnt, sp_cnt, row_off, res->d_j, res->d_votes, tj, tv, mofs), FAST_LAUNCHED(c);
+    }
+    release();
+    stage_mark(c, 8, s);
+    if ((st = sync_check(c, s, "search output"))) {
+        fast_result_free(res);
+        return st;
+    }
+    c->stats.n_emissions = S;
+    c->stats.n_dense_pairs = dense_pairs;
+    c->stats.n_groups = ngroups;
+    c->stats.n_detections = M;
+    c->stats.query_parts = 1;
+    c->stats.map_slots = 0;
+    *out = res;
+    return FAST_OK;
+}
+
+fast_status search_run(fast_ctx *c, const fast_tables *tb, const uint32_t *d_sig, fast_result **out,
+                       cudaStream_t s) {
+    if (tb->N == 0) {  // nothing to launch
+        fast_result *res = new fast_result();
+        res->ctx = c;
+        res->stream = s;
+        fast_status st;
+        if ((st = dalloc_t(c, &res->d_i, 1, s)) || (st = dalloc_t(c, &res->d_j, 1, s)) ||
+            (st = dalloc_t(c, &res->d_votes, 1, s))) {
+            fast_result_free(res);
+            return st;
+        }
+        c->stats = fast_stats{};
+        *out = res;
+        return FAST_OK;
+    }
+    return c->vote_map ? search_map(c, tb, d_sig, out, s) : search_rows(c, tb, d_sig, out, s);
 }
 
 }  // namespace fastgb

@@ -5,7 +5,7 @@
 // One launch sorts `nseg` equal-length segments (all b tables at once).
 // Each 8-bit pass is reduce-then-scan, with no inter-CTA waits:
 //   k_hist    per (segment, chunk) digit counts        -- reads keys
-//   k_scan    per segment exclusive scan, digit-major  -- tiny
+//   scan      per segment exclusive scan, digit-major (k_scan.cu)
 //   k_scatter per chunk: stable rank of every key inside the chunk (warp
 //             match_any + per-warp counters), staging in shared memory in
 //             digit order, then coalesced runs written to the digit's
@@ -214,7 +214,7 @@ fast_status sort_impl(fast_ctx *c, uint32_t nseg, uint64_t len, const KT *keys_i
         KT *dk = (pass & 1) ? kb : ka;
         uint32_t *dv = (pass & 1) ? vb : va;
         k_hist<KT><<<grid, kThreads, 0, s>>>(src_k, len, nchunks, shift, counts), FAST_LAUNCHED(c);
-        k_scan<<<nseg, 1024, 0, s>>>(counts, offs, nchunks), FAST_LAUNCHED(c);
+        if ((st = scan_excl(c, counts, offs, (uint64_t)kRadix * nchunks, nseg, nullptr, s))) break;
         if (HAS_VAL && pass == 0 && src_v == nullptr)
             k_scatter<KT, true, true><<<grid, kThreads, 0, s>>>(src_k, nullptr, dk, dv, len, nchunks, shift, offs), FAST_LAUNCHED(c);
         else if (HAS_VAL)
@@ -227,6 +227,7 @@ fast_status sort_impl(fast_ctx *c, uint32_t nseg, uint64_t len, const KT *keys_i
     }
     dfree(c, counts, entries * 4, s);
     dfree(c, offs, entries * 8, s);
+    if (st) return st;
     cudaError_t e = cudaGetLastError();
     if (e) return cuda_fail(c, e, "radix sort");
     *kout = const_cast<KT *>(src_k);

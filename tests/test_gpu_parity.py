@@ -99,6 +99,9 @@ DETECT_CASES = [
     ("c1", 60_000, dict(query_part=3), dict(map_load=0.8)),   # partitioned vote map
     ("c1", 40_000, dict(occ_num=0), dict(large_min=64)),      # no filter: the 60 s source stays
     ("c1", 20_000, dict(kind=0, r=2, b=40, v=3), dict()),     # MinHash on the C1 shape
+    ("c1", 60_000, dict(), dict(vote_map=1)),                 # global vote map instead of per-row votes
+    ("c1", 60_000, dict(query_part=4), dict(vote_map=1, large_min=10**9)),
+    ("c1", 30_000, dict(occ_num=0), dict(large_min=10**9)),   # no dense groups: long rows per fingerprint
 ]
 
 
@@ -125,15 +128,15 @@ def test_dense_and_sparse_paths_agree():
     w = synth.scaled("c1", 50_000, occ_num=0)
     idx = torch.from_numpy(synth.generate(w, ld=400)).cuda()
     out = []
-    for lm in (0, 10, 100, 10**9):
-        s = _searcher(w.params(), large_min=lm)
+    for lm, vm in ((0, 0), (10, 0), (100, 0), (10**9, 0), (0, 1), (10**9, 1)):
+        s = _searcher(w.params(), large_min=lm, vote_map=vm)
         r = s.detect(idx)
         out.append((r.numpy(), s.stats()))
         r.free()
         s.close()
     for o, st in out[1:]:
         _assert_lists(o, out[0][0])
-    assert out[1][1]["n_groups"] > 0 and out[3][1]["n_groups"] == 0
+    assert out[1][1]["n_groups"] > 0 and out[3][1]["n_groups"] == 0 and out[5][1]["n_groups"] == 0
 
 
 def test_host_entry_point_matches_device():
