@@ -210,6 +210,87 @@ fast_status fast_get_stats(const fast_ctx *ctx, fast_stats *out);
  */
 fast_status fast_set_option(fast_ctx *ctx, const char *name, double value);
 
+/* ------------------------------------------------------------------ */
+/* Streaming search server                                             */
+/* ------------------------------------------------------------------ */
+/*
+ * A server keeps, per station, the hash tables of a preloaded history
+ * resident in HBM and answers requests -- batches of new windows of one
+ * station -- against the history and every earlier batch of that station
+ * (the tables stay populated while new fingerprints query them, §6.4
+ * "Partition"; each new fingerprint queries its buckets, §6.1 "Search").
+ *
+ * Semantics.  Window ids continue the station timeline: the history is
+ * 0..N0-1, each submitted batch takes the next n ids in submission order.
+ * Request q reports every pair (i, j) with j in its batch and i < j (i in the
+ * history, an earlier batch of the station, or its own batch), neither
+ * dropped, j - i > excl, votes >= v, sorted by (i, j).  History windows keep
+ * the drop flag of the history alone (occurrence filter on the N0 windows);
+ * a later window is dropped iff its key falls in a heavy history bucket
+ * (occ_den * size > occ_num * N0) in more than b/2 tables.  The result of a
+ * request depends only on the station's submission sequence, never on the
+ * timing or interleaving of other requests.
+ *
+ * Execution.  One worker thread and one CUDA stream per station: a station's
+ * requests run in submission order, different stations run concurrently on
+ * the device.  A request starts when an estimate of its working set fits the
+ * HBM budget next to the requests already running (continuous admission as
+ * memory frees up).  Thread safety: submit / poll / latency / release may be
+ * called from any host thread.
+ */
+typedef struct fast_server fast_server;
+
+/*
+ * Creates a server with n_stations stations (1..1024) on the current
+ * device.  max_stream_windows bounds the windows each station may receive
+ * after its history (the device delta tables are sized for it);
+ * hbm_budget_bytes bounds resident tables plus running requests (0 = none).
+ */
+fast_status fast_server_create(const fast_params *p, uint32_t n_stations, uint64_t max_stream_windows,
+                               uint64_t hbm_budget_bytes, fast_server **out);
+
+/* Stops the workers (queued requests fail with FAST_ETIMEOUT) and frees all. */
+void fast_server_destroy(fast_server *srv);
+
+const char *fast_server_last_error(const fast_server *srv);
+
+/*
+ * Loads a station's history (N rows of ld uint16 indices, host memory):
+ * signs it, builds and keeps its tables, applies the occurrence filter.
+ * Synchronous.  Must precede the station's first submit; at most once.
+ */
+fast_status fast_server_load_history(fast_server *srv, uint32_t station, const uint16_t *h_idx, uint64_t N,
+                                     uint32_t ld);
+
+/*
+ * Queues a batch of n >= 1 new windows (host memory, n rows of ld uint16)
+ * for `station` and returns its request id.  The input is copied before the
+ * call returns.
+ */
+fast_status fast_stream_submit(fast_server *srv, uint32_t station, const uint16_t *h_idx, uint32_t n, uint32_t ld,
+                               uint64_t *req_id);
+
+/*
+ * Waits up to timeout_us microseconds for a request.  FAST_EPENDING if it is
+ * not finished; the request's own error if it failed; FAST_OK with its
+ * detections otherwise: *M pairs as host arrays (valid until
+ * fast_stream_release) and *first_id, the id of the batch's first window.
+ */
+fast_status fast_stream_poll(fast_server *srv, uint64_t req_id, uint64_t timeout_us, uint64_t *M, uint64_t *first_id,
+                             const uint32_t **h_i, const uint32_t **h_j, const uint8_t **h_votes);
+
+/* Seconds from submit to completion of a finished request. */
+fast_status fast_stream_latency(fast_server *srv, uint64_t req_id, double *seconds);
+
+/* Forgets a finished request and frees its results. */
+fast_status fast_stream_release(fast_server *srv, uint64_t req_id);
+
+/*
+ * Test hook: the request with id req_id fails on the host (FAST_EINTERNAL)
+ * instead of running; every other request is unaffected.
+ */
+fast_status fast_server_inject_failure(fast_server *srv, uint64_t req_id);
+
 /*
  * One table's stable (key, id) sort without any device allocation.
  * No counterpart in the paper: this is a service entry point of this library.

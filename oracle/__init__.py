@@ -63,6 +63,7 @@ def _L():
         "orc_search_brute": (u64, [P, vp, vp, u64, pp(vp), pp(vp), pp(vp)]),
         "orc_search_row": (u64, [P, vp, vp, u64, u64, pp(vp), pp(vp)]),
         "orc_pair_votes": (u32, [P, vp, u64, u64, u64]),
+        "orc_stream_query": (u64, [P, vp, u64, u64, u64, vp, pp(vp), pp(vp), pp(vp)]),
         "orc_free": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -191,3 +192,13 @@ def run(params: dict, idx: np.ndarray, threads: int = 0, brute: bool = False):
     k = keys(params, idx, threads)
     d = drop(params, k, threads)
     return search(params, k, d, brute=brute)
+
+
+def stream_query(params: dict, keys_all: np.ndarray, n0: int, j0: int, hist_drop: np.ndarray | None):
+    """One streamed request by definition: pairs (i, j) with j in [j0, N)."""
+    keys_all = np.ascontiguousarray(keys_all, dtype=np.uint32)
+    N = keys_all.shape[1]
+    pi, pj, pv = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    n = _L().orc_stream_query(ctypes.byref(_p(params)), _ptr(keys_all), N, n0, j0, _ptr(hist_drop),
+                              ctypes.byref(pi), ctypes.byref(pj), ctypes.byref(pv))
+    return _take(n, pi, pj, pv)

@@ -428,3 +428,52 @@ uint64_t orc_search_row(const orc_params *p, const uint32_t *keys, const uint8_t
 }
 
 void orc_free(void *ptr) { free(ptr); }
+
+/* ------------------------------------------------------------------ */
+/* 7. streaming replay (serving reading of §6.4 "Partition")           */
+/* ------------------------------------------------------------------ */
+
+/*
+ * One streamed request, by definition.  keys [b][Ntot] holds the bucket keys
+ * of every window of a station so far, in id order: the N0 history windows,
+ * then all earlier requests' batches, then this request's batch [j0, Ntot).
+ * A history window keeps its drop flag from the history alone (hist_drop,
+ * orc_drop on the history keys).  Any later window w is dropped iff its key
+ * falls in a heavy history bucket -- occ_den * size > occ_num * N0, size
+ * counted over the N0 history windows -- in more than b/2 tables.
+ * Reported: pairs (i, j), j in the batch, i < j, neither dropped,
+ * j - i > E, votes >= v, sorted by (i, j).
+ */
+uint64_t orc_stream_query(const orc_params *p, const uint32_t *keys, uint64_t Ntot, uint64_t N0, uint64_t j0,
+                          const uint8_t *hist_drop, uint32_t **out_i, uint32_t **out_j, uint8_t **out_votes)
+{
+    uint8_t *drop = calloc(Ntot ? Ntot : 1, 1);
+    for (uint64_t w = 0; w < N0; w++) drop[w] = hist_drop ? hist_drop[w] : 0;
+    if (p->occ_num > 0 && Ntot > N0) {
+        uint32_t *cnt = calloc(Ntot - N0, sizeof(uint32_t));
+        uint32_t *hk = malloc(sizeof(uint32_t) * (N0 ? N0 : 1));
+        for (uint32_t t = 0; t < p->b; t++) {
+            const uint32_t *kt = keys + (uint64_t)t * Ntot;
+            for (uint64_t w = N0; w < Ntot; w++) {
+                uint64_t size = 0; /* history windows sharing the key */
+                for (uint64_t h = 0; h < N0; h++) size += kt[h] == kt[w];
+                if ((uint64_t)p->occ_den * size > (uint64_t)p->occ_num * N0) cnt[w - N0]++;
+            }
+        }
+        for (uint64_t w = N0; w < Ntot; w++) drop[w] = 2ULL * cnt[w - N0] > p->b;
+        free(cnt);
+        free(hk);
+    }
+    orc_list L = {0};
+    for (uint64_t i = 0; i < Ntot; i++)
+        for (uint64_t j = (i + 1 > j0 ? i + 1 : j0); j < Ntot; j++) {
+            if (!orc_pair_ok(p, drop, i, j)) continue;
+            uint32_t v = orc_pair_votes(p, keys, Ntot, i, j);
+            if (v >= p->v) orc_list_push(&L, (uint32_t)i, (uint32_t)j, v);
+        }
+    free(drop);
+    *out_i = L.i;
+    *out_j = L.j;
+    *out_votes = L.votes;
+    return L.n;
+}

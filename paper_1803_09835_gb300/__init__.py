@@ -16,12 +16,16 @@ import numpy as np
 
 from . import _lib
 from ._lib import (FAST_MINHASH, FAST_MINMAX, FastError, fast_build_tables, fast_create, fast_destroy, fast_detect,
-                   fast_detect_host, fast_get_stats, fast_result_free, fast_result_view, fast_search, fast_set_option,
-                   fast_sig, fast_tables_free, fast_tables_view)
+                   fast_detect_host, fast_get_stats, fast_result_free, fast_result_view, fast_search,
+                   fast_server_create, fast_server_destroy, fast_server_inject_failure, fast_server_load_history,
+                   fast_set_option, fast_sig, fast_stream_latency, fast_stream_poll, fast_stream_release,
+                   fast_stream_submit, fast_tables_free, fast_tables_view)
 
 __all__ = ["Searcher", "Result", "Tables", "FastError", "FAST_MINHASH", "FAST_MINMAX", "fast_create", "fast_destroy",
            "fast_sig", "fast_build_tables", "fast_tables_view", "fast_tables_free", "fast_search", "fast_detect",
-           "fast_detect_host", "fast_result_view", "fast_result_free", "fast_get_stats", "fast_set_option"]
+           "fast_detect_host", "fast_result_view", "fast_result_free", "fast_get_stats", "fast_set_option", "Server",
+           "fast_server_create", "fast_server_destroy", "fast_server_load_history", "fast_stream_submit",
+           "fast_stream_poll", "fast_stream_latency", "fast_stream_release", "fast_server_inject_failure"]
 
 
 class Result:
@@ -127,3 +131,49 @@ class Searcher:
 
     def stats(self) -> dict:
         return fast_get_stats(self.ctx)
+
+
+class Server:
+    """Streaming search: resident station histories, batches answered as they arrive."""
+
+    def __init__(self, params: dict, n_stations: int, max_stream_windows: int, hbm_budget_bytes: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise FastError(_lib.FAST_ECUDA, "no CUDA device: this library has no CPU fallback")
+        self.params = dict(params)
+        self.srv = fast_server_create(self.params, n_stations, max_stream_windows, hbm_budget_bytes)
+
+    def load_history(self, station: int, idx: np.ndarray):
+        fast_server_load_history(self.srv, station, np.ascontiguousarray(idx))
+
+    def submit(self, station: int, idx: np.ndarray) -> int:
+        return fast_stream_submit(self.srv, station, np.ascontiguousarray(idx))
+
+    def poll(self, req_id: int, timeout_s: float = 0.0):
+        return fast_stream_poll(self.srv, req_id, int(timeout_s * 1e6))
+
+    def wait(self, req_id: int, timeout_s: float = 600.0):
+        r = self.poll(req_id, timeout_s)
+        if r is None:
+            raise FastError(_lib.FAST_ETIMEOUT, f"request {req_id} still pending after {timeout_s} s")
+        return r
+
+    def latency(self, req_id: int) -> float:
+        return fast_stream_latency(self.srv, req_id)
+
+    def release(self, req_id: int):
+        fast_stream_release(self.srv, req_id)
+
+    def inject_failure(self, req_id: int):
+        fast_server_inject_failure(self.srv, req_id)
+
+    def close(self):
+        if getattr(self, "srv", None):
+            fast_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

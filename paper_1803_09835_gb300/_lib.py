@@ -75,6 +75,15 @@ def load():
         "fast_get_stats": (st, [vp, pp(fast_stats)]),
         "fast_set_option": (st, [vp, ctypes.c_char_p, ctypes.c_double]),
         "fast_table_sort_static": (st, [vp, u64, vp, vp, vp]),
+        "fast_server_create": (st, [pp(fast_params), u32, u64, u64, pp(vp)]),
+        "fast_server_destroy": (None, [vp]),
+        "fast_server_last_error": (ctypes.c_char_p, [vp]),
+        "fast_server_load_history": (st, [vp, u32, vp, u64, u32]),
+        "fast_stream_submit": (st, [vp, u32, vp, u32, u32, pp(u64)]),
+        "fast_stream_poll": (st, [vp, u64, u64, pp(u64), pp(u64), pp(vp), pp(vp), pp(vp)]),
+        "fast_stream_latency": (st, [vp, u64, pp(ctypes.c_double)]),
+        "fast_stream_release": (st, [vp, u64]),
+        "fast_server_inject_failure": (st, [vp, u64]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -236,3 +245,72 @@ def fast_last_error(ctx) -> str:
 def fast_table_sort_static(d_keys, n: int, d_skey, d_sid, stream=None):
     """Sorts one table's keys with the library's fixed scratch (no allocation)."""
     _check(None, load().fast_table_sort_static(_dptr(d_keys), n, _dptr(d_skey), _dptr(d_sid), _stream(stream)))
+
+
+# ------------------------------------------------------------- serving
+
+def _scheck(srv, status: int):
+    if status != FAST_OK:
+        raise FastError(status, load().fast_server_last_error(srv).decode() if srv else "")
+
+
+def fast_server_create(params: dict, n_stations: int, max_stream_windows: int, hbm_budget_bytes: int = 0):
+    out = ctypes.c_void_p()
+    _scheck(None, load().fast_server_create(ctypes.byref(params_struct(params)), n_stations, max_stream_windows,
+                                            hbm_budget_bytes, ctypes.byref(out)))
+    return out
+
+
+def fast_server_destroy(srv):
+    load().fast_server_destroy(srv)
+
+
+def fast_server_last_error(srv) -> str:
+    return load().fast_server_last_error(srv).decode()
+
+
+def fast_server_load_history(srv, station: int, h_idx):
+    N, ld = h_idx.shape
+    _scheck(srv, load().fast_server_load_history(srv, station, _hptr(h_idx), N, ld))
+
+
+def fast_stream_submit(srv, station: int, h_idx) -> int:
+    n, ld = h_idx.shape
+    rid = ctypes.c_uint64()
+    _scheck(srv, load().fast_stream_submit(srv, station, _hptr(h_idx), n, ld, ctypes.byref(rid)))
+    return rid.value
+
+
+def fast_stream_poll(srv, req_id: int, timeout_us: int = 0):
+    """None while pending; else (first_id, i, j, votes) as numpy copies."""
+    import numpy as np
+    M, first = ctypes.c_uint64(), ctypes.c_uint64()
+    pi, pj, pv = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    st = load().fast_stream_poll(srv, req_id, timeout_us, ctypes.byref(M), ctypes.byref(first), ctypes.byref(pi),
+                                 ctypes.byref(pj), ctypes.byref(pv))
+    if st == FAST_EPENDING:
+        return None
+    _scheck(srv, st)
+    m = M.value
+
+    def arr(p, ct, dt):
+        if not m:
+            return np.empty(0, dt)
+        return np.ctypeslib.as_array(ctypes.cast(p, ctypes.POINTER(ct)), (m,)).copy()
+
+    return first.value, arr(pi, ctypes.c_uint32, np.uint32), arr(pj, ctypes.c_uint32, np.uint32), \
+        arr(pv, ctypes.c_uint8, np.uint8)
+
+
+def fast_stream_latency(srv, req_id: int) -> float:
+    sec = ctypes.c_double()
+    _scheck(srv, load().fast_stream_latency(srv, req_id, ctypes.byref(sec)))
+    return sec.value
+
+
+def fast_stream_release(srv, req_id: int):
+    _scheck(srv, load().fast_stream_release(srv, req_id))
+
+
+def fast_server_inject_failure(srv, req_id: int):
+    _scheck(srv, load().fast_server_inject_failure(srv, req_id))

@@ -64,7 +64,7 @@ fast_status sync_check(fast_ctx *c, cudaStream_t s, const char *where) {
     return set_error(c, FAST_EINTERNAL, w + ": device error flag " + std::to_string(flags));
 }
 
-static uint32_t g_marked = 0;  // slots recorded in the current call (per process; calls are not reentrant per ctx)
+static thread_local uint32_t g_marked = 0;  // stage slots recorded by the current call on this thread
 
 void stage_mark(fast_ctx *c, int slot, cudaStream_t s) {
     if (!c->timing) return;

@@ -88,33 +88,6 @@ __global__ void k_drop(const uint32_t *__restrict__ heavy, uint64_t N, uint32_t 
 
 // ---------------------------------------------------------- vote map
 
-struct Map {
-    unsigned long long *slot;
-    uint64_t cap;
-};
-
-__device__ __forceinline__ uint64_t pair_key(uint32_t i, uint32_t j) { return ((uint64_t)i << 28) | j; }
-
-// Adds one vote to (i, j).  Slot = key56 << 8 | votes; 0 = empty.
-__device__ __forceinline__ void map_add(Map m, uint64_t key56, uint32_t *err) {
-    const unsigned long long want = (unsigned long long)(key56 << 8);
-    uint64_t h = __umul64hi(mix64(key56), m.cap);
-    for (uint32_t probe = 0; probe < 1u << 16; probe++) {
-        unsigned long long cur = __ldcg(m.slot + h);
-        if (cur == 0) {
-            unsigned long long old = atomicCAS(m.slot + h, 0ull, want | 1ull);
-            if (old == 0) return;
-            cur = old;
-        }
-        if ((cur & ~0xFFull) == want) {
-            atomicAdd(m.slot + h, 1ull);
-            return;
-        }
-        if (++h == m.cap) h = 0;
-    }
-    set_err(err, ERR_MAP_FULL);
-}
-
 // --------------------------------------------------- bucket enumeration
 
 struct EnumArgs {

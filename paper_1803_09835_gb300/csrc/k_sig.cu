@@ -30,7 +30,7 @@ namespace fastgb {
 
 namespace {
 
-constexpr int kSigThreads = 256;
+constexpr int kSigThreads = 512;
 constexpr int kTile = 32;
 
 // Rank tables: walk[w][k], w = f (MinHash) or 2f / 2f+1 (Min-Max min / max),
@@ -145,8 +145,10 @@ __global__ void __launch_bounds__(kSigThreads, 2)
             bb = __ldg(hb + f);
             seq = reinterpret_cast<const uint4 *>(walk + (size_t)w * Dpad);
         }
+        uint4 nxt = w < W ? __ldg(seq) : make_uint4(0, 0, 0, 0);
         while (w < W) {
-            uint4 v = __ldg(seq + k8);
+            const uint4 v = nxt;
+            if (k8 + 1 < nk8) nxt = __ldg(seq + k8 + 1);  // next 8 steps in flight while these run
 #pragma unroll
             for (int s = 0; s < 8; s++) {
                 uint32_t x = u16_of(v, s);
@@ -174,6 +176,7 @@ __global__ void __launch_bounds__(kSigThreads, 2)
                     a_hi = (uint32_t)(a >> 32);
                     bb = __ldg(hb + f);
                     seq = reinterpret_cast<const uint4 *>(walk + (size_t)w * Dpad);
+                    nxt = __ldg(seq);
                 }
             }
         }
