@@ -289,6 +289,93 @@ def gpu_arm(args, rank, world, local_rank):
     return 0
 
 
+# ------------------------------------------------------------------ serving leg
+
+def serving_arm(args):
+    """Streaming workload: resident station histories, Poisson arrivals of
+    batches (open loop), p50/p99 latency submit -> result, windows/s; the
+    plain search (tables rebuilt for history + batch) per request beside it."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1803_09835_gb300 import Searcher, Server
+
+    torch.cuda.set_device(0)
+    n_st = args.stations
+    n_req = int(args.rate * args.duration)
+    t_arr, st_of, size = synth.requests(n_req, args.rate, n_stations=n_st)
+    per_st = [int(size[st_of == s].sum()) for s in range(n_st)]
+    base = synth.workload("c3") if not args.n else synth.scaled("c3", args.n)
+    N0 = base.N
+    ld = ((base.K + 7) // 8) * 8
+    srv = Server(base.params(), n_st, max_stream_windows=max(per_st) + 1, hbm_budget_bytes=args.budget_gb << 30)
+    idx = []
+    t0 = time.perf_counter()
+    from dataclasses import replace
+    for s in range(n_st):
+        # the station's 3-month history followed by the windows its requests carry
+        ws = synth.scaled("c3", args.n, station=s) if args.n else synth.workload("c3", station=s)
+        w = replace(ws, N=N0 + per_st[s])
+        a = synth.generate(w, ld=ld)
+        srv.load_history(s, a[:N0])
+        idx.append(a)
+    load_s = time.perf_counter() - t0
+    # open-loop replay
+    cursor = [N0] * n_st
+    ids = []
+    start = time.perf_counter()
+    for q in range(n_req):
+        now = time.perf_counter() - start
+        if t_arr[q] > now:
+            time.sleep(t_arr[q] - now)
+        s = int(st_of[q])
+        sl = idx[s][cursor[s]:cursor[s] + int(size[q])]
+        ids.append(srv.submit(s, sl))
+        cursor[s] += int(size[q])
+    results = [srv.wait(r) for r in ids]
+    end = time.perf_counter()
+    lat = np.array([srv.latency(r) for r in ids]) * 1000
+    windows = int(size.sum())
+    # plain search per request: tables rebuilt over history + every earlier batch + the batch
+    plain_ms, plain_win, plain_ok = [], [], True
+    pl = Searcher(base.params())
+    cur0 = N0
+    for q in [q for q in range(n_req) if st_of[q] == 0][:args.plain_requests]:
+        n = int(size[q])
+        hist = torch.from_numpy(idx[0][:cur0 + n]).cuda()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        r = pl.detect(hist)
+        gi, gj, gv = r.numpy()
+        torch.cuda.synchronize()
+        plain_ms.append(1000 * (time.perf_counter() - t1))
+        plain_win.append(n)
+        r.free()
+        keep = gj >= cur0
+        first, si, sj, sv = results[q]
+        plain_ok &= first == cur0 and np.array_equal(gi[keep], si) and np.array_equal(gj[keep], sj) \
+            and np.array_equal(gv[keep], sv)
+        cur0 += n
+        del hist
+    pl.close()
+    srv.close()
+    line = {"metric": "stream p50/p99 ms vs plain", "value": windows / (end - start), "unit": "windows/s",
+            "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "u32",
+            "config": {"workload": f"c3: {n_st} stations x {N0:,} history windows resident, Poisson {args.rate:g} req/s "
+                                   f"open loop for {args.duration:g} s, batches log-U[60,3600] windows",
+                       "requests": n_req, "windows": windows, "budget_gb": args.budget_gb,
+                       "history_load_s": load_s},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "plain": {"requests": len(plain_ms), "p50_ms": float(np.median(plain_ms)) if plain_ms else None,
+                      "windows_per_s": float(sum(plain_win) / (sum(plain_ms) / 1000)) if plain_ms else None,
+                      "same_as_stream": bool(plain_ok)},
+            "detections": int(sum(len(r[1]) for r in results))}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -301,7 +388,15 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=300_000)
     ap.add_argument("--ref-sample", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", action="store_true", help="streaming workload (c3) instead of the batch search")
+    ap.add_argument("--stations", type=int, default=12)
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--duration", type=float, default=5.0)
+    ap.add_argument("--budget-gb", type=int, default=150)
+    ap.add_argument("--plain-requests", type=int, default=3)
     args = ap.parse_args()
+    if args.serving:
+        return serving_arm(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

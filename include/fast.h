@@ -285,6 +285,9 @@ fast_status fast_stream_latency(fast_server *srv, uint64_t req_id, double *secon
 /* Forgets a finished request and frees its results. */
 fast_status fast_stream_release(fast_server *srv, uint64_t req_id);
 
+/* fast_set_option on every station's context; before any history is loaded. */
+fast_status fast_server_set_option(fast_server *srv, const char *name, double value);
+
 /*
  * Test hook: the request with id req_id fails on the host (FAST_EINTERNAL)
  * instead of running; every other request is unaffected.

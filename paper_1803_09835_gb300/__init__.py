@@ -136,12 +136,15 @@ class Searcher:
 class Server:
     """Streaming search: resident station histories, batches answered as they arrive."""
 
-    def __init__(self, params: dict, n_stations: int, max_stream_windows: int, hbm_budget_bytes: int = 0):
+    def __init__(self, params: dict, n_stations: int, max_stream_windows: int, hbm_budget_bytes: int = 0,
+                 **options):
         import torch
         if not torch.cuda.is_available():
             raise FastError(_lib.FAST_ECUDA, "no CUDA device: this library has no CPU fallback")
         self.params = dict(params)
         self.srv = fast_server_create(self.params, n_stations, max_stream_windows, hbm_budget_bytes)
+        for k, v in options.items():
+            _lib.fast_server_set_option(self.srv, k, v)
 
     def load_history(self, station: int, idx: np.ndarray):
         fast_server_load_history(self.srv, station, np.ascontiguousarray(idx))

@@ -84,6 +84,7 @@ def load():
         "fast_stream_latency": (st, [vp, u64, pp(ctypes.c_double)]),
         "fast_stream_release": (st, [vp, u64]),
         "fast_server_inject_failure": (st, [vp, u64]),
+        "fast_server_set_option": (st, [vp, ctypes.c_char_p, ctypes.c_double]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -314,3 +315,7 @@ def fast_stream_release(srv, req_id: int):
 
 def fast_server_inject_failure(srv, req_id: int):
     _scheck(srv, load().fast_server_inject_failure(srv, req_id))
+
+
+def fast_server_set_option(srv, name: str, value: float):
+    _scheck(srv, load().fast_server_set_option(srv, name.encode(), float(value)))

@@ -79,6 +79,26 @@ __device__ __forceinline__ void map_add(Map m, uint64_t key56, uint32_t *err) {
     set_err(err, ERR_MAP_FULL);
 }
 
+// Adds `n` votes to (i, j) (n <= 255 - current votes, always true: votes <= b).
+__device__ __forceinline__ void map_add_n(Map m, uint64_t key56, uint32_t n, uint32_t *err) {
+    const unsigned long long want = (unsigned long long)(key56 << 8);
+    uint64_t h = __umul64hi(mix64(key56), m.cap);
+    for (uint32_t probe = 0; probe < 1u << 16; probe++) {
+        unsigned long long cur = __ldcg(m.slot + h);
+        if (cur == 0) {
+            unsigned long long old = atomicCAS(m.slot + h, 0ull, want | n);
+            if (old == 0) return;
+            cur = old;
+        }
+        if ((cur & ~0xFFull) == want) {
+            atomicAdd(m.slot + h, (unsigned long long)n);
+            return;
+        }
+        if (++h == m.cap) h = 0;
+    }
+    set_err(err, ERR_MAP_FULL);
+}
+
 
 // ------------------------------------------------------------------- host
 
@@ -197,6 +217,24 @@ fast_status scan_excl(fast_ctx *c, const uint32_t *in, uint64_t *out, uint64_t n
 fast_status filter_launch(fast_ctx *c, fast_tables *tb, cudaStream_t s);
 fast_status search_run(fast_ctx *c, const fast_tables *tb, const uint32_t *d_sig, fast_result **out,
                        cudaStream_t s);
+
+// Dense groups of a station's history, kept resident by the streaming server:
+// components of large buckets (live size >= large_min), their members, the
+// members' keys, and every table's large buckets with their group.
+struct HistGroups {
+    uint32_t large_min = 0;
+    uint64_t nm = 0, ng = 0, nlarge = 0;
+    uint32_t *label = nullptr;   // [N0] group index of each window, ~0 outside groups
+    uint32_t *ids = nullptr;     // [nm] members, sorted by (group, id)
+    uint32_t *GT = nullptr;      // [b][nm] members' keys
+    uint32_t *gstart = nullptr;  // [ng + 1] member offsets of each group
+    uint4 *large = nullptr;      // [nlarge] (table, start, end, group), sorted by (table, start)
+    uint32_t *tstart = nullptr;  // [b + 1] first large bucket of each table in `large`
+    uint32_t *bm = nullptr;      // membership bitmaps: bit m of large bucket x = member m of its group
+    uint64_t *bm_off = nullptr;  // [nlarge] first word of each large bucket's bitmap
+};
+fast_status history_groups(fast_ctx *c, const fast_tables *tb, const uint32_t *d_sig, HistGroups *g, cudaStream_t s);
+void history_groups_free(HistGroups *g);
 
 // timing helpers (fast_api.cu)
 void stage_mark(fast_ctx *c, int slot, cudaStream_t s);

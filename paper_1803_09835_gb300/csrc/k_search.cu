@@ -1702,6 +1702,198 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
     return FAST_OK;
 }
 
+// Bit m of large bucket x's bitmap: member m of the bucket's group (members
+// of a group sorted by id) belongs to the bucket.
+__global__ void k_bucket_bitmaps(const uint4 *__restrict__ large, uint64_t nlarge, const uint32_t *__restrict__ sid,
+                                 const uint8_t *__restrict__ drop, uint64_t N, const uint32_t *__restrict__ gstart,
+                                 const uint32_t *__restrict__ ids, uint32_t *__restrict__ bm,
+                                 const uint64_t *__restrict__ bm_off) {
+    for (uint64_t x = blockIdx.x; x < nlarge; x += gridDim.x) {
+        const uint4 e = large[x];
+        const uint32_t *s = sid + (uint64_t)e.x * N;
+        const uint32_t *gi = ids + gstart[e.w];
+        const uint32_t gn = gstart[e.w + 1] - gstart[e.w];
+        for (uint32_t q = e.y + threadIdx.x; q < e.z; q += blockDim.x) {
+            const uint32_t id = s[q];
+            if (drop[id]) continue;
+            uint32_t lo = 0, hi = gn;  // position of id among the group's sorted members
+            while (lo < hi) {
+                const uint32_t m = (lo + hi) / 2;
+                if (gi[m] < id) lo = m + 1;
+                else hi = m;
+            }
+            if (lo < gn && gi[lo] == id) atomicOr(bm + bm_off[x] + lo / 32, 1u << (lo % 32));
+        }
+    }
+}
+
+void history_groups_free(HistGroups *g) {
+    cudaFree(g->label);
+    cudaFree(g->ids);
+    cudaFree(g->GT);
+    cudaFree(g->gstart);
+    cudaFree(g->large);
+    cudaFree(g->tstart);
+    cudaFree(g->bm);
+    cudaFree(g->bm_off);
+    *g = HistGroups{};
+}
+
+fast_status history_groups(fast_ctx *c, const fast_tables *tb, const uint32_t *d_sig, HistGroups *g, cudaStream_t s) {
+    const fast_params &p = c->p;
+    const uint64_t N = tb->N;
+    const uint32_t nb = p.b;
+    unsigned long long *scal = reinterpret_cast<unsigned long long *>(c->d_scal);
+    fast_status st;
+    *g = HistGroups{};
+    uint32_t large_min = c->large_min;
+    if (!large_min) {
+        double ptop = std::pow((double)p.K / p.D, (double)p.r);
+        large_min = (uint32_t)std::max(512.0, std::min(1e9, 8.0 * N * ptop));
+    }
+    g->large_min = large_min;
+    auto dev = [&](auto **ptr, size_t count) -> fast_status {
+        cudaError_t e = cudaMalloc(ptr, std::max<size_t>(count, 1) * sizeof(**ptr));
+        return e ? cuda_fail(c, e, "history groups") : FAST_OK;
+    };
+    if ((st = dev(&g->label, N)) || (st = dev(&g->tstart, nb + 1))) return st;
+    cudaMemsetAsync(g->label, 0xFF, N * 4, s);
+    if (N == 0) {
+        cudaMemsetAsync(g->tstart, 0, (nb + 1) * 4, s);
+        return sync_check(c, s, "history groups");
+    }
+    const uint64_t big_cap = (uint64_t)nb * (N / (kSmall + 1) + 1);
+    uint4 *big = nullptr, *large = nullptr, *medium = nullptr;
+    if ((st = dalloc_t(c, &big, big_cap, s))) return st;
+    cudaMemsetAsync(scal, 0, sizeof(uint64_t) * kScal, s);
+    EnumArgs ea{tb->d_skey, tb->d_sid, tb->d_drop, nullptr, N, p.excl, 0, (uint32_t)N, 1};
+    const dim3 eg(std::max(1u, std::min<unsigned>(ceil_div(N, 256), 2048)), nb);
+    k_find_big<<<eg, 256, 0, s>>>(ea, big, scal + Scal::NBIG, big_cap, scal + Scal::SMALLPAIRS, c->d_err),
+        FAST_LAUNCHED(c);
+    if ((st = read_scal(c, s, "history buckets"))) {
+        dfree(c, big, big_cap * 16, s);
+        return st;
+    }
+    const uint64_t nbig = c->h_scal[Scal::NBIG];
+    if ((st = dalloc_t(c, &large, nbig ? nbig : 1, s)) || (st = dalloc_t(c, &medium, nbig ? nbig : 1, s))) {
+        dfree(c, big, big_cap * 16, s);
+        return st;
+    }
+    k_big_classify<<<std::max<uint64_t>(1, std::min<uint64_t>(nbig, c->num_sms * 8)), 256, 0, s>>>(
+        ea, big, scal + Scal::NBIG, big_cap, large_min, large, scal + Scal::NLARGE, medium, scal + Scal::NMEDIUM,
+        scal + Scal::PART0), FAST_LAUNCHED(c);
+    st = read_scal(c, s, "history classify");
+    const uint64_t nlarge = c->h_scal[Scal::NLARGE];
+    std::vector<uint4> hl(nlarge);
+    if (!st && nlarge) {
+        const unsigned lg = (unsigned)std::min<uint64_t>(nlarge, c->num_sms * 8);
+        k_label_init<<<lg, 256, 0, s>>>(large, nlarge, tb->d_sid, tb->d_drop, N, g->label), FAST_LAUNCHED(c);
+        int it = 0;
+        for (; it < 256 && !st; it++) {
+            cudaMemsetAsync(scal + Scal::CHANGED, 0, 8, s);
+            k_label_prop<<<lg, 256, 0, s>>>(large, nlarge, tb->d_sid, tb->d_drop, N, g->label,
+                                            reinterpret_cast<uint32_t *>(scal + Scal::CHANGED)), FAST_LAUNCHED(c);
+            st = read_scal(c, s, "history labels");
+            if (!st && !c->h_scal[Scal::CHANGED]) break;
+        }
+        if (!st && it == 256) st = set_error(c, FAST_EINTERNAL, "group labels did not converge");
+        cudaMemcpyAsync(hl.data(), large, nlarge * sizeof(uint4), cudaMemcpyDeviceToHost, s);
+    }
+    dfree(c, big, big_cap * 16, s);
+    dfree(c, large, (nbig ? nbig : 1) * 16, s);
+    dfree(c, medium, (nbig ? nbig : 1) * 16, s);
+    if (st) return st;
+    // members sorted by (label, id)
+    unsigned long long *memb = nullptr, *memb2 = nullptr;
+    if ((st = dalloc_t(c, &memb, N, s))) return st;
+    cudaMemsetAsync(scal + Scal::NMEMB, 0, 8, s);
+    k_collect_members<<<std::max(1u, std::min<unsigned>(ceil_div(N, 256), c->num_sms * 8)), 256, 0, s>>>(
+        g->label, N, memb, scal + Scal::NMEMB), FAST_LAUNCHED(c);
+    if ((st = read_scal(c, s, "history members"))) {
+        dfree(c, memb, N * 8, s);
+        return st;
+    }
+    const uint64_t nm = c->h_scal[Scal::NMEMB];
+    g->nm = nm;
+    std::vector<uint64_t> hm(nm);
+    if (nm) {
+        if ((st = dalloc_t(c, &memb2, nm, s))) {
+            dfree(c, memb, N * 8, s);
+            return st;
+        }
+        uint64_t *sorted = nullptr;
+        st = sort_u64(c, nm, reinterpret_cast<uint64_t *>(memb), reinterpret_cast<uint64_t *>(memb2), 0,
+                      32 + bits_for(N), &sorted, s);
+        if (!st) st = dev(&g->GT, (size_t)nm * nb);
+        if (!st) st = dev(&g->ids, nm);
+        if (!st) {
+            cudaMemcpyAsync(hm.data(), sorted, nm * 8, cudaMemcpyDeviceToHost, s);
+            k_gather_keys<<<std::max(1u, std::min<unsigned>(ceil_div(nm, 128), c->num_sms * 8)), 128, 0, s>>>(
+                reinterpret_cast<unsigned long long *>(sorted), nm, d_sig, N, nb, g->GT, g->ids), FAST_LAUNCHED(c);
+            st = sync_check(c, s, "history member keys");
+        }
+        dfree(c, memb2, nm * 8, s);
+    }
+    dfree(c, memb, N * 8, s);
+    if (st) return st;
+    // group table and the large buckets of every table with their group index
+    std::vector<uint32_t> gstart, glabel;
+    for (uint64_t a = 0; a < nm; a++)
+        if (a == 0 || (hm[a] >> 32) != (hm[a - 1] >> 32)) {
+            gstart.push_back((uint32_t)a);
+            glabel.push_back((uint32_t)(hm[a] >> 32));
+        }
+    g->ng = gstart.size();
+    gstart.push_back((uint32_t)nm);
+    std::vector<uint32_t> hlabel(N);
+    if (nlarge) cudaMemcpy(hlabel.data(), g->label, N * 4, cudaMemcpyDeviceToHost);
+    std::vector<uint32_t> hsid;
+    std::vector<uint4> lg;
+    for (const uint4 &e : hl) {
+        // the group of a large bucket: label of any live member (all share it)
+        uint32_t lab = kNone;
+        std::vector<uint32_t> ids_probe(std::min<uint32_t>(e.z - e.y, 64));
+        cudaMemcpy(ids_probe.data(), tb->d_sid + (uint64_t)e.x * N + e.y, ids_probe.size() * 4, cudaMemcpyDeviceToHost);
+        for (uint32_t id : ids_probe)
+            if (hlabel[id] != kNone) {
+                lab = hlabel[id];
+                break;
+            }
+        if (lab == kNone) continue;
+        const uint32_t gi = (uint32_t)(std::lower_bound(glabel.begin(), glabel.end(), lab) - glabel.begin());
+        lg.push_back(make_uint4(e.x, e.y, e.z, gi));
+    }
+    std::sort(lg.begin(), lg.end(), [](const uint4 &a, const uint4 &b) { return a.x != b.x ? a.x < b.x : a.y < b.y; });
+    // the resident per-window array holds the group index (not the label)
+    if (nlarge) {
+        for (uint64_t x = 0; x < N; x++)
+            if (hlabel[x] != kNone)
+                hlabel[x] = (uint32_t)(std::lower_bound(glabel.begin(), glabel.end(), hlabel[x]) - glabel.begin());
+        cudaMemcpy(g->label, hlabel.data(), N * 4, cudaMemcpyHostToDevice);
+    }
+    std::vector<uint32_t> ts(nb + 1, 0);
+    for (const uint4 &e : lg) ts[e.x + 1]++;
+    for (uint32_t t = 0; t < nb; t++) ts[t + 1] += ts[t];
+    g->nlarge = lg.size();
+    std::vector<uint64_t> boff(lg.size() + 1, 0);
+    for (size_t x = 0; x < lg.size(); x++) {
+        const uint32_t gs = gstart[lg[x].w + 1] - gstart[lg[x].w];
+        boff[x + 1] = boff[x] + (gs + 31) / 32;
+    }
+    if ((st = dev(&g->gstart, gstart.size())) || (st = dev(&g->large, lg.size())) ||
+        (st = dev(&g->bm_off, lg.size() + 1)) || (st = dev(&g->bm, boff.back())))
+        return st;
+    cudaMemcpy(g->gstart, gstart.data(), gstart.size() * 4, cudaMemcpyHostToDevice);
+    if (!lg.empty()) cudaMemcpy(g->large, lg.data(), lg.size() * sizeof(uint4), cudaMemcpyHostToDevice);
+    cudaMemcpy(g->tstart, ts.data(), ts.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(g->bm_off, boff.data(), boff.size() * 8, cudaMemcpyHostToDevice);
+    cudaMemsetAsync(g->bm, 0, std::max<uint64_t>(boff.back(), 1) * 4, s);
+    if (!lg.empty())
+        k_bucket_bitmaps<<<(unsigned)std::min<uint64_t>(lg.size(), c->num_sms * 8), 256, 0, s>>>(
+            g->large, lg.size(), tb->d_sid, tb->d_drop, N, g->gstart, g->ids, g->bm, g->bm_off), FAST_LAUNCHED(c);
+    return sync_check(c, s, "history groups");
+}
+
 fast_status search_run(fast_ctx *c, const fast_tables *tb, const uint32_t *d_sig, fast_result **out,
                        cudaStream_t s) {
     if (tb->N == 0) {  // nothing to launch

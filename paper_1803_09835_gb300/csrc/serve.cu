@@ -88,16 +88,105 @@ struct ReqArgs {
     uint32_t n, nb, excl;
     uint64_t first_id;
     uint32_t occ_num, occ_den;
+    // dense groups of the history
+    const uint32_t *label;   // [N0] group index of each history window (~0 = none)
+    const uint4 *large;      // large buckets (table, start, end, group), by (table, start)
+    const uint32_t *tstart;  // [b + 1]
+    uint32_t *wg;            // [n][kWG] groups a window meets in large buckets (~0 = free)
 };
 
+constexpr uint32_t kWG = 4;            // groups tracked per new window
+constexpr uint32_t kLargeFlag = 0x80000000u;
+
+// History bucket of every (table, window); heavy-bucket counts for the frozen
+// filter; a bucket listed as large is flagged and its group recorded for the
+// window (when the window already tracks kWG other groups the bucket stays
+// in the sparse path -- any split is exact as long as a group is wholly
+// dense or wholly sparse for the window).
 __global__ void k_req_lookup(ReqArgs a, uint2 *__restrict__ range, uint32_t *__restrict__ hcnt) {
     const uint32_t t = blockIdx.y;
     for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < a.n; w += gridDim.x * blockDim.x) {
         uint64_t lo, hi;
         equal_range(a.hkey + (uint64_t)t * a.N0, a.N0, a.keys[(uint64_t)t * a.n + w], &lo, &hi);
-        range[(uint64_t)t * a.n + w] = make_uint2((uint32_t)lo, (uint32_t)hi);
+        uint32_t flag = 0, x_large = 0;
+        if (hi > lo) {
+            uint32_t x0 = a.tstart[t], x1 = a.tstart[t + 1];  // large buckets of table t, by start
+            while (x0 < x1) {
+                const uint32_t m = (x0 + x1) / 2;
+                if (a.large[m].y < lo) x0 = m + 1;
+                else x1 = m;
+            }
+            if (x0 < a.tstart[t + 1] && a.large[x0].y == lo) {
+                const uint32_t g = a.large[x0].w;
+                uint32_t *slot = a.wg + (uint64_t)w * kWG;
+                for (uint32_t k = 0; k < kWG; k++) {
+                    const uint32_t old = atomicCAS(slot + k, kNoneId, g);
+                    if (old == kNoneId || old == g) {
+                        flag = kLargeFlag;
+                        x_large = x0;
+                        break;
+                    }
+                }
+            }
+        }
+        // a flagged range carries the large bucket's index instead of its start
+        range[(uint64_t)t * a.n + w] = make_uint2(flag ? x_large : (uint32_t)lo, (uint32_t)hi | flag);
         if (a.occ_num && (uint64_t)a.occ_den * (hi - lo) > (uint64_t)a.occ_num * a.N0) atomicAdd(hcnt + w, 1u);
     }
+}
+
+// Dense part of a request: for each group window w meets in large history
+// buckets, the votes of every member i from those buckets are the number of
+// the buckets' membership bitmaps holding i; they enter the request's vote map
+// as one addition per member.  One CTA per window.
+template <int MODE>
+__global__ void k_req_dense(ReqArgs a, const uint32_t *__restrict__ gstart, const uint32_t *__restrict__ ids,
+                            const uint32_t *__restrict__ bm, const uint64_t *__restrict__ bm_off,
+                            unsigned long long *__restrict__ total, unsigned long long *__restrict__ map,
+                            uint64_t map_cap, uint32_t *err) {
+    extern __shared__ uint32_t s_bk[];  // [nb] large-bucket index per table of this window's group, ~0 = none
+    const uint32_t w = blockIdx.x;
+    if (w >= a.n || a.ndrop[w]) return;  // block-uniform
+    const uint64_t j = a.first_id + w;
+    unsigned long long mine = 0;
+    for (uint32_t k = 0; k < kWG; k++) {
+        const uint32_t g = a.wg[(uint64_t)w * kWG + k];
+        if (g == kNoneId) break;  // slots fill in order
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < a.nb; t += blockDim.x) {
+            const uint2 rg = a.range[(uint64_t)t * a.n + w];
+            s_bk[t] = ((rg.y & kLargeFlag) && a.large[rg.x].w == g) ? rg.x : kNoneId;
+        }
+        __syncthreads();
+        const uint32_t g0 = gstart[g], gn = gstart[g + 1] - g0;
+        if (MODE == 0) {
+            if (threadIdx.x == 0) mine += gn;
+            continue;
+        }
+        for (uint32_t x = threadIdx.x; x < (gn + 31) / 32; x += blockDim.x) {
+            uint32_t cnt[32];
+#pragma unroll
+            for (int q = 0; q < 32; q++) cnt[q] = 0;
+            for (uint32_t t = 0; t < a.nb; t++) {
+                const uint32_t bx = s_bk[t];
+                if (bx == kNoneId) continue;
+                const uint32_t word = bm[bm_off[bx] + x];
+#pragma unroll
+                for (int q = 0; q < 32; q++) cnt[q] += (word >> q) & 1u;
+            }
+#pragma unroll
+            for (int q = 0; q < 32; q++) {
+                if (!cnt[q]) continue;
+                const uint32_t m = x * 32 + q;
+                const uint32_t i = ids[g0 + m];
+                if (j - i > a.excl) {
+                    Map mp{map, map_cap};
+                    map_add_n(mp, pair_key(i, (uint32_t)j), cnt[q], err);
+                }
+            }
+        }
+    }
+    if (MODE == 0 && threadIdx.x == 0 && mine) atomicAdd(total, mine);
 }
 
 __global__ void k_req_drop(const uint32_t *__restrict__ hcnt, uint32_t n, uint32_t nb, uint8_t *__restrict__ ndrop) {
@@ -126,15 +215,17 @@ __global__ void k_req_pairs(ReqArgs a, unsigned long long *__restrict__ total, u
         const uint32_t key = a.keys[tw];
         const uint2 rg = a.range[tw];
         const uint32_t *hid = a.hid + (uint64_t)t * a.N0;
-        // history members: i < N0 <= j
-        if (MODE == 0) {
-            mine += rg.y - rg.x;
-        } else {
-            for (uint32_t q = rg.x; q < rg.y; q++) {
-                const uint32_t i = hid[q];
-                if (!a.hdrop[i] && j - i > a.excl) {
-                    Map m{map, map_cap};
-                    map_add(m, pair_key(i, (uint32_t)j), err);
+        // history members (i < N0 <= j); large buckets come from the bitmaps
+        if (!(rg.y & kLargeFlag)) {
+            if (MODE == 0) {
+                mine += rg.y - rg.x;
+            } else {
+                for (uint32_t q = rg.x; q < rg.y; q++) {
+                    const uint32_t i = hid[q];
+                    if (!a.hdrop[i] && j - i > a.excl) {
+                        Map m{map, map_cap};
+                        map_add(m, pair_key(i, (uint32_t)j), err);
+                    }
                 }
             }
         }
@@ -264,6 +355,7 @@ struct fast_station {
     fast_ctx *ctx = nullptr;
     cudaStream_t stream = nullptr;
     fast_tables *hist = nullptr;
+    HistGroups hg;
     uint64_t N0 = 0;
     bool loaded = false;
     uint64_t next_id = 0;    // id of the next admitted window
@@ -344,6 +436,8 @@ fast_status process(fast_server *S, fast_station *st, fast_request *r) {
              *hcnt = nullptr;
     uint2 *range = nullptr;
     uint8_t *ndrop = nullptr;
+    uint32_t *wg = nullptr;
+    if ((stt = alloc(&wg, (size_t)n * kWG))) return fail(stt);
     if ((stt = alloc(&d_idx, (size_t)n * r->ld)) || (stt = alloc(&keys, (size_t)nb * n)) ||
         (stt = alloc(&bkey, (size_t)nb * n)) || (stt = alloc(&bid, (size_t)nb * n)) ||
         (stt = alloc(&bka, (size_t)nb * n)) || (stt = alloc(&bia, (size_t)nb * n)) ||
@@ -370,6 +464,11 @@ fast_status process(fast_server *S, fast_station *st, fast_request *r) {
     a.first_id = r->first_id;
     a.occ_num = p.occ_num;
     a.occ_den = p.occ_den;
+    a.label = st->hg.label;
+    a.large = st->hg.large;
+    a.tstart = st->hg.tstart;
+    a.wg = wg;
+    cudaMemsetAsync(wg, 0xFF, (size_t)n * kWG * 4, s);
     cudaMemsetAsync(hcnt, 0, (size_t)n * 4, s);
     const dim3 g(std::max(1u, ceil_div(n, 128)), nb);
     k_req_lookup<<<g, 128, 0, s>>>(a, range, hcnt), FAST_LAUNCHED(c);
@@ -386,6 +485,11 @@ fast_status process(fast_server *S, fast_station *st, fast_request *r) {
     // 4. candidate count, vote map
     cudaMemsetAsync(scal, 0, 16, s);
     k_req_pairs<0><<<g, 128, 0, s>>>(a, scal, nullptr, 0, c->d_err), FAST_LAUNCHED(c);
+    const bool dense = st->hg.nlarge > 0;
+    const size_t dsm = (size_t)nb * 4;
+    if (dense)
+        k_req_dense<0><<<n, 256, dsm, s>>>(a, st->hg.gstart, st->hg.ids, st->hg.bm, st->hg.bm_off, scal, nullptr, 0,
+                                           c->d_err), FAST_LAUNCHED(c);
     uint64_t total = 0;
     cudaMemcpyAsync(&total, scal, 8, cudaMemcpyDeviceToHost, s);
     if ((stt = sync_check(c, s, "request count"))) return fail(stt);
@@ -394,16 +498,21 @@ fast_status process(fast_server *S, fast_station *st, fast_request *r) {
     if ((stt = alloc(&map, mcap))) return fail(stt);
     cudaMemsetAsync(map, 0, mcap * 8, s);
     k_req_pairs<1><<<g, 128, 0, s>>>(a, nullptr, map, mcap, c->d_err), FAST_LAUNCHED(c);
+    if (dense)
+        k_req_dense<1><<<n, 256, dsm, s>>>(a, st->hg.gstart, st->hg.ids, st->hg.bm, st->hg.bm_off, nullptr, map, mcap,
+                                           c->d_err), FAST_LAUNCHED(c);
     // 5. keep, order, copy out
     const uint64_t max_id = r->first_id + n;
     uint32_t nbits = 1;
     while (nbits < 28 && (1ull << nbits) < max_id) nbits++;
-    cudaMemsetAsync(scal + 1, 0, 8, s);
+    cudaMemsetAsync(scal + 1, 0, 16, s);
     const unsigned cg = (unsigned)std::min<uint64_t>(ceil_div(mcap, 256), c->num_sms * 8);
     k_req_compact<<<cg, 256, 0, s>>>(map, mcap, p.v, nbits, nullptr, scal + 1, 0), FAST_LAUNCHED(c);
-    uint64_t M = 0;
-    cudaMemcpyAsync(&M, scal + 1, 8, cudaMemcpyDeviceToHost, s);
+    uint64_t Ms = 0, Md = 0;
+    cudaMemcpyAsync(&Ms, scal + 1, 8, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&Md, scal + 2, 8, cudaMemcpyDeviceToHost, s);
     if ((stt = sync_check(c, s, "request votes"))) return fail(stt);
+    const uint64_t M = Ms + Md;
     r->ri.resize(M);
     r->rj.resize(M);
     r->rv.resize(M);
@@ -416,6 +525,7 @@ fast_status process(fast_server *S, fast_station *st, fast_request *r) {
             return fail(stt);
         cudaMemsetAsync(scal + 1, 0, 8, s);
         k_req_compact<<<cg, 256, 0, s>>>(map, mcap, p.v, nbits, ok, scal + 1, M), FAST_LAUNCHED(c);
+
         uint64_t *sorted = reinterpret_cast<uint64_t *>(ok);
         if (M > 1 && (stt = sort_u64(c, M, reinterpret_cast<uint64_t *>(ok), reinterpret_cast<uint64_t *>(ok2), 8,
                                      8 + 2 * nbits, &sorted, s)))
@@ -554,6 +664,7 @@ void fast_server_destroy(fast_server *S) {
         }
         if (sn->stream) cudaStreamSynchronize(sn->stream);
         if (sn->hist) fast_tables_free(sn->hist);
+        history_groups_free(&sn->hg);
         if (sn->ctx) fast_destroy(sn->ctx);
         cudaFree(sn->dslot);
         cudaFree(sn->dent_id);
@@ -581,7 +692,7 @@ fast_status fast_server_load_history(fast_server *S, uint32_t station, const uin
     fast_ctx *c = sn->ctx;
     cudaStream_t s = sn->stream;
     const fast_params &p = S->p;
-    const uint64_t hist_bytes = (uint64_t)p.b * N * 8 + N;
+    const uint64_t hist_bytes = (uint64_t)p.b * N * 8 + N * 5;  // tables, drop mask, labels
     if (S->budget && S->resident + hist_bytes > S->budget) {
         S->err = "history does not fit the HBM budget";
         return FAST_EBUDGET;
@@ -599,11 +710,14 @@ fast_status fast_server_load_history(fast_server *S, uint32_t station, const uin
     st = sig_launch(c, d_idx, N, ld, sig, s);
     fast_tables *tb = nullptr;
     if (!st) st = fast_build_tables(c, sig, N, &tb, s);
+    if (!st) st = history_groups(c, tb, sig, &sn->hg, s);
     dfree(c, d_idx, (size_t)N * ld * 2, s);
     dfree(c, sig, (size_t)p.b * (N ? N : 1) * 4, s);
     cudaStreamSynchronize(s);
     if (st) {
         S->err = c->err;
+        if (tb) fast_tables_free(tb);
+        history_groups_free(&sn->hg);
         return st;
     }
     tb->d_sig = nullptr;  // the server never searches the history itself
@@ -701,6 +815,25 @@ fast_status fast_stream_release(fast_server *S, uint64_t req_id) {
         S->reqs.erase(it);
     }
     delete r;
+    return FAST_OK;
+}
+
+fast_status fast_server_set_option(fast_server *S, const char *name, double value) {
+    if (!S || !name) return FAST_EINVAL;
+    for (auto *sn : S->st) {
+        std::lock_guard<std::mutex> lk(sn->mu);
+        if (sn->loaded) {
+            S->err = "options must be set before any history is loaded";
+            return FAST_EINVAL;
+        }
+    }
+    for (auto *sn : S->st) {
+        fast_status st = fast_set_option(sn->ctx, name, value);
+        if (st) {
+            S->err = sn->ctx->err;
+            return st;
+        }
+    }
     return FAST_OK;
 }
 

@@ -128,3 +128,22 @@ def test_budget_admission_serialises_but_stays_exact():
     srv.close()
     with pytest.raises(FastError):
         tiny = _server(p, 1, hbm_budget_bytes=1 << 20)
+
+
+def test_dense_groups_in_requests_stay_exact():
+    # With large_min small enough for the noise and template copies of the
+    # history to form dense groups, request windows meeting them are compared
+    # with the groups key by key; results must not change.
+    stations = [_station(s) for s in (11, 12)]
+    p = stations[0][0].params()
+    want = [_replay(p, idx, w.K) for w, idx in stations]
+    for lm in (6, 12):
+        srv = _server(p, 2, large_min=lm)
+        for s, (w, idx) in enumerate(stations):
+            srv.load_history(s, idx[:N0])
+        ids = [[srv.submit(s, sl) for sl in _slices(idx)] for s, (w, idx) in enumerate(stations)]
+        got = [[srv.wait(r) for r in row] for row in ids]
+        srv.close()
+        for s in range(2):
+            for q in range(len(SIZES)):
+                assert _same(got[s][q][1:], want[s][q]), f"large_min {lm} station {s} request {q}"
