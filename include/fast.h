@@ -178,6 +178,58 @@ fast_status fast_detect(fast_ctx *ctx, const uint16_t *d_idx, uint64_t N, uint32
                         void *stream);
 
 /*
+ * Batched search of several stations in one pass (pairs never cross
+ * stations).  d_idx holds the stations' windows one after the other
+ * (station x: h_station_N[x] rows of ld uint16, device memory); every stage
+ * runs once over all of them -- one signature launch, one table sort with a
+ * final stable pass on the station, one launch per search stage -- with each
+ * station's own occurrence threshold (its own N).  out[x] receives station
+ * x's detections with station-local ids, exactly those of fast_detect on that
+ * station alone.  1 <= n_st <= 256; sum of the N < 2^28.
+ */
+fast_status fast_detect_batch(fast_ctx *ctx, const uint16_t *d_idx, const uint64_t *h_station_N, uint32_t n_st,
+                              uint32_t ld, fast_result **out, void *stream);
+
+/*
+ * Batched search plans: a fixed batch shape whose table build (signatures,
+ * radix passes, occurrence filter) is captured once as a CUDA graph and
+ * replayed for every run, and whose search options are chosen by an
+ * autotuner on the first run.  The plan reads d_idx, the device buffer given
+ * at creation, on every run: refill that buffer between runs.  `stream` must
+ * not be the legacy default stream (graph capture).  Creation runs the build
+ * once (to size the plan's arena, which the plan then owns).
+ */
+typedef struct fast_plan fast_plan;
+
+typedef struct {
+    uint32_t vote_map;   /* 1 = global vote map, 0 = row-partitioned votes */
+    uint32_t large_min;  /* dense-group threshold (0 = automatic)          */
+    float map_load;      /* vote-map load factor                           */
+    float ms;            /* measured search time of this choice            */
+} fast_plan_choice;
+
+typedef struct {
+    uint64_t graph_nodes, graph_kernels, arena_bytes;
+    float build_ms;      /* last replay of the build graph (timing option on) */
+    uint32_t tuned, n_tried;
+    fast_plan_choice best;
+    fast_plan_choice tried[8];
+} fast_plan_info_t;
+
+fast_status fast_plan_create(fast_ctx *ctx, const uint16_t *d_idx, const uint64_t *h_station_N, uint32_t n_st,
+                             uint32_t ld, void *stream, fast_plan **out);
+
+/* Replays the build graph and searches; out[x] as fast_detect_batch gives.
+ * The first run times every candidate option set (vote path, dense-group
+ * threshold, map load) and keeps the fastest for later runs; the context's
+ * own options are left as they were.  Every candidate gives the same list. */
+fast_status fast_plan_run(fast_plan *plan, fast_result **out, void *stream);
+
+fast_status fast_plan_info(const fast_plan *plan, fast_plan_info_t *info);
+
+void fast_plan_destroy(fast_plan *plan);
+
+/*
  * The whole path from and to host memory: copies h_idx (N rows of ld uint16)
  * to the device, runs fast_detect, and copies at most `cap` detections back
  * to h_i / h_j / h_votes.  *M receives the total number of detections (which

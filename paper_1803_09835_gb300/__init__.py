@@ -21,7 +21,7 @@ from ._lib import (FAST_MINHASH, FAST_MINMAX, FastError, fast_build_tables, fast
                    fast_set_option, fast_sig, fast_stream_latency, fast_stream_poll, fast_stream_release,
                    fast_stream_submit, fast_tables_free, fast_tables_view)
 
-__all__ = ["Searcher", "Result", "Tables", "FastError", "FAST_MINHASH", "FAST_MINMAX", "fast_create", "fast_destroy",
+__all__ = ["Searcher", "Plan", "Result", "Tables", "FastError", "FAST_MINHASH", "FAST_MINMAX", "fast_create", "fast_destroy",
            "fast_sig", "fast_build_tables", "fast_tables_view", "fast_tables_free", "fast_search", "fast_detect",
            "fast_detect_host", "fast_result_view", "fast_result_free", "fast_get_stats", "fast_set_option", "Server",
            "fast_server_create", "fast_server_destroy", "fast_server_load_history", "fast_stream_submit",
@@ -117,6 +117,14 @@ class Searcher:
         N, ld = idx.shape
         return Result(fast_detect(self.ctx, idx, N, ld, stream))
 
+    def detect_batch(self, idx, station_N, stream=None):
+        """Several stations in one pass: idx holds their rows one after another."""
+        return [Result(h) for h in _lib.fast_detect_batch(self.ctx, idx, list(station_N), idx.shape[1], stream)]
+
+    def plan(self, idx, station_N, stream) -> "Plan":
+        """A batch plan over idx (refill it between runs); see :class:`Plan`."""
+        return Plan(self, idx, station_N, stream)
+
     def detect_host(self, idx: np.ndarray, cap: int | None = None, stream=None):
         """Whole path from host memory: returns (M, i, j, votes) numpy arrays."""
         N, ld = idx.shape
@@ -131,6 +139,34 @@ class Searcher:
 
     def stats(self) -> dict:
         return fast_get_stats(self.ctx)
+
+
+class Plan:
+    """A fixed batch shape: the build replays as a CUDA graph, the search options are autotuned once."""
+
+    def __init__(self, searcher: Searcher, idx, station_N, stream):
+        self.searcher = searcher
+        self.idx = idx  # the graph reads this buffer on every run
+        self.n_st = len(station_N)
+        self.stream = stream
+        self.handle = _lib.fast_plan_create(searcher.ctx, idx, list(station_N), idx.shape[1], stream)
+
+    def run(self):
+        return [Result(h) for h in _lib.fast_plan_run(self.searcher.ctx, self.handle, self.n_st, self.stream)]
+
+    def info(self) -> dict:
+        return _lib.fast_plan_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.fast_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

@@ -45,6 +45,20 @@ class fast_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class fast_plan_choice(ctypes.Structure):
+    _fields_ = [("vote_map", ctypes.c_uint32), ("large_min", ctypes.c_uint32), ("map_load", ctypes.c_float),
+                ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class fast_plan_info_t(ctypes.Structure):
+    _fields_ = [("graph_nodes", ctypes.c_uint64), ("graph_kernels", ctypes.c_uint64), ("arena_bytes", ctypes.c_uint64),
+                ("build_ms", ctypes.c_float), ("tuned", ctypes.c_uint32), ("n_tried", ctypes.c_uint32),
+                ("best", fast_plan_choice), ("tried", fast_plan_choice * 8)]
+
+
 _lib = None
 
 
@@ -69,6 +83,7 @@ def load():
         "fast_tables_free": (None, [vp]),
         "fast_search": (st, [vp, vp, pp(vp), vp]),
         "fast_detect": (st, [vp, vp, u64, u32, pp(vp), vp]),
+        "fast_detect_batch": (st, [vp, vp, vp, u32, u32, vp, vp]),
         "fast_detect_host": (st, [vp, vp, u64, u32, pp(u64), vp, vp, vp, u64, vp]),
         "fast_result_view": (st, [vp, pp(u64), pp(vp), pp(vp), pp(vp)]),
         "fast_result_free": (None, [vp]),
@@ -85,6 +100,10 @@ def load():
         "fast_stream_release": (st, [vp, u64]),
         "fast_server_inject_failure": (st, [vp, u64]),
         "fast_server_set_option": (st, [vp, ctypes.c_char_p, ctypes.c_double]),
+        "fast_plan_create": (st, [vp, vp, vp, u32, u32, vp, pp(vp)]),
+        "fast_plan_run": (st, [vp, vp, vp]),
+        "fast_plan_info": (st, [vp, pp(fast_plan_info_t)]),
+        "fast_plan_destroy": (None, [vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -319,3 +338,43 @@ def fast_server_inject_failure(srv, req_id: int):
 
 def fast_server_set_option(srv, name: str, value: float):
     _scheck(srv, load().fast_server_set_option(srv, name.encode(), float(value)))
+
+
+def fast_detect_batch(ctx, d_idx, station_N, ld: int, stream=None):
+    """One pass over several stations (rows concatenated in d_idx); one result per station."""
+    n = len(station_N)
+    arr = (ctypes.c_uint64 * n)(*[int(x) for x in station_N])
+    out = (ctypes.c_void_p * n)()
+    _check(ctx, load().fast_detect_batch(ctx, _dptr(d_idx), ctypes.cast(arr, ctypes.c_void_p), n, ld,
+                                         ctypes.cast(out, ctypes.c_void_p), _stream(stream)))
+    return [ctypes.c_void_p(out[k]) for k in range(n)]
+
+
+# ------------------------------------------------------------- batch plans
+
+def fast_plan_create(ctx, d_idx, station_N, ld: int, stream):
+    """A batch plan over the rows of d_idx (read again on every run)."""
+    n = len(station_N)
+    arr = (ctypes.c_uint64 * n)(*[int(x) for x in station_N])
+    out = ctypes.c_void_p()
+    _check(ctx, load().fast_plan_create(ctx, _dptr(d_idx), ctypes.cast(arr, ctypes.c_void_p), n, ld, _stream(stream),
+                                        ctypes.byref(out)))
+    return out
+
+
+def fast_plan_run(ctx, plan, n_st: int, stream):
+    out = (ctypes.c_void_p * n_st)()
+    _check(ctx, load().fast_plan_run(plan, ctypes.cast(out, ctypes.c_void_p), _stream(stream)))
+    return [ctypes.c_void_p(out[k]) for k in range(n_st)]
+
+
+def fast_plan_info(plan) -> dict:
+    info = fast_plan_info_t()
+    _check(None, load().fast_plan_info(plan, ctypes.byref(info)))
+    return {"graph_nodes": info.graph_nodes, "graph_kernels": info.graph_kernels, "arena_bytes": info.arena_bytes,
+            "build_ms": info.build_ms, "tuned": bool(info.tuned), "best": info.best.as_dict(),
+            "tried": [info.tried[k].as_dict() for k in range(info.n_tried)]}
+
+
+def fast_plan_destroy(plan):
+    load().fast_plan_destroy(plan)

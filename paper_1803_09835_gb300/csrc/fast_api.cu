@@ -28,6 +28,14 @@ fast_status cuda_fail(fast_ctx *c, cudaError_t e, const char *where) {
 fast_status dalloc(fast_ctx *c, void **p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    const size_t rounded = (bytes + 255) & ~(size_t)255;
+    if (c->trace) c->trace_total += rounded;
+    if (c->arena) {
+        if (c->arena_off + rounded > c->arena_size) return set_error(c, FAST_EINTERNAL, "plan arena exhausted");
+        *p = c->arena + c->arena_off;
+        c->arena_off += rounded;
+        return FAST_OK;
+    }
     if (c->budget && c->live + bytes > c->budget)
         return set_error(c, FAST_EBUDGET,
                          "HBM budget exceeded: " + std::to_string(c->live + bytes) + " > " + std::to_string(c->budget));
@@ -43,6 +51,7 @@ fast_status dalloc(fast_ctx *c, void **p, size_t bytes, cudaStream_t s) {
 
 void dfree(fast_ctx *c, void *p, size_t bytes, cudaStream_t s) {
     if (!p) return;
+    if (c->arena && (char *)p >= c->arena && (char *)p < c->arena + c->arena_size) return;  // arena: freed with the plan
     if (bytes == 0) bytes = 16;
     cudaFreeAsync(p, s);
     c->live -= std::min<uint64_t>(c->live, bytes);
@@ -66,8 +75,10 @@ fast_status sync_check(fast_ctx *c, cudaStream_t s, const char *where) {
 
 static thread_local uint32_t g_marked = 0;  // stage slots recorded by the current call on this thread
 
+void stage_reset() { g_marked = 0; }
+
 void stage_mark(fast_ctx *c, int slot, cudaStream_t s) {
-    if (!c->timing) return;
+    if (!c->timing || c->capturing) return;
     cudaEventRecord(c->ev[slot], s);
     g_marked |= 1u << slot;
 }
@@ -97,7 +108,7 @@ static fast_status validate(const fast_params *p, std::string &why) {
     return FAST_OK;
 }
 
-static void stats_times(fast_ctx *c, bool whole) {
+void stats_times(fast_ctx *c, bool whole) {
     fast_stats &s = c->stats;
     s.ms_sig = whole ? stage_ms(c, 0, 1) : 0.f;
     s.ms_sort = whole ? stage_ms(c, 1, 2) : 0.f;
@@ -186,10 +197,16 @@ fast_status fast_sig(fast_ctx *c, const uint16_t *d_idx, uint64_t N, uint32_t ld
     return sync_check(c, s, "fast_sig");
 }
 
-static fast_status build_tables(fast_ctx *c, const uint32_t *d_sig, uint64_t N, fast_tables **out, cudaStream_t s) {
+}  // extern "C"
+
+// Builds the tables of N windows; with nst > 1 stations (offsets h_soff,
+// nst + 1 entries) the per-table listing is ordered by (station, key, id).
+fast_status build_tables(fast_ctx *c, const uint32_t *d_sig, uint64_t N, const uint64_t *h_soff, uint32_t nst,
+                         fast_tables **out, cudaStream_t s) {
     *out = nullptr;
     if (N > (1ull << 28) - 1) return set_error(c, FAST_EINVAL, "N must be < 2^28");
     if (N && !d_sig) return set_error(c, FAST_EINVAL, "d_sig is NULL");
+    if (nst < 1 || nst > 256) return set_error(c, FAST_EINVAL, "1 to 256 stations per batch");
     const uint32_t nb = c->p.b;
     fast_tables *tb = new fast_tables();
     tb->ctx = c;
@@ -197,22 +214,35 @@ static fast_status build_tables(fast_ctx *c, const uint32_t *d_sig, uint64_t N, 
     tb->b = nb;
     tb->d_sig = d_sig;
     tb->stream = s;
+    tb->nst = nst;
+    if (h_soff) tb->soff.assign(h_soff, h_soff + nst + 1);
+    else tb->soff = {0, N};
     const size_t n = (size_t)nb * N;
     uint32_t *ka = nullptr, *va = nullptr;
     fast_status st;
-    if ((st = dalloc_t(c, &tb->d_skey, n, s)) || (st = dalloc_t(c, &tb->d_sid, n, s)) ||
-        (st = dalloc_t(c, &tb->d_drop, N ? N : 1, s)) || (st = dalloc_t(c, &ka, n, s)) ||
-        (st = dalloc_t(c, &va, n, s))) {
+    if ((st = dalloc_t(c, &tb->d_soff, nst + 1, s)) || (st = dalloc_t(c, &tb->d_skey, n, s)) ||
+        (st = dalloc_t(c, &tb->d_sid, n, s)) || (st = dalloc_t(c, &tb->d_drop, N ? N : 1, s)) ||
+        (st = dalloc_t(c, &ka, n, s)) || (st = dalloc_t(c, &va, n, s))) {
         dfree(c, ka, n * 4, s);
         dfree(c, va, n * 4, s);
         fast_tables_free(tb);
         return st;
     }
+    if (!c->capturing)  // a captured build gets its offsets uploaded once by the plan
+        cudaMemcpyAsync(tb->d_soff, tb->soff.data(), (nst + 1) * 8, cudaMemcpyHostToDevice, s);
     uint32_t *ko = nullptr, *vo = nullptr;
     st = sort_u32(c, nb, N, d_sig, nullptr, ka, va, tb->d_skey, tb->d_sid, 0, 32, &ko, &vo, s, &c->stats.sort_passes);
     if (!st && N && ko != tb->d_skey) {  // odd number of passes: result sits in the scratch pair
         cudaMemcpyAsync(tb->d_skey, ko, n * 4, cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(tb->d_sid, vo, n * 4, cudaMemcpyDeviceToDevice, s);
+    }
+    if (!st && N && nst > 1) {  // stable station pass into the scratch pair, which becomes the table
+        st = sort_station_pass(c, nb, N, tb->d_skey, tb->d_sid, ka, va, Stations{tb->d_soff, nst}, s);
+        if (!st) {
+            std::swap(tb->d_skey, ka);
+            std::swap(tb->d_sid, va);
+            c->stats.sort_passes++;
+        }
     }
     dfree(c, ka, n * 4, s);
     dfree(c, va, n * 4, s);
@@ -227,11 +257,13 @@ static fast_status build_tables(fast_ctx *c, const uint32_t *d_sig, uint64_t N, 
     return FAST_OK;
 }
 
+extern "C" {
+
 fast_status fast_build_tables(fast_ctx *c, const uint32_t *d_sig, uint64_t N, fast_tables **out, void *stream) {
     if (!c || !out) return FAST_EINVAL;
     c->err.clear();
     c->stats.n_launches = 0;
-    return build_tables(c, d_sig, N, out, (cudaStream_t)stream);
+    return build_tables(c, d_sig, N, nullptr, 1, out, (cudaStream_t)stream);
 }
 
 fast_status fast_tables_view(const fast_tables *tb, uint64_t *N, uint32_t *b, const uint32_t **d_skey,
@@ -252,6 +284,7 @@ void fast_tables_free(fast_tables *tb) {
     dfree(c, tb->d_skey, n * 4, tb->stream);
     dfree(c, tb->d_sid, n * 4, tb->stream);
     dfree(c, tb->d_drop, tb->N ? tb->N : 1, tb->stream);
+    dfree(c, tb->d_soff, (tb->nst + 1) * 8, tb->stream);
     delete tb;
 }
 
@@ -285,13 +318,125 @@ fast_status fast_detect(fast_ctx *c, const uint16_t *d_idx, uint64_t N, uint32_t
     st = sig_launch(c, d_idx, N, ld, sig, s);
     stage_mark(c, 1, s);
     fast_tables *tb = nullptr;
-    if (!st) st = build_tables(c, sig, N, &tb, s);  // synchronises: reports bad indices too
+    if (!st) st = build_tables(c, sig, N, nullptr, 1, &tb, s);  // synchronises: reports bad indices too
     if (!st) st = search_run(c, tb, sig, out, s);
     fast_tables_free(tb);
     dfree(c, sig, n * 4, s);
     if (!st) stats_times(c, true);
     c->stats.n_fingerprints = N;
     return st;
+}
+
+// Splits a batch's (i, j)-ordered list into per-station lists with local ids.
+__global__ void k_split_station(const uint32_t *__restrict__ gi, const uint32_t *__restrict__ gj,
+                                const uint8_t *__restrict__ gv, uint64_t a0, uint64_t m, uint32_t base,
+                                uint32_t *__restrict__ oi, uint32_t *__restrict__ oj, uint8_t *__restrict__ ov) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < m; x += (uint64_t)gridDim.x * blockDim.x) {
+        oi[x] = gi[a0 + x] - base;
+        oj[x] = gj[a0 + x] - base;
+        ov[x] = gv[a0 + x];
+    }
+}
+
+__global__ void k_station_bounds(const uint32_t *__restrict__ gi, uint64_t M, const uint64_t *__restrict__ soff,
+                                 uint32_t nst, unsigned long long *__restrict__ first) {
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s > nst) return;
+    uint64_t lo = 0, hi = M;  // first entry with i >= soff[s]
+    while (lo < hi) {
+        const uint64_t m = (lo + hi) / 2;
+        if (gi[m] < soff[s]) lo = m + 1;
+        else hi = m;
+    }
+    first[s] = lo;
+}
+
+}  // extern "C"
+
+namespace fastgb {
+// Splits a batch result (global ids, (i, j) order) into per-station results
+// with local ids; frees `all`.
+fast_status split_stations(fast_ctx *c, fast_result *all, const std::vector<uint64_t> &soff, fast_result **out,
+                           cudaStream_t s) {
+    const uint32_t n_st = (uint32_t)soff.size() - 1;
+    unsigned long long *first = nullptr;
+    uint64_t *d_soff = nullptr;
+    fast_status st;
+    if ((st = dalloc_t(c, &first, n_st + 1, s)) || (st = dalloc_t(c, &d_soff, n_st + 1, s))) {
+        fast_result_free(all);
+        return st;
+    }
+    cudaMemcpyAsync(d_soff, soff.data(), (n_st + 1) * 8, cudaMemcpyHostToDevice, s);
+    k_station_bounds<<<ceil_div(n_st + 1, 128), 128, 0, s>>>(all->d_i, all->M, d_soff, n_st, first), FAST_LAUNCHED(c);
+    std::vector<unsigned long long> hf(n_st + 1);
+    cudaMemcpyAsync(hf.data(), first, (n_st + 1) * 8, cudaMemcpyDeviceToHost, s);
+    st = sync_check(c, s, "station bounds");
+    hf[n_st] = all->M;
+    for (uint32_t x = 0; x < n_st && !st; x++) {
+        fast_result *r = new fast_result();
+        r->ctx = c;
+        r->stream = s;
+        r->M = hf[x + 1] - hf[x];
+        const uint64_t m = r->M ? r->M : 1;
+        if ((st = dalloc_t(c, &r->d_i, m, s)) || (st = dalloc_t(c, &r->d_j, m, s)) ||
+            (st = dalloc_t(c, &r->d_votes, m, s))) {
+            fast_result_free(r);
+            break;
+        }
+        if (r->M)
+            k_split_station<<<std::max(1u, std::min<unsigned>(ceil_div(r->M, 256), c->num_sms * 8)), 256, 0, s>>>(
+                all->d_i, all->d_j, all->d_votes, hf[x], r->M, (uint32_t)soff[x], r->d_i, r->d_j, r->d_votes),
+                FAST_LAUNCHED(c);
+        out[x] = r;
+    }
+    dfree(c, first, (n_st + 1) * 8, s);
+    dfree(c, d_soff, (n_st + 1) * 8, s);
+    fast_result_free(all);
+    if (!st) st = sync_check(c, s, "batch split");
+    if (st)
+        for (uint32_t x = 0; x < n_st; x++) {
+            fast_result_free(out[x]);
+            out[x] = nullptr;
+        }
+    return st;
+}
+}  // namespace fastgb
+
+extern "C" {
+
+fast_status fast_detect_batch(fast_ctx *c, const uint16_t *d_idx, const uint64_t *h_station_N, uint32_t n_st,
+                              uint32_t ld, fast_result **out, void *stream) {
+    if (!c || !out || !h_station_N || n_st == 0) return FAST_EINVAL;
+    c->err.clear();
+    for (uint32_t x = 0; x < n_st; x++) out[x] = nullptr;
+    if (n_st > 256) return set_error(c, FAST_EINVAL, "at most 256 stations per batch");
+    if (ld < c->p.K) return set_error(c, FAST_EINVAL, "ld < K");
+    std::vector<uint64_t> soff(n_st + 1, 0);
+    for (uint32_t x = 0; x < n_st; x++) soff[x + 1] = soff[x] + h_station_N[x];
+    const uint64_t N = soff[n_st];
+    if (N > (1ull << 28) - 1) return set_error(c, FAST_EINVAL, "batch larger than 2^28 - 1 windows");
+    if (N && !d_idx) return set_error(c, FAST_EINVAL, "d_idx is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    g_marked = 0;
+    c->stats.n_launches = 0;
+    stage_mark(c, 0, s);
+    uint32_t *sig = nullptr;
+    const size_t n = (size_t)c->p.b * N;
+    fast_status st = dalloc_t(c, &sig, n ? n : 1, s);
+    if (st) return st;
+    st = sig_launch(c, d_idx, N, ld, sig, s);
+    stage_mark(c, 1, s);
+    fast_tables *tb = nullptr;
+    fast_result *all = nullptr;
+    if (!st) st = build_tables(c, sig, N, soff.data(), n_st, &tb, s);
+    if (!st) st = search_run(c, tb, sig, &all, s);
+    fast_tables_free(tb);
+    dfree(c, sig, n * 4, s);
+    if (st) return st;
+    if ((st = split_stations(c, all, soff, out, s))) return st;
+    stats_times(c, true);
+    c->stats.n_fingerprints = N;
+    return FAST_OK;
 }
 
 fast_status fast_detect_host(fast_ctx *c, const uint16_t *h_idx, uint64_t N, uint32_t ld, uint64_t *M,

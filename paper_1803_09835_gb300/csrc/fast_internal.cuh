@@ -39,6 +39,24 @@ __device__ __forceinline__ uint32_t hash_ab(uint32_t a_lo, uint32_t a_hi, uint64
     return (uint32_t)(t >> 32) + a_hi * x;
 }
 
+// A batched search concatenates stations: station s holds window ids and
+// table positions [soff[s], soff[s+1]) (soff has nst + 1 entries; a single
+// station is nst = 1, soff = {0, N}).  Buckets never cross a station.
+struct Stations {
+    const uint64_t *soff;
+    uint32_t nst;
+};
+
+__device__ __forceinline__ uint32_t station_of(const Stations &S, uint64_t p) {
+    uint32_t lo = 0, hi = S.nst;  // largest s with soff[s] <= p
+    while (hi - lo > 1) {
+        const uint32_t m = (lo + hi) / 2;
+        if (S.soff[m] <= p) lo = m;
+        else hi = m;
+    }
+    return lo;
+}
+
 // Device error flags, OR-ed into ctx->d_err.
 enum : uint32_t {
     ERR_BAD_INDEX = 1u << 0,   // fingerprint index >= D
@@ -132,6 +150,13 @@ struct fast_ctx {
     uint64_t budget = 0;   // 0 = unbounded
     uint64_t live = 0;     // bytes currently allocated through the pool
     uint64_t peak = 0;
+    // arena mode (CUDA-graph capture): allocations bump-allocate from a fixed
+    // buffer and frees are no-ops; trace mode sums the bytes allocated
+    char *arena = nullptr;
+    uint64_t arena_size = 0, arena_off = 0;
+    bool trace = false;
+    uint64_t trace_total = 0;
+    bool capturing = false;     // no host synchronisation while a graph is being captured
     // tuning
     uint32_t large_min = 0;     // live bucket size from which a bucket goes to the dense path (0 = auto)
     float map_load = 0.5f;      // vote-map load factor target
@@ -148,6 +173,9 @@ struct fast_tables {
     uint64_t N = 0;
     uint32_t b = 0;
     const uint32_t *d_sig = nullptr;  // [b][N] keys the tables were built from (caller-owned)
+    uint32_t nst = 1;                 // stations (batched search)
+    std::vector<uint64_t> soff;       // [nst + 1] station offsets (host)
+    uint64_t *d_soff = nullptr;       // same, device
     uint32_t *d_skey = nullptr;  // [b][N]
     uint32_t *d_sid = nullptr;   // [b][N]
     uint8_t *d_drop = nullptr;   // [N]
@@ -207,6 +235,10 @@ fast_status sort_u32(fast_ctx *c, uint32_t nseg, uint64_t len, const uint32_t *k
                      uint32_t bit1, uint32_t **keys_out, uint32_t **vals_out, cudaStream_t s, uint32_t *passes);
 fast_status sort_u64(fast_ctx *c, uint64_t len, uint64_t *keys_a, uint64_t *keys_b, uint32_t bit0, uint32_t bit1,
                      uint64_t **keys_out, cudaStream_t s);
+// One more stable pass that orders every segment by the station of its
+// values (ids): (key, id) runs become (station, key, id) runs.  nst <= 256.
+fast_status sort_station_pass(fast_ctx *c, uint32_t nseg, uint64_t len, const uint32_t *keys_in, const uint32_t *vals_in,
+                              uint32_t *keys_out, uint32_t *vals_out, Stations S, cudaStream_t s);
 
 // k_scan.cu: out[seg][k] = sum of in[seg][0..k), nseg segments of n counts;
 // totals[seg] (optional, device) receives each segment's sum.
@@ -234,7 +266,22 @@ struct HistGroups {
     uint64_t *bm_off = nullptr;  // [nlarge] first word of each large bucket's bitmap
 };
 fast_status history_groups(fast_ctx *c, const fast_tables *tb, const uint32_t *d_sig, HistGroups *g, cudaStream_t s);
+uint32_t large_min_for(const fast_ctx *c, uint64_t N);  // the dense-group threshold (option or automatic)
+struct Scal {  // device scalar slots (ctx->d_scal)
+    enum { NBIG, NLARGE, NMEDIUM, NHEAVY, NDROP, NMEMB, CUR_DENSE, CUR_SPARSE, CHANGED, NLONG, NMERGE, NMERGE_TOT,
+           NCAND, NMID, SMALLPAIRS, PART0 };
+};
 void history_groups_free(HistGroups *g);
+
+// fast_api.cu
+fast_status split_stations(fast_ctx *c, fast_result *all, const std::vector<uint64_t> &soff, fast_result **out,
+                           cudaStream_t s);
+}  // namespace fastgb
+fast_status build_tables(fast_ctx *c, const uint32_t *d_sig, uint64_t N, const uint64_t *h_soff, uint32_t nst,
+                         fast_tables **out, cudaStream_t s);
+void stats_times(fast_ctx *c, bool whole);
+namespace fastgb {
+void stage_reset();  // forget the stage marks of the previous call on this thread
 
 // timing helpers (fast_api.cu)
 void stage_mark(fast_ctx *c, int slot, cudaStream_t s);

@@ -34,26 +34,30 @@ constexpr uint32_t kSmall = 32;  // buckets up to this size are enumerated by on
 
 // -------------------------------------------------------------- filter
 
-// Heavy bucket starts: size >= smin, i.e. occ_den * size > occ_num * N.
-__global__ void k_heavy_find(const uint32_t *__restrict__ skey, uint64_t N, uint64_t smin,
-                             uint4 *__restrict__ list, unsigned long long *__restrict__ count, uint64_t cap,
-                             uint32_t *err) {
+// Heavy bucket starts: size >= smin, i.e. occ_den * size > occ_num * N_s,
+// N_s the size of the bucket's station.
+__global__ void k_heavy_find(const uint32_t *__restrict__ skey, uint64_t N, Stations S, uint32_t occ_num,
+                             uint32_t occ_den, uint4 *__restrict__ list, unsigned long long *__restrict__ count,
+                             uint64_t cap, uint32_t *err) {
     const uint32_t t = blockIdx.y;
     const uint32_t *k = skey + (uint64_t)t * N;
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t sx = station_of(S, p);
+        const uint64_t s0 = S.soff[sx], s1 = S.soff[sx + 1];
+        const uint64_t smin = (uint64_t)occ_num * (s1 - s0) / occ_den + 1;
         const uint32_t key = k[p];
-        if (p > 0 && k[p - 1] == key) continue;
-        if (p + smin - 1 >= N || k[p + smin - 1] != key) continue;
+        if (p > s0 && k[p - 1] == key) continue;
+        if (p + smin - 1 >= s1 || k[p + smin - 1] != key) continue;
         // gallop then bisect to the end of the run
         uint64_t lo = p + smin - 1, step = 1, hi;
         for (;;) {
             hi = lo + step;
-            if (hi >= N || k[hi] != key) break;
+            if (hi >= s1 || k[hi] != key) break;
             lo = hi;
             step <<= 1;
         }
-        if (hi > N) hi = N;
-        while (hi - lo > 1) {  // k[lo] == key, k[hi] != key or hi == N
+        if (hi > s1) hi = s1;
+        while (hi - lo > 1) {  // k[lo] == key, k[hi] != key or hi == s1
             uint64_t mid = lo + (hi - lo) / 2;
             if (k[mid] == key) lo = mid;
             else hi = mid;
@@ -98,6 +102,7 @@ struct EnumArgs {
     uint32_t excl;
     uint32_t i_lo, i_hi;  // query partition [i_lo, i_hi)
     uint32_t nparts;      // counting: partition of i is i * nparts / N
+    Stations st;          // station ranges: buckets never cross them
 };
 
 __device__ __forceinline__ bool pair_live(const EnumArgs &a, uint32_t i, uint32_t j) {
@@ -126,21 +131,23 @@ __global__ void __launch_bounds__(256) k_enum(EnumArgs a, uint4 *__restrict__ bi
     const uint32_t *k = a.skey + (uint64_t)t * N;
     const uint32_t *s = a.sid + (uint64_t)t * N;
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t sx = station_of(a.st, p);
+        const uint64_t s0 = a.st.soff[sx], s1 = a.st.soff[sx + 1];
         const uint32_t key = k[p];
-        if (p > 0 && k[p - 1] == key) continue;
+        if (p > s0 && k[p - 1] == key) continue;
         uint64_t e = p + 1;
-        while (e < N && e - p <= kSmall && k[e] == key) e++;
+        while (e < s1 && e - p <= kSmall && k[e] == key) e++;
         if (e - p == 1) continue;
         if (e - p > kSmall) {
             if (MODE == 0) {
                 uint64_t lo = e - 1, step = 1, hi;
                 for (;;) {
                     hi = lo + step;
-                    if (hi >= N || k[hi] != key) break;
+                    if (hi >= s1 || k[hi] != key) break;
                     lo = hi;
                     step <<= 1;
                 }
-                if (hi > N) hi = N;
+                if (hi > s1) hi = s1;
                 while (hi - lo > 1) {
                     uint64_t mid = lo + (hi - lo) / 2;
                     if (k[mid] == key) lo = mid;
@@ -586,12 +593,14 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
     const uint32_t *s = a.sid + (uint64_t)t * N;
     const uint32_t lmask = (1u << gshift) - 1;
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t sx = station_of(a.st, x);
+        const uint64_t lo_b = a.st.soff[sx], hi_b = a.st.soff[sx + 1];
         const uint32_t key = k[x];
         uint64_t s0 = x;
-        while (s0 > 0 && x - s0 < kSmall && k[s0 - 1] == key) s0--;
+        while (s0 > lo_b && x - s0 < kSmall && k[s0 - 1] == key) s0--;
         if (x - s0 >= kSmall) continue;  // at least kSmall + 1 entries: a big bucket
         uint64_t e = x + 1;
-        while (e < N && e - s0 <= kSmall && k[e] == key) e++;
+        while (e < hi_b && e - s0 <= kSmall && k[e] == key) e++;
         if (e - s0 > kSmall || e - x == 1) continue;
         const uint32_t i = s[x];
         if (a.drop[i]) continue;
@@ -1103,10 +1112,12 @@ __global__ void __launch_bounds__(256) k_find_big(EnumArgs a, uint4 *__restrict_
     const uint32_t *k = a.skey + (uint64_t)t * N;
     unsigned long long pairs = 0;
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t sx = station_of(a.st, p);
+        const uint64_t s0 = a.st.soff[sx], s1 = a.st.soff[sx + 1];
         const uint32_t key = k[p];
-        if (p > 0 && k[p - 1] == key) continue;
+        if (p > s0 && k[p - 1] == key) continue;
         uint64_t e = p + 1;
-        while (e < N && e - p <= kSmall && k[e] == key) e++;
+        while (e < s1 && e - p <= kSmall && k[e] == key) e++;
         if (e - p <= kSmall) {  // small bucket: its pairs bound the sparse work
             pairs += (e - p) * (e - p - 1) / 2;
             continue;
@@ -1114,11 +1125,11 @@ __global__ void __launch_bounds__(256) k_find_big(EnumArgs a, uint4 *__restrict_
         uint64_t lo = p + kSmall, step = 1, hi;
         for (;;) {
             hi = lo + step;
-            if (hi >= N || k[hi] != key) break;
+            if (hi >= s1 || k[hi] != key) break;
             lo = hi;
             step <<= 1;
         }
-        if (hi > N) hi = N;
+        if (hi > s1) hi = s1;
         while (hi - lo > 1) {
             uint64_t mid = lo + (hi - lo) / 2;
             if (k[mid] == key) lo = mid;
@@ -1138,12 +1149,17 @@ uint32_t bits_for(uint64_t N) {
     return nb;
 }
 
-struct Scal {  // device scalar slots (ctx->d_scal)
-    enum { NBIG, NLARGE, NMEDIUM, NHEAVY, NDROP, NMEMB, CUR_DENSE, CUR_SPARSE, CHANGED, NLONG, NMERGE, NMERGE_TOT,
-           NCAND, NMID, SMALLPAIRS, PART0 };
-};
 
 }  // namespace
+
+// large_min: above the largest bucket the random background makes.  The most
+// likely key of a table has probability ~(K/D)^r, so the background tops out
+// near N (K/D)^r members; take 8x that, at least 512.
+uint32_t large_min_for(const fast_ctx *c, uint64_t N) {
+    if (c->large_min) return c->large_min;
+    const double ptop = std::pow((double)c->p.K / c->p.D, (double)c->p.r);
+    return (uint32_t)std::max(512.0, std::min(1e9, 8.0 * N * ptop));
+}
 
 // ------------------------------------------------------------ host side
 
@@ -1155,8 +1171,11 @@ fast_status filter_launch(fast_ctx *c, fast_tables *tb, cudaStream_t s) {
     cudaMemsetAsync(scal, 0, sizeof(uint64_t) * kScal, s);
     uint32_t *heavy = nullptr;
     if (p.occ_num > 0 && N > 0) {
-        const uint64_t smin = (uint64_t)p.occ_num * N / p.occ_den + 1;  // heavy iff size >= smin
-        const uint64_t cap = (uint64_t)p.b * (N / smin + 1);
+        uint64_t smin = ~0ull;  // smallest heavy size over the stations
+        for (uint32_t x = 0; x < tb->nst; x++)
+            if (tb->soff[x + 1] > tb->soff[x])
+                smin = std::min<uint64_t>(smin, (uint64_t)p.occ_num * (tb->soff[x + 1] - tb->soff[x]) / p.occ_den + 1);
+        const uint64_t cap = (uint64_t)p.b * (N / smin + tb->nst);
         if (cap > (1ull << 26)) return set_error(c, FAST_EBUDGET, "occurrence threshold too small for this N");
         uint4 *list = nullptr;
         if ((st = dalloc_t(c, &heavy, N, s))) return st;
@@ -1166,7 +1185,8 @@ fast_status filter_launch(fast_ctx *c, fast_tables *tb, cudaStream_t s) {
         }
         cudaMemsetAsync(heavy, 0, N * 4, s);
         dim3 g(std::max(1u, std::min<unsigned>(ceil_div(N, 256), 4096)), p.b);
-        k_heavy_find<<<g, 256, 0, s>>>(tb->d_skey, N, smin, list, scal + Scal::NHEAVY, cap, c->d_err), FAST_LAUNCHED(c);
+        k_heavy_find<<<g, 256, 0, s>>>(tb->d_skey, N, Stations{tb->d_soff, tb->nst}, p.occ_num, p.occ_den, list,
+                                       scal + Scal::NHEAVY, cap, c->d_err), FAST_LAUNCHED(c);
         k_heavy_mark<<<c->num_sms * 4, 256, 0, s>>>(list, scal + Scal::NHEAVY, cap, tb->d_sid, N, heavy), FAST_LAUNCHED(c);
         dfree(c, list, cap * sizeof(uint4), s);
     }
@@ -1175,6 +1195,7 @@ fast_status filter_launch(fast_ctx *c, fast_tables *tb, cudaStream_t s) {
     if (heavy) dfree(c, heavy, N * 4, s);
     cudaError_t e = cudaGetLastError();
     if (e) return cuda_fail(c, e, "filter");
+    if (c->capturing) return FAST_OK;  // the plan reads the counters after the graph runs
     cudaMemcpyAsync(c->h_scal, c->d_scal, sizeof(uint64_t) * kScal, cudaMemcpyDeviceToHost, s);
     if ((st = sync_check(c, s, "occurrence filter"))) return st;
     tb->n_dropped = c->h_scal[Scal::NDROP];
@@ -1215,14 +1236,7 @@ static fast_status search_map(fast_ctx *c, const fast_tables *tb, const uint32_t
     c->stats.n_fingerprints = N;
     c->stats.n_dropped = tb->n_dropped;
 
-    // large_min: above the largest bucket the random background makes.  The
-    // most likely key of a table has probability ~(K/D)^r, so the background
-    // tops out near N (K/D)^r members; take 8x that, at least 512.
-    uint32_t large_min = c->large_min;
-    if (!large_min) {
-        double ptop = std::pow((double)p.K / p.D, (double)p.r);
-        large_min = (uint32_t)std::max(512.0, std::min(1e9, 8.0 * N * ptop));
-    }
+    const uint32_t large_min = large_min_for(c, N);
 
     uint32_t nparts = p.query_part ? p.query_part : 1;
     nparts = std::min<uint32_t>(nparts, 64);
@@ -1233,7 +1247,7 @@ static fast_status search_map(fast_ctx *c, const fast_tables *tb, const uint32_t
     const uint64_t big_cap = (uint64_t)nb * (N / (kSmall + 1) + 1);
     uint4 *big = nullptr, *large = nullptr, *medium = nullptr;
     if ((st = alloc(&big, big_cap))) return fail(st);
-    EnumArgs ea{tb->d_skey, tb->d_sid, tb->d_drop, nullptr, N, p.excl, 0, (uint32_t)N, nparts};
+    EnumArgs ea{tb->d_skey, tb->d_sid, tb->d_drop, nullptr, N, p.excl, 0, (uint32_t)N, nparts, {tb->d_soff, tb->nst}};
     Map nomap{nullptr, 0};
     const dim3 eg(std::max(1u, std::min<unsigned>(ceil_div(N, 256), 2048)), nb);
     k_enum<0><<<eg, 256, 0, s>>>(ea, big, scal + Scal::NBIG, big_cap, scal + Scal::PART0, nomap, c->d_err), FAST_LAUNCHED(c);
@@ -1519,11 +1533,7 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
     c->stats.n_fingerprints = N;
     c->stats.n_dropped = tb->n_dropped;
     c->stats.n_long_rows = c->stats.n_huge_rows = c->stats.max_row = 0;
-    uint32_t large_min = c->large_min;
-    if (!large_min) {
-        double ptop = std::pow((double)p.K / p.D, (double)p.r);
-        large_min = (uint32_t)std::max(512.0, std::min(1e9, 8.0 * N * ptop));
-    }
+    const uint32_t large_min = large_min_for(c, N);
     const unsigned blocksN = std::max(1u, std::min<unsigned>(ceil_div(N, 256), c->num_sms * 8));
 
     // ---- big buckets
@@ -1532,7 +1542,7 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
     const uint64_t big_cap = (uint64_t)nb * (N / (kSmall + 1) + 1);
     uint4 *big = nullptr, *large = nullptr, *medium = nullptr;
     if ((st = alloc(&big, big_cap))) return fail(st);
-    EnumArgs ea{tb->d_skey, tb->d_sid, tb->d_drop, nullptr, N, p.excl, 0, (uint32_t)N, 1};
+    EnumArgs ea{tb->d_skey, tb->d_sid, tb->d_drop, nullptr, N, p.excl, 0, (uint32_t)N, 1, {tb->d_soff, tb->nst}};
     const dim3 eg(std::max(1u, std::min<unsigned>(ceil_div(N, 256), 2048)), nb);
     k_find_big<<<eg, 256, 0, s>>>(ea, big, scal + Scal::NBIG, big_cap, scal + Scal::SMALLPAIRS, c->d_err),
         FAST_LAUNCHED(c);
@@ -1746,11 +1756,7 @@ fast_status history_groups(fast_ctx *c, const fast_tables *tb, const uint32_t *d
     unsigned long long *scal = reinterpret_cast<unsigned long long *>(c->d_scal);
     fast_status st;
     *g = HistGroups{};
-    uint32_t large_min = c->large_min;
-    if (!large_min) {
-        double ptop = std::pow((double)p.K / p.D, (double)p.r);
-        large_min = (uint32_t)std::max(512.0, std::min(1e9, 8.0 * N * ptop));
-    }
+    const uint32_t large_min = large_min_for(c, N);
     g->large_min = large_min;
     auto dev = [&](auto **ptr, size_t count) -> fast_status {
         cudaError_t e = cudaMalloc(ptr, std::max<size_t>(count, 1) * sizeof(**ptr));
@@ -1766,7 +1772,7 @@ fast_status history_groups(fast_ctx *c, const fast_tables *tb, const uint32_t *d
     uint4 *big = nullptr, *large = nullptr, *medium = nullptr;
     if ((st = dalloc_t(c, &big, big_cap, s))) return st;
     cudaMemsetAsync(scal, 0, sizeof(uint64_t) * kScal, s);
-    EnumArgs ea{tb->d_skey, tb->d_sid, tb->d_drop, nullptr, N, p.excl, 0, (uint32_t)N, 1};
+    EnumArgs ea{tb->d_skey, tb->d_sid, tb->d_drop, nullptr, N, p.excl, 0, (uint32_t)N, 1, {tb->d_soff, tb->nst}};
     const dim3 eg(std::max(1u, std::min<unsigned>(ceil_div(N, 256), 2048)), nb);
     k_find_big<<<eg, 256, 0, s>>>(ea, big, scal + Scal::NBIG, big_cap, scal + Scal::SMALLPAIRS, c->d_err),
         FAST_LAUNCHED(c);

@@ -34,9 +34,11 @@ __device__ __forceinline__ uint32_t digit_of(KT k, uint32_t shift) {
     return (uint32_t)(k >> shift) & (kRadix - 1);
 }
 
-template <typename KT>
+template <typename KT, bool STD = false>
 __global__ void __launch_bounds__(kThreads) k_hist(const KT *__restrict__ keys, uint64_t len, uint32_t nchunks,
-                                                   uint32_t shift, uint32_t *__restrict__ counts) {
+                                                   uint32_t shift, uint32_t *__restrict__ counts,
+                                                   const uint32_t *__restrict__ vals = nullptr,
+                                                   Stations S = Stations{nullptr, 1}) {
     __shared__ uint32_t h[kWarps][kRadix];
     const uint32_t seg = blockIdx.y, chunk = blockIdx.x;
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&h[0][0])[i] = 0;
@@ -44,7 +46,9 @@ __global__ void __launch_bounds__(kThreads) k_hist(const KT *__restrict__ keys, 
     const KT *k = keys + (uint64_t)seg * len;
     const uint64_t lo = (uint64_t)chunk * kChunk, hi = std::min<uint64_t>(lo + kChunk, len);
     const int warp = threadIdx.x >> 5;
-    for (uint64_t e = lo + threadIdx.x; e < hi; e += kThreads) atomicAdd(&h[warp][digit_of(k[e], shift)], 1u);
+    const uint32_t *vv = STD ? vals + (uint64_t)seg * len : nullptr;
+    for (uint64_t e = lo + threadIdx.x; e < hi; e += kThreads)
+        atomicAdd(&h[warp][STD ? station_of(S, vv[e]) : digit_of(k[e], shift)], 1u);
     __syncthreads();
     uint32_t d = threadIdx.x, tot = 0;
 #pragma unroll
@@ -90,11 +94,12 @@ __global__ void __launch_bounds__(1024) k_scan(const uint32_t *__restrict__ coun
     }
 }
 
-template <typename KT, bool HAS_VAL, bool IOTA>
+template <typename KT, bool HAS_VAL, bool IOTA, bool STD = false>
 __global__ void __launch_bounds__(kThreads) k_scatter(const KT *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                       KT *__restrict__ kout, uint32_t *__restrict__ vout, uint64_t len,
                                                       uint32_t nchunks, uint32_t shift,
-                                                      const uint64_t *__restrict__ offsets) {
+                                                      const uint64_t *__restrict__ offsets,
+                                                      Stations S = Stations{nullptr, 1}) {
     __shared__ uint64_t run[kRadix];
     __shared__ uint32_t wcnt[kWarps][kRadix];
     __shared__ uint32_t tot[kRadix], dstart[kRadix], wscan[kWarps];
@@ -126,7 +131,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const KT *__restrict__ kin
             const bool valid = e < nvalid;
             key[j] = valid ? ki[sbase + e] : (KT)0;
             if (HAS_VAL) val[j] = valid ? (IOTA ? (uint32_t)(sbase + e) : vi[sbase + e]) : 0u;
-            dig[j] = valid ? digit_of(key[j], shift) : (uint32_t)kRadix;
+            dig[j] = valid ? (STD ? station_of(S, val[j]) : digit_of(key[j], shift)) : (uint32_t)kRadix;
             const uint32_t peers = __match_any_sync(~0u, dig[j]);
             const uint32_t before = peers & lt_mask;
             uint32_t basec = 0;
@@ -172,7 +177,9 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const KT *__restrict__ kin
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < nvalid; i += kThreads) {
             KT k = sk[i];
-            uint32_t d = digit_of(k, shift);
+            uint32_t d;
+            if constexpr (STD) d = station_of(S, sv[i]);
+            else d = digit_of(k, shift);
             uint64_t o = run[d] + (i - dstart[d]);
             ko[o] = k;
             if (HAS_VAL) vo[o] = sv[i];
@@ -242,6 +249,32 @@ fast_status sort_u32(fast_ctx *c, uint32_t nseg, uint64_t len, const uint32_t *k
                      uint32_t bit1, uint32_t **keys_out, uint32_t **vals_out, cudaStream_t s, uint32_t *passes) {
     return sort_impl<uint32_t, true>(c, nseg, len, keys_in, vals_in, keys_a, vals_a, keys_b, vals_b, bit0, bit1,
                                      keys_out, vals_out, s, passes);
+}
+
+fast_status sort_station_pass(fast_ctx *c, uint32_t nseg, uint64_t len, const uint32_t *keys_in, const uint32_t *vals_in,
+                              uint32_t *keys_out, uint32_t *vals_out, Stations S, cudaStream_t s) {
+    if (len == 0 || nseg == 0) return FAST_OK;
+    const uint32_t nchunks = (uint32_t)((len + kChunk - 1) / kChunk);
+    const size_t entries = (size_t)nseg * kRadix * nchunks;
+    uint32_t *counts = nullptr;
+    uint64_t *offs = nullptr;
+    fast_status st;
+    if ((st = dalloc_t(c, &counts, entries, s))) return st;
+    if ((st = dalloc_t(c, &offs, entries, s))) {
+        dfree(c, counts, entries * 4, s);
+        return st;
+    }
+    const dim3 grid(nchunks, nseg);
+    k_hist<uint32_t, true><<<grid, kThreads, 0, s>>>(keys_in, len, nchunks, 0, counts, vals_in, S), FAST_LAUNCHED(c);
+    st = scan_excl(c, counts, offs, (uint64_t)kRadix * nchunks, nseg, nullptr, s);
+    if (!st)
+        k_scatter<uint32_t, true, false, true><<<grid, kThreads, 0, s>>>(keys_in, vals_in, keys_out, vals_out, len,
+                                                                         nchunks, 0, offs, S), FAST_LAUNCHED(c);
+    dfree(c, counts, entries * 4, s);
+    dfree(c, offs, entries * 8, s);
+    if (st) return st;
+    cudaError_t e = cudaGetLastError();
+    return e ? cuda_fail(c, e, "station pass") : FAST_OK;
 }
 
 fast_status sort_u64(fast_ctx *c, uint64_t len, uint64_t *keys_a, uint64_t *keys_b, uint32_t bit0, uint32_t bit1,

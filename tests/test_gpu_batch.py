@@ -1,0 +1,77 @@
+"""Batched multi-station search (one pass over uneven stations) vs per-station results (GPU)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1803_09835_gb300 import _build
+    _build.build()
+    assert torch.cuda.is_available()
+
+
+def _stations(lengths, **over):
+    ws = [synth.scaled("c2", n, station=s, **over) for s, n in enumerate(lengths)]
+    return ws, [synth.generate(w, ld=((w.K + 7) // 8) * 8) for w in ws]
+
+
+def _eq(a, b):
+    return all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+@pytest.mark.parametrize("opts", [{}, {"large_min": 16}, {"vote_map": 1}])
+def test_uneven_stations_equal_single_station_runs(opts):
+    from paper_1803_09835_gb300 import Searcher
+    lengths = [s * 1500 for s in range(1, 13)]
+    ws, idx = _stations(lengths, D=2048, K=100, b=30)
+    p = ws[0].params()
+    s = Searcher(p, **opts)
+    batch = s.detect_batch(torch.from_numpy(np.concatenate(idx)).cuda(), lengths)
+    for x, (w, a) in enumerate(zip(ws, idx)):
+        keys = oracle.keys(p, np.ascontiguousarray(a[:, :w.K]))
+        want = oracle.search(p, keys, oracle.drop(p, keys))
+        got = batch[x].numpy()
+        assert _eq(got, want), f"station {x}"
+        alone = s.detect(torch.from_numpy(a).cuda())
+        assert _eq(alone.numpy(), got)
+        alone.free()
+    for r in batch:
+        r.free()
+    s.close()
+
+
+def test_equal_keys_across_a_station_boundary():
+    # station 1 repeats station 0 window for window: the last keys of one
+    # station equal the first keys of the next, and buckets must not merge
+    from paper_1803_09835_gb300 import Searcher
+    ws, idx = _stations([3000], D=2048, K=100, b=20)
+    a = idx[0]
+    p = ws[0].params()
+    s = Searcher(p)
+    batch = s.detect_batch(torch.from_numpy(np.concatenate([a, a, a[:1000]])).cuda(), [3000, 3000, 1000])
+    keys = oracle.keys(p, np.ascontiguousarray(a[:, :100]))
+    want = oracle.search(p, keys, oracle.drop(p, keys))
+    assert _eq(batch[0].numpy(), want) and _eq(batch[1].numpy(), want)
+    k2 = np.ascontiguousarray(keys[:, :1000])
+    assert _eq(batch[2].numpy(), oracle.search(p, k2, oracle.drop(p, k2)))
+    s.close()
+
+
+def test_batch_of_one_and_empty_stations():
+    from paper_1803_09835_gb300 import Searcher
+    ws, idx = _stations([2500], D=2048, K=100, b=20)
+    p = ws[0].params()
+    s = Searcher(p)
+    a = torch.from_numpy(idx[0]).cuda()
+    one = s.detect_batch(a, [2500])[0].numpy()
+    ref = s.detect(a).numpy()
+    assert _eq(one, ref)
+    parts = s.detect_batch(a, [0, 2500, 0])
+    assert parts[0].M == 0 and parts[2].M == 0 and _eq(parts[1].numpy(), ref)
+    s.close()
