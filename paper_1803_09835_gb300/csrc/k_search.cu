@@ -581,45 +581,91 @@ __device__ __forceinline__ PT pack_entry(uint32_t local, uint32_t j, uint32_t nb
     return ((PT)local << nbits) | (PT)j;
 }
 
-// Small buckets (at most kSmall entries, dropped ones included): one thread
-// per table position x pairs x with every later entry of its bucket.
+// Small buckets (at most kSmall entries, dropped ones included).  A warp walks
+// a run of 32-entry tiles of one table with a window of three tiles in
+// registers -- previous (bucket heads only), current and next -- so every key,
+// id, drop flag and group label is loaded once.  Lane L owns position L of the
+// current tile and pairs it with the later entries of its bucket, which lie in
+// the current or the next tile (a small bucket spans at most 32 positions);
+// their ids and labels come by shuffle.  Bucket bounds come from the head
+// bitmasks: a head is a position whose key differs from its predecessor's, or
+// the first position of a station.
+constexpr uint32_t kLabDrop = 0xFFFFFFFEu;  // window label of a dropped (or absent) entry
+
+struct PairWin {
+    uint32_t id, lab, heads;
+};
+
+__device__ __forceinline__ PairWin pair_tile(const EnumArgs &a, const uint32_t *__restrict__ K,
+                                             const uint32_t *__restrict__ S, uint64_t T) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t x = T * 32 + lane, N = a.N;
+    const bool valid = x < N;
+    const uint32_t key = valid ? K[x] : 0u;
+    uint32_t kprev = __shfl_up_sync(~0u, key, 1);
+    if (lane == 0 && valid && x > 0) kprev = K[x - 1];
+    bool head = !valid || x == 0 || key != kprev;
+    if (a.st.nst > 1 && valid && !head) head = a.st.soff[station_of(a.st, x)] == x;
+    PairWin w;
+    w.heads = __ballot_sync(~0u, head);
+    w.id = valid ? S[x] : 0u;
+    w.lab = kLabDrop;
+    if (valid && !a.drop[w.id]) w.lab = a.label ? __ldg(a.label + w.id) : kNone;
+    return w;
+}
+
 template <int MODE, typename PT>
-__global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, uint32_t nbits,
+__global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, uint32_t nbits, uint32_t tiles_per_warp,
                                                    uint32_t *__restrict__ gcnt, const uint64_t *__restrict__ goff,
                                                    uint32_t *__restrict__ gcur, PT *__restrict__ ent) {
-    const uint32_t t = blockIdx.y;
-    const uint64_t N = a.N;
-    const uint32_t *k = a.skey + (uint64_t)t * N;
-    const uint32_t *s = a.sid + (uint64_t)t * N;
+    const uint32_t t = blockIdx.y, lane = threadIdx.x & 31;
+    const uint64_t N = a.N, ntiles = (N + 31) / 32;
+    const uint32_t *K = a.skey + (uint64_t)t * N;
+    const uint32_t *S = a.sid + (uint64_t)t * N;
     const uint32_t lmask = (1u << gshift) - 1;
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t sx = station_of(a.st, x);
-        const uint64_t lo_b = a.st.soff[sx], hi_b = a.st.soff[sx + 1];
-        const uint32_t key = k[x];
-        uint64_t s0 = x;
-        while (s0 > lo_b && x - s0 < kSmall && k[s0 - 1] == key) s0--;
-        if (x - s0 >= kSmall) continue;  // at least kSmall + 1 entries: a big bucket
-        uint64_t e = x + 1;
-        while (e < hi_b && e - s0 <= kSmall && k[e] == key) e++;
-        if (e - s0 > kSmall || e - x == 1) continue;
-        const uint32_t i = s[x];
-        if (a.drop[i]) continue;
-        uint32_t c = 0;
-        for (uint64_t y = x + 1; y < e; y++) {
-            const uint32_t j = s[y];
-            c += !a.drop[j] && pair_live(a, i, j);
+    const uint64_t T0 = ((uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32) * tiles_per_warp;
+    if (T0 >= ntiles) return;  // warp-uniform
+    const uint64_t T1 = min(T0 + tiles_per_warp, ntiles);
+    uint32_t hp = T0 ? pair_tile(a, K, S, T0 - 1).heads : ~0u;
+    PairWin c = pair_tile(a, K, S, T0);
+    for (uint64_t T = T0; T < T1; T++) {
+        const PairWin n = pair_tile(a, K, S, T + 1);
+        // bucket of position L: first position s0 (window coordinates, previous
+        // tile = 0..31) and end e (coordinates of current + next = 0..63)
+        const uint64_t hpc = (uint64_t)c.heads << 32 | hp;
+        const uint64_t hcn = (uint64_t)n.heads << 32 | c.heads;
+        const uint64_t below = hpc & (lane == 31 ? ~0ull : (2ull << (32 + lane)) - 1);
+        const uint64_t above = hcn & ~((2ull << lane) - 1);
+        const int s0 = below ? 63 - __clzll((long long)below) : -1;
+        const int e = above ? __ffsll((long long)above) - 1 : 64;
+        const bool act = s0 >= 0 && e < 64 && e + 32 - s0 <= (int)kSmall && e > (int)lane + 1 && c.lab != kLabDrop;
+        const uint32_t dmax = __reduce_max_sync(~0u, act ? (uint32_t)(e - (int)lane - 1) : 0u);
+        const uint32_t i = c.id;
+        uint32_t cnt = 0;
+        for (uint32_t d = 1; d <= dmax; d++) {
+            const uint32_t src = (lane + d) & 31;
+            const uint32_t jc = __shfl_sync(~0u, c.id, src), jn = __shfl_sync(~0u, n.id, src);
+            const uint32_t lc = __shfl_sync(~0u, c.lab, src), ln = __shfl_sync(~0u, n.lab, src);
+            const bool inc = lane + d < 32;
+            const uint32_t j = inc ? jc : jn, lj = inc ? lc : ln;
+            cnt += act && (int)(lane + d) < e && lj != kLabDrop && j - i > a.excl && (c.lab == kNone || c.lab != lj);
         }
-        if (!c) continue;
-        const uint32_t g = i >> gshift;
         if (MODE == 0) {
-            atomicAdd(gcnt + g, c);
-        } else {
-            uint64_t o = goff[g] + atomicAdd(gcur + g, c);
-            for (uint64_t y = x + 1; y < e; y++) {
-                const uint32_t j = s[y];
-                if (!a.drop[j] && pair_live(a, i, j)) ent[o++] = pack_entry<PT>(i & lmask, j, nbits);
+            if (cnt) atomicAdd(gcnt + (i >> gshift), cnt);
+        } else if (__any_sync(~0u, cnt != 0)) {
+            uint64_t o = cnt ? goff[i >> gshift] + atomicAdd(gcur + (i >> gshift), cnt) : 0;
+            for (uint32_t d = 1; d <= dmax; d++) {
+                const uint32_t src = (lane + d) & 31;
+                const uint32_t jc = __shfl_sync(~0u, c.id, src), jn = __shfl_sync(~0u, n.id, src);
+                const uint32_t lc = __shfl_sync(~0u, c.lab, src), ln = __shfl_sync(~0u, n.lab, src);
+                const bool inc = lane + d < 32;
+                const uint32_t j = inc ? jc : jn, lj = inc ? lc : ln;
+                if (cnt && (int)(lane + d) < e && lj != kLabDrop && j - i > a.excl && (c.lab == kNone || c.lab != lj))
+                    ent[o++] = pack_entry<PT>(i & lmask, j, nbits);
             }
         }
+        hp = c.heads;
+        c = n;
     }
 }
 
@@ -723,9 +769,11 @@ size_t group_vote_smem() {
     return (size_t)2 * kVCap * sizeof(PT) + (size_t)2 * kVCap / 4 * 4;
 }
 
-template <typename PT>
-__device__ __forceinline__ uint32_t ghash(PT key) {
-    return (uint32_t)(mix64((uint64_t)key) >> 32);
+// Slot of a key in a table of 2^lg slots: multiplicative (Fibonacci) hashing,
+// top lg bits of key * 2^w / golden ratio; 64-bit keys are mixed first.
+__device__ __forceinline__ uint32_t ghash(uint32_t key, uint32_t lg) { return (key * 0x9E3779B1u) >> (32 - lg); }
+__device__ __forceinline__ uint32_t ghash(unsigned long long key, uint32_t lg) {
+    return (uint32_t)(mix64(key) >> (64 - lg));
 }
 
 // One CTA per group: every entry (local row, j) of the group counted in one
@@ -737,7 +785,6 @@ __global__ void __launch_bounds__(256) k_group_vote(VoteArgs A, const PT *__rest
     PT *K = reinterpret_cast<PT *>(vsm_raw);                             // [<= 2 kVCap] keys (entry + 1)
     uint32_t *C = reinterpret_cast<uint32_t *>(K + 2 * kVCap);           // [<= 2 kVCap / 4] byte counts
     __shared__ uint32_t wsum[32];
-    __shared__ uint32_t s_nk;
     __shared__ unsigned long long s_b0;
     const PT jmask = ((PT)1 << A.nbits) - 1;
     for (uint64_t g = blockIdx.x; g < A.ngroups; g += gridDim.x) {
@@ -752,14 +799,14 @@ __global__ void __launch_bounds__(256) k_group_vote(VoteArgs A, const PT *__rest
             }
             continue;
         }
-        uint32_t slots = 64;
-        while (slots < 2 * n) slots <<= 1;
+        uint32_t slots = 64, lg = 6;
+        while (slots < 2 * n) slots <<= 1, lg++;
         for (uint32_t x = threadIdx.x; x < slots; x += blockDim.x) K[x] = 0;
         for (uint32_t x = threadIdx.x; x < slots / 4; x += blockDim.x) C[x] = 0;
         __syncthreads();
         for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) {
             const PT want = ent[e0 + x] + 1;
-            uint32_t h = ghash(want) & (slots - 1);
+            uint32_t h = ghash(want, lg);
             for (uint32_t probe = 0; probe < slots; probe++) {
                 PT kk = K[h];
                 if (kk == 0) {
@@ -774,49 +821,63 @@ __global__ void __launch_bounds__(256) k_group_vote(VoteArgs A, const PT *__rest
             }
         }
         __syncthreads();
-        // kept entries compacted to the front: key into K, votes into count bytes
-        if (threadIdx.x == 0) s_nk = 0;
-        __syncthreads();
-        for (uint32_t base = 0; base < slots; base += blockDim.x) {
-            const uint32_t x = base + threadIdx.x;
+        // kept entries compacted to the front of each warp's slot segment (a
+        // kept slot's new position never exceeds its old one, and every lane
+        // reads its slot before the ballot, so no unread slot is overwritten)
+        const uint32_t nw = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+        const uint32_t seg = slots / nw, lo = warp * seg;
+        uint32_t wn = 0;
+        for (uint32_t base = lo; base < lo + seg; base += 32) {
+            const uint32_t x = base + lane;
             PT kk = 0;
             uint32_t cc = 0;
-            if (x < slots) {
+            if (x < lo + seg) {
                 kk = K[x];
                 cc = (C[x >> 2] >> (8 * (x & 3))) & 0xFF;
             }
-            const uint32_t keep = kk != 0 && cc >= A.v;
-            uint32_t tot;
-            const uint32_t pos = s_nk + block_excl_scan(keep, wsum, &tot);
-            __syncthreads();
-            if (keep) {  // pos <= x: never overwrites an unread slot
+            const bool keep = kk != 0 && cc >= A.v;
+            const uint32_t m = __ballot_sync(~0u, keep);
+            if (keep) {
+                const uint32_t pos = lo + wn + __popc(m & ((1u << lane) - 1));
                 K[pos] = kk - 1;
                 reinterpret_cast<uint8_t *>(C)[pos] = (uint8_t)cc;
             }
-            __syncthreads();
-            if (threadIdx.x == 0) s_nk += tot;
-            __syncthreads();
+            wn += __popc(m);
         }
-        const uint32_t nk = s_nk;
-        if (!nk) continue;  // block-uniform
+        if (lane == 0) wsum[warp] = wn;
+        __syncthreads();
+        uint32_t nk = 0;
+        for (uint32_t w = 0; w < nw; w++) nk += wsum[w];
+        if (!nk) {  // block-uniform
+            __syncthreads();
+            continue;
+        }
         if (threadIdx.x == 0) s_b0 = atomicAdd(A.sp_cursor, (unsigned long long)nk);
         __syncthreads();
         const uint64_t b0 = s_b0;
         const uint8_t *V = reinterpret_cast<const uint8_t *>(C);
-        for (uint32_t x = threadIdx.x; x < nk; x += blockDim.x) {
-            const PT kx = K[x];
-            uint32_t rank = 0, first = 1;
-            for (uint32_t y = 0; y < nk; y++) {
-                rank += K[y] < kx;
-                first &= (uint32_t)((K[y] >> A.nbits) != (kx >> A.nbits) || K[y] >= kx);
+        // each kept entry's rank among the group's kept entries = its place in (i, j) order
+        for (uint32_t w = 0; w < nw; w++) {
+            for (uint32_t q = threadIdx.x; q < wsum[w]; q += blockDim.x) {
+                const uint32_t x = w * seg + q;
+                const PT kx = K[x];
+                uint32_t rank = 0, first = 1;
+                for (uint32_t w2 = 0; w2 < nw; w2++) {
+                    const PT *Kw = K + w2 * seg;
+                    for (uint32_t y = 0, ny = wsum[w2]; y < ny; y++) {
+                        const PT ky = Kw[y];
+                        rank += ky < kx;
+                        first &= (uint32_t)((ky >> A.nbits) != (kx >> A.nbits) || ky >= kx);
+                    }
+                }
+                const uint64_t i = row0 + (uint32_t)(kx >> A.nbits);
+                if (b0 + nk <= A.sp_cap) {
+                    A.sp_j[b0 + rank] = (uint32_t)(kx & jmask);
+                    A.sp_v[b0 + rank] = V[x];
+                }
+                atomicAdd(A.sp_cnt + i, 1u);
+                if (first) A.sp_start[i] = b0 + rank;  // the row's smallest j
             }
-            const uint64_t i = row0 + (uint32_t)(kx >> A.nbits);
-            if (b0 + nk <= A.sp_cap) {
-                A.sp_j[b0 + rank] = (uint32_t)(kx & jmask);
-                A.sp_v[b0 + rank] = V[x];
-            }
-            atomicAdd(A.sp_cnt + i, 1u);
-            if (first) A.sp_start[i] = b0 + rank;  // the row's smallest j
         }
         __syncthreads();
     }
@@ -1427,9 +1488,14 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     if ((st = alloc(&gcnt, ng)) || (st = alloc(&gcur, ng)) || (st = alloc(&goff, ng + 1))) return st;
     cudaMemsetAsync(gcnt, 0, ng * 4, s);
     cudaMemsetAsync(gcur, 0, ng * 4, s);
-    const dim3 eg(std::max(1u, std::min<unsigned>(ceil_div(N, 256), 2048)), p.b);
+    // small-bucket pairs: warps over runs of 32-entry tiles, about 16 warps per SM slot in all
+    const uint64_t ntiles = (N + 31) / 32;
+    const uint32_t tpw = (uint32_t)std::max<uint64_t>(
+        1, std::min<uint64_t>(64, ntiles * p.b / ((uint64_t)c->num_sms * 64 * 16)));
+    const uint64_t nwarps = (ntiles + tpw - 1) / tpw;
+    const dim3 eg((unsigned)std::max<uint64_t>(1, (nwarps + 7) / 8), p.b);
     const unsigned mg = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(nmedium, c->num_sms * 8));
-    k_pairs_grp<0, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, gcnt, nullptr, nullptr, nullptr), FAST_LAUNCHED(c);
+    k_pairs_grp<0, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, tpw, gcnt, nullptr, nullptr, nullptr), FAST_LAUNCHED(c);
     if (nmedium)
         k_medium_grp<0, PT><<<mg, 256, 0, s>>>(ea, medium, scal + Scal::NMEDIUM, gshift, nbits, gcnt, nullptr, nullptr,
                                                nullptr), FAST_LAUNCHED(c);
@@ -1439,7 +1505,7 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     if ((st = sync_check(c, s, "pair count"))) return st;
     S_out = S;
     if ((st = alloc(&ent, S))) return st;
-    k_pairs_grp<1, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, nullptr, goff, gcur, ent), FAST_LAUNCHED(c);
+    k_pairs_grp<1, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, tpw, nullptr, goff, gcur, ent), FAST_LAUNCHED(c);
     if (nmedium)
         k_medium_grp<1, PT><<<mg, 256, 0, s>>>(ea, medium, scal + Scal::NMEDIUM, gshift, nbits, nullptr, goff, gcur,
                                                ent), FAST_LAUNCHED(c);
@@ -1639,7 +1705,8 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
         const uint32_t nbits = bits_for(N);
         uint32_t gshift = 0;
         while (gshift < 12 && (double)(2ull << gshift) * avg <= kVTarget) gshift++;
-        const fast_status r = gshift + nbits <= 32
+        // 32-bit entries while entry + 1 cannot wrap to the empty key
+        const fast_status r = gshift + nbits < 32
                                   ? sparse_groups<uint32_t>(c, ea, medium, nmedium, gshift, nbits, sp_cnt, sp_start,
                                                             &sp_j, &sp_v, long_rows, S, alloc, s)
                                   : sparse_groups<unsigned long long>(c, ea, medium, nmedium, gshift, nbits, sp_cnt,
