@@ -155,7 +155,7 @@ def reference_arm(args, rank, world):
 
 # ------------------------------------------------------------------- GB300 leg
 
-STAGES = ("sig", "sort", "filter", "enum", "dense", "sparse", "output")
+STAGES = ("sig", "sort", "filter", "enum", "dense", "sparse", "output", "pair_count", "pair_emit", "vote")
 
 
 def stage_bytes(w, N, st):

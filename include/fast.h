@@ -108,11 +108,15 @@ typedef struct {
     uint64_t n_detections;    /* M                                                   */
     uint64_t map_slots;       /* vote-map capacity (slots) of the last partition     */
     uint64_t n_launches;      /* CUDA kernels launched by the call                   */
-    uint64_t n_long_rows;     /* rows too long for the first vote tier (> 358 candidates) */
-    uint64_t n_huge_rows;     /* rows voted by a whole CTA (> 1433 candidates)       */
-    uint64_t max_row;         /* most candidates of one row among the CTA-voted rows */
+    uint64_t n_long_rows;     /* rows of row groups too large for one shared-memory
+                                 hash, voted one CTA per row                          */
+    uint64_t n_huge_rows;     /* long rows whose hash lives in global scratch         */
+    uint64_t max_row;         /* most candidates of one long row                      */
     uint32_t query_parts;     /* query partitions actually used                      */
     uint32_t sort_passes;     /* radix passes per table sort                         */
+    /* the sparse stage of the row-partitioned search, split: counting the
+       small/medium-bucket pairs per row group, writing them, voting */
+    float ms_pair_count, ms_pair_emit, ms_vote;
 } fast_stats;
 
 /*

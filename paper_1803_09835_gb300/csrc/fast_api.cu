@@ -118,6 +118,9 @@ void stats_times(fast_ctx *c, bool whole) {
     s.ms_sparse = stage_ms(c, 5, 6);
     s.ms_output = stage_ms(c, 6, 8);
     s.ms_total = whole ? stage_ms(c, 0, 8) : stage_ms(c, 3, 8);
+    s.ms_pair_count = stage_ms(c, 5, 10);
+    s.ms_pair_emit = stage_ms(c, 10, 11);
+    s.ms_vote = stage_ms(c, 11, 6);
 }
 
 extern "C" {

@@ -1505,11 +1505,13 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     if ((st = sync_check(c, s, "pair count"))) return st;
     S_out = S;
     if ((st = alloc(&ent, S))) return st;
+    stage_mark(c, 10, s);
     k_pairs_grp<1, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, tpw, nullptr, goff, gcur, ent), FAST_LAUNCHED(c);
     if (nmedium)
         k_medium_grp<1, PT><<<mg, 256, 0, s>>>(ea, medium, scal + Scal::NMEDIUM, gshift, nbits, nullptr, goff, gcur,
                                                ent), FAST_LAUNCHED(c);
 
+    stage_mark(c, 11, s);
     const size_t vsm = group_vote_smem<PT>();
     cudaFuncSetAttribute(k_group_vote<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
     int vper = 1;
