@@ -153,6 +153,61 @@ def reference_arm(args, rank, world):
     return 0
 
 
+# ------------------------------------------------------------ multi-rank plumbing
+#
+# One rank per GPU, one station per rank (an independent problem): the only
+# collectives are the barriers around the timed region and the max of the
+# per-rank step times.  The functions below are also driven on CPU ranks
+# (gloo) by the tests.
+
+def station_workload(name: str, rank: int, n: int = 0):
+    """The workload rank `rank` searches: station `rank` of `name` (own seed)."""
+    import synth
+    return synth.scaled(name, n, station=rank) if n else synth.workload(name, station=rank)
+
+
+def timed_steps(step, steps: int, warmup: int, dist=None, sync=None, clock=None):
+    """W untimed warm-up steps, then exactly K timed steps bracketed by a
+    barrier and a device sync on both sides.  `clock` is a pair of callables
+    (start, stop -> ms); the default is the host clock.  Returns ms per step
+    on this rank and the outputs of the last step."""
+    out = None
+    for _ in range(warmup):
+        out = step()
+    for phase in (0, 1):
+        if phase == 1:
+            ms = clock[1]() if clock else 1000 * (time.perf_counter() - t0)
+        if sync:
+            sync()
+        if dist:
+            dist.barrier()
+        if sync:
+            sync()
+        if phase == 0:
+            if clock:
+                clock[0]()
+            else:
+                t0 = time.perf_counter()
+            for _ in range(steps):
+                out = step()
+    return ms / steps, out
+
+
+def max_over_ranks(x: float, dist=None, device: str = "cpu") -> float:
+    """The largest x over all ranks (x itself on a single rank)."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(n_per_rank, ms_max: float) -> float:
+    """Whole-job throughput: the windows of every rank over the slowest rank's time."""
+    return sum(n_per_rank) / (ms_max / 1000)
+
+
 # ------------------------------------------------------------------- GB300 leg
 
 STAGES = ("sig", "sort", "filter", "enum", "dense", "sparse", "output", "pair_count", "pair_emit", "vote")
@@ -183,9 +238,7 @@ def gpu_arm(args, rank, world, local_rank):
     dist = None
     if world > 1:
         import torch.distributed as dist
-    w = synth.workload(args.workload, station=rank)
-    if args.n:
-        w = synth.scaled(args.workload, args.n, station=rank)
+    w = station_workload(args.workload, rank, args.n)
     ld = ((w.K + 7) // 8) * 8
     h_idx = torch.empty((w.N, ld), dtype=torch.uint16, pin_memory=True)
     synth.generate(w, ld=ld, out=h_idx)
@@ -198,39 +251,36 @@ def gpu_arm(args, rank, world, local_rank):
         r.free()
         return m, s.stats()
 
-    M = 0
-    for _ in range(args.warmup):
-        M, _ = step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks = Clocks(local_rank)
-    clocks.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
     acc = {k: 0.0 for k in STAGES}
-    launches = 0
-    last = None
-    for _ in range(args.steps):
+    counted = {"launches": 0, "on": False}
+
+    def timed_step():
         M, st = step()
-        for k in STAGES:
-            acc[k] += st["ms_" + k]
-        launches += st["n_launches"]
-        last = st
-    ev1.record()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
+        if counted["on"]:
+            for k in STAGES:
+                acc[k] += st["ms_" + k]
+            counted["launches"] += st["n_launches"]
+        return M, st
+
+    clocks = Clocks(local_rank)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def start():
+        clocks.start()
+        counted["on"] = True
+        ev0.record()
+
+    def stop():
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    ms, (M, last) = timed_steps(timed_step, args.steps, args.warmup, dist, torch.cuda.synchronize, (start, stop))
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = counted["launches"]
+    ms = max_over_ranks(ms, dist, "cuda")
     n_total = w.N * world
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n_total / (ms / 1000)
+    value = weak_value([w.N] * world, ms)
 
     # end to end through the host entry point: pinned input in, pinned result out
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
@@ -245,10 +295,7 @@ def gpu_arm(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_ms = 1000 * (time.perf_counter() - t0) / e2e_steps
     assert m2 == M
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
 
     # roofline of the dominant kernel
     peaks = {}

@@ -259,6 +259,8 @@ fast_status fast_get_stats(const fast_ctx *ctx, fast_stats *out);
  *   "large_min"  live bucket size from which buckets are summed by direct key
  *                comparison inside groups instead of the vote map (0 = auto)
  *   "map_load"   target load factor of the vote map, in (0.05, 0.95)
+ *   "group_pairs" expected sparse pairs per row group of the row-partitioned
+ *                vote, 0 (= 1536) or in [64, 8192]
  *   "timing"     1 = record per-stage CUDA events (default), 0 = off
  *   "vote_map"   1 = sum sparse votes in one global open-addressing map of
  *                packed (i, j) -> votes and order the list by a radix sort;

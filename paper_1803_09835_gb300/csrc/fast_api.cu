@@ -497,6 +497,11 @@ fast_status fast_get_stats(const fast_ctx *c, fast_stats *out) {
 fast_status fast_set_option(fast_ctx *c, const char *name, double value) {
     if (!c || !name) return FAST_EINVAL;
     if (!strcmp(name, "large_min")) c->large_min = (uint32_t)std::max(0.0, value);
+    else if (!strcmp(name, "group_pairs")) {
+        if (!(value == 0 || (value >= 64 && value <= 8192)))
+            return set_error(c, FAST_EINVAL, "group_pairs must be 0 or in [64, 8192]");
+        c->group_pairs = (uint32_t)value;
+    }
     else if (!strcmp(name, "map_load")) {
         if (!(value > 0.05 && value < 0.95)) return set_error(c, FAST_EINVAL, "map_load must be in (0.05, 0.95)");
         c->map_load = (float)value;

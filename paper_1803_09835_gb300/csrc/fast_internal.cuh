@@ -159,6 +159,7 @@ struct fast_ctx {
     bool capturing = false;     // no host synchronisation while a graph is being captured
     // tuning
     uint32_t large_min = 0;     // live bucket size from which a bucket goes to the dense path (0 = auto)
+    uint32_t group_pairs = 0;   // expected sparse pairs per row group of the vote (0 = 1536)
     float map_load = 0.5f;      // vote-map load factor target
     bool vote_map = false;      // sum sparse votes in one global hash map instead of per row
     // instrumentation

@@ -98,6 +98,7 @@ struct EnumArgs {
     const uint32_t *skey, *sid;
     const uint8_t *drop;
     const uint32_t *label;  // nullptr before grouping
+    const uint32_t *fsid;   // sid with bit 31 set on dropped ids and group members (nullptr: not built)
     uint64_t N;
     uint32_t excl;
     uint32_t i_lo, i_hi;  // query partition [i_lo, i_hi)
@@ -597,7 +598,8 @@ struct PairWin {
 };
 
 __device__ __forceinline__ PairWin pair_tile(const EnumArgs &a, const uint32_t *__restrict__ K,
-                                             const uint32_t *__restrict__ S, uint64_t T) {
+                                             const uint32_t *__restrict__ S, const uint32_t *__restrict__ FS,
+                                             uint64_t T) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t x = T * 32 + lane, N = a.N;
     const bool valid = x < N;
@@ -608,11 +610,54 @@ __device__ __forceinline__ PairWin pair_tile(const EnumArgs &a, const uint32_t *
     if (a.st.nst > 1 && valid && !head) head = a.st.soff[station_of(a.st, x)] == x;
     PairWin w;
     w.heads = __ballot_sync(~0u, head);
-    w.id = valid ? S[x] : 0u;
     w.lab = kLabDrop;
-    if (valid && !a.drop[w.id]) w.lab = a.label ? __ldg(a.label + w.id) : kNone;
+    if (FS) {  // only flagged entries (dropped or in a dense group) need the random lookups
+        const uint32_t raw = valid ? FS[x] : 0u;
+        w.id = raw & 0x7FFFFFFFu;
+        if (valid) w.lab = !(raw >> 31) ? kNone : a.drop[w.id] ? kLabDrop : __ldg(a.label + w.id);
+    } else {
+        w.id = valid ? S[x] : 0u;
+        if (valid && !a.drop[w.id]) w.lab = a.label ? __ldg(a.label + w.id) : kNone;
+    }
     return w;
 }
+
+// Flag bitmap over ids: bit id set iff id is dropped or a dense-group member.
+__global__ void __launch_bounds__(256) k_flag_bits(const uint8_t *__restrict__ drop, const uint32_t *__restrict__ label,
+                                                   uint64_t N, uint32_t *__restrict__ bits) {
+    const uint64_t nw = (N + 31) / 32;
+    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t m = 0;
+        for (uint32_t k = 0; k < 32; k++) {
+            const uint64_t id = w * 32 + k;
+            if (id < N && (drop[id] || label[id] != kNone)) m |= 1u << k;
+        }
+        bits[w] = m;
+    }
+}
+
+// fsid = sid with bit 31 = flag bit of the id, for all n table entries
+// (sid and fsid 16-byte aligned; four entries per load, the ragged tail alone).
+__device__ __forceinline__ uint32_t flag_id(uint32_t id, const uint32_t *__restrict__ bits) {
+    return id | (bits[id >> 5] >> (id & 31)) << 31;
+}
+
+__global__ void __launch_bounds__(256) k_flag_ids(const uint32_t *__restrict__ sid, uint64_t n,
+                                                  const uint32_t *__restrict__ bits, uint32_t *__restrict__ fsid) {
+    const uint64_t n4 = n / 4, tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(sid);
+    uint4 *f4 = reinterpret_cast<uint4 *>(fsid);
+    for (uint64_t q = tid; q < n4; q += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 v = s4[q];
+        f4[q] = make_uint4(flag_id(v.x, bits), flag_id(v.y, bits), flag_id(v.z, bits), flag_id(v.w, bits));
+    }
+    if (tid < n - n4 * 4) fsid[n4 * 4 + tid] = flag_id(sid[n4 * 4 + tid], bits);
+}
+
+struct PairSmem {  // one warp's tile window and its pair bookkeeping
+    uint32_t id[64], lab[64], pre[32], cnt[32];
+    uint64_t base[32];
+};
 
 template <int MODE, typename PT>
 __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, uint32_t nbits, uint32_t tiles_per_warp,
@@ -622,14 +667,17 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
     const uint64_t N = a.N, ntiles = (N + 31) / 32;
     const uint32_t *K = a.skey + (uint64_t)t * N;
     const uint32_t *S = a.sid + (uint64_t)t * N;
+    const uint32_t *FS = a.fsid ? a.fsid + (uint64_t)t * N : nullptr;
     const uint32_t lmask = (1u << gshift) - 1;
     const uint64_t T0 = ((uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32) * tiles_per_warp;
     if (T0 >= ntiles) return;  // warp-uniform
     const uint64_t T1 = min(T0 + tiles_per_warp, ntiles);
-    uint32_t hp = T0 ? pair_tile(a, K, S, T0 - 1).heads : ~0u;
-    PairWin c = pair_tile(a, K, S, T0);
+    __shared__ PairSmem ps[8];
+    PairSmem &W = ps[threadIdx.x / 32];
+    uint32_t hp = T0 ? pair_tile(a, K, S, FS, T0 - 1).heads : ~0u;
+    PairWin c = pair_tile(a, K, S, FS, T0);
     for (uint64_t T = T0; T < T1; T++) {
-        const PairWin n = pair_tile(a, K, S, T + 1);
+        const PairWin n = pair_tile(a, K, S, FS, T + 1);
         // bucket of position L: first position s0 (window coordinates, previous
         // tile = 0..31) and end e (coordinates of current + next = 0..63)
         const uint64_t hpc = (uint64_t)c.heads << 32 | hp;
@@ -639,30 +687,53 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
         const int s0 = below ? 63 - __clzll((long long)below) : -1;
         const int e = above ? __ffsll((long long)above) - 1 : 64;
         const bool act = s0 >= 0 && e < 64 && e + 32 - s0 <= (int)kSmall && e > (int)lane + 1 && c.lab != kLabDrop;
-        const uint32_t dmax = __reduce_max_sync(~0u, act ? (uint32_t)(e - (int)lane - 1) : 0u);
-        const uint32_t i = c.id;
-        uint32_t cnt = 0;
-        for (uint32_t d = 1; d <= dmax; d++) {
-            const uint32_t src = (lane + d) & 31;
-            const uint32_t jc = __shfl_sync(~0u, c.id, src), jn = __shfl_sync(~0u, n.id, src);
-            const uint32_t lc = __shfl_sync(~0u, c.lab, src), ln = __shfl_sync(~0u, n.lab, src);
-            const bool inc = lane + d < 32;
-            const uint32_t j = inc ? jc : jn, lj = inc ? lc : ln;
-            cnt += act && (int)(lane + d) < e && lj != kLabDrop && j - i > a.excl && (c.lab == kNone || c.lab != lj);
+        // the tile's candidate pairs, dealt out evenly: pair k belongs to the
+        // lane L with pre[L] <= k < pre[L] + cand[L], partner position L + d
+        const uint32_t cand = act ? (uint32_t)(e - (int)lane - 1) : 0u;
+        uint32_t incl = cand;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(~0u, incl, o);
+            if ((int)lane >= o) incl += y;
         }
-        if (MODE == 0) {
-            if (cnt) atomicAdd(gcnt + (i >> gshift), cnt);
-        } else if (__any_sync(~0u, cnt != 0)) {
-            uint64_t o = cnt ? goff[i >> gshift] + atomicAdd(gcur + (i >> gshift), cnt) : 0;
-            for (uint32_t d = 1; d <= dmax; d++) {
-                const uint32_t src = (lane + d) & 31;
-                const uint32_t jc = __shfl_sync(~0u, c.id, src), jn = __shfl_sync(~0u, n.id, src);
-                const uint32_t lc = __shfl_sync(~0u, c.lab, src), ln = __shfl_sync(~0u, n.lab, src);
-                const bool inc = lane + d < 32;
-                const uint32_t j = inc ? jc : jn, lj = inc ? lc : ln;
-                if (cnt && (int)(lane + d) < e && lj != kLabDrop && j - i > a.excl && (c.lab == kNone || c.lab != lj))
-                    ent[o++] = pack_entry<PT>(i & lmask, j, nbits);
+        const uint32_t P = __shfl_sync(~0u, incl, 31);
+        if (P) {  // warp-uniform
+            W.id[lane] = c.id;
+            W.id[32 + lane] = n.id;
+            W.lab[lane] = c.lab;
+            W.lab[32 + lane] = n.lab;
+            W.pre[lane] = incl - cand;
+            W.cnt[lane] = 0;
+            __syncwarp();
+            for (uint32_t k = lane; k < P; k += 32) {
+                uint32_t L = 0;
+#pragma unroll
+                for (uint32_t step = 16; step; step >>= 1)
+                    if (W.pre[L + step] <= k) L += step;
+                const uint32_t y = L + 1 + (k - W.pre[L]);
+                const uint32_t i = W.id[L], li = W.lab[L], j = W.id[y], lj = W.lab[y];
+                if (lj != kLabDrop && j - i > a.excl && (li == kNone || li != lj)) atomicAdd(&W.cnt[L], 1u);
             }
+            __syncwarp();
+            const uint32_t cnt = W.cnt[lane], g = c.id >> gshift;
+            if (MODE == 0) {
+                if (cnt) atomicAdd(gcnt + g, cnt);
+            } else if (__any_sync(~0u, cnt != 0)) {
+                W.base[lane] = cnt ? goff[g] + atomicAdd(gcur + g, cnt) : 0;
+                W.cnt[lane] = 0;
+                __syncwarp();
+                for (uint32_t k = lane; k < P; k += 32) {
+                    uint32_t L = 0;
+#pragma unroll
+                    for (uint32_t step = 16; step; step >>= 1)
+                        if (W.pre[L + step] <= k) L += step;
+                    const uint32_t y = L + 1 + (k - W.pre[L]);
+                    const uint32_t i = W.id[L], li = W.lab[L], j = W.id[y], lj = W.lab[y];
+                    if (lj != kLabDrop && j - i > a.excl && (li == kNone || li != lj))
+                        ent[W.base[L] + atomicAdd(&W.cnt[L], 1u)] = pack_entry<PT>(i & lmask, j, nbits);
+                }
+            }
+            __syncwarp();
         }
         hp = c.heads;
         c = n;
@@ -730,7 +801,7 @@ __global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, const uint4 *__r
 struct VoteArgs {
     const uint64_t *goff;
     uint64_t ngroups, N;
-    uint32_t gshift, nbits, v;
+    uint32_t gshift, nbits, v, vcap;
     uint32_t *sp_cnt;
     uint64_t *sp_start;
     uint32_t *sp_j;
@@ -761,12 +832,17 @@ __device__ __forceinline__ bool vadd(uint32_t *K, uint32_t *C, uint32_t slots, u
     return false;
 }
 
-constexpr uint32_t kVCap = 4096;       // pairs of a group counted in shared memory (larger groups: per row)
-constexpr uint32_t kVTarget = 1536;    // expected pairs per group
+// A row group's pairs are counted in one shared-memory hash of >= 2n slots
+// when n <= vcap (larger groups: one CTA per row).  The expected pairs per
+// group (`group_pairs`, default 1536) sets the group size 2^gshift rows, and
+// vcap is twice the power of two above it: larger groups mean fewer
+// concurrent write frontiers in the emission pass, smaller ones more resident
+// CTAs in the vote.
+constexpr uint32_t kVTargetDefault = 1536;
 
 template <typename PT>
-size_t group_vote_smem() {
-    return (size_t)2 * kVCap * sizeof(PT) + (size_t)2 * kVCap / 4 * 4;
+size_t group_vote_smem(uint32_t vcap) {
+    return (size_t)2 * vcap * sizeof(PT) + (size_t)2 * vcap / 4 * 4;
 }
 
 // Slot of a key in a table of 2^lg slots: multiplicative (Fibonacci) hashing,
@@ -782,8 +858,8 @@ __device__ __forceinline__ uint32_t ghash(unsigned long long key, uint32_t lg) {
 template <typename PT>
 __global__ void __launch_bounds__(256) k_group_vote(VoteArgs A, const PT *__restrict__ ent) {
     extern __shared__ unsigned long long vsm_raw[];
-    PT *K = reinterpret_cast<PT *>(vsm_raw);                             // [<= 2 kVCap] keys (entry + 1)
-    uint32_t *C = reinterpret_cast<uint32_t *>(K + 2 * kVCap);           // [<= 2 kVCap / 4] byte counts
+    PT *K = reinterpret_cast<PT *>(vsm_raw);                             // [<= 2 vcap] keys (entry + 1)
+    uint32_t *C = reinterpret_cast<uint32_t *>(K + 2 * A.vcap);          // [<= 2 vcap / 4] byte counts
     __shared__ uint32_t wsum[32];
     __shared__ unsigned long long s_b0;
     const PT jmask = ((PT)1 << A.nbits) - 1;
@@ -791,7 +867,7 @@ __global__ void __launch_bounds__(256) k_group_vote(VoteArgs A, const PT *__rest
         const uint64_t e0 = A.goff[g], n = A.goff[g + 1] - e0;
         if (n < A.v) continue;  // block-uniform
         const uint64_t row0 = g << A.gshift;
-        if (n > kVCap) {  // every row of the group is voted one CTA each
+        if (n > A.vcap) {  // every row of the group is voted one CTA each
             for (uint32_t r = threadIdx.x; r < (1u << A.gshift); r += blockDim.x) {
                 if (row0 + r >= A.N) break;
                 unsigned long long q = atomicAdd(A.n_long, 1ull);
@@ -1308,7 +1384,7 @@ static fast_status search_map(fast_ctx *c, const fast_tables *tb, const uint32_t
     const uint64_t big_cap = (uint64_t)nb * (N / (kSmall + 1) + 1);
     uint4 *big = nullptr, *large = nullptr, *medium = nullptr;
     if ((st = alloc(&big, big_cap))) return fail(st);
-    EnumArgs ea{tb->d_skey, tb->d_sid, tb->d_drop, nullptr, N, p.excl, 0, (uint32_t)N, nparts, {tb->d_soff, tb->nst}};
+    EnumArgs ea{tb->d_skey, tb->d_sid, tb->d_drop, nullptr, nullptr, N, p.excl, 0, (uint32_t)N, nparts, {tb->d_soff, tb->nst}};
     Map nomap{nullptr, 0};
     const dim3 eg(std::max(1u, std::min<unsigned>(ceil_div(N, 256), 2048)), nb);
     k_enum<0><<<eg, 256, 0, s>>>(ea, big, scal + Scal::NBIG, big_cap, scal + Scal::PART0, nomap, c->d_err), FAST_LAUNCHED(c);
@@ -1512,12 +1588,16 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
                                                ent), FAST_LAUNCHED(c);
 
     stage_mark(c, 11, s);
-    const size_t vsm = group_vote_smem<PT>();
+    // hash capacity: twice the power of two above the target (group sizes vary)
+    uint32_t vcap = 64;
+    while (vcap < (c->group_pairs ? c->group_pairs : kVTargetDefault)) vcap <<= 1;
+    vcap = std::min<uint32_t>(2 * vcap, sizeof(PT) == 4 ? 1u << 14 : 1u << 13);
+    const size_t vsm = group_vote_smem<PT>(vcap);
     cudaFuncSetAttribute(k_group_vote<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
     int vper = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&vper, k_group_vote<PT>, 256, vsm);
     uint64_t sp_cap = std::max<uint64_t>(N, 1 << 20);
-    VoteArgs va{goff, ng, N, gshift, nbits, p.v, sp_cnt, sp_start, nullptr, nullptr, 0, scal + Scal::CUR_SPARSE,
+    VoteArgs va{goff, ng, N, gshift, nbits, p.v, vcap, sp_cnt, sp_start, nullptr, nullptr, 0, scal + Scal::CUR_SPARSE,
                 long_rows, scal + Scal::NLONG, N};
     for (int attempt = 0; attempt < 2; attempt++) {
         uint32_t *sp_j = nullptr;
@@ -1610,7 +1690,7 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
     const uint64_t big_cap = (uint64_t)nb * (N / (kSmall + 1) + 1);
     uint4 *big = nullptr, *large = nullptr, *medium = nullptr;
     if ((st = alloc(&big, big_cap))) return fail(st);
-    EnumArgs ea{tb->d_skey, tb->d_sid, tb->d_drop, nullptr, N, p.excl, 0, (uint32_t)N, 1, {tb->d_soff, tb->nst}};
+    EnumArgs ea{tb->d_skey, tb->d_sid, tb->d_drop, nullptr, nullptr, N, p.excl, 0, (uint32_t)N, 1, {tb->d_soff, tb->nst}};
     const dim3 eg(std::max(1u, std::min<unsigned>(ceil_div(N, 256), 2048)), nb);
     k_find_big<<<eg, 256, 0, s>>>(ea, big, scal + Scal::NBIG, big_cap, scal + Scal::SMALLPAIRS, c->d_err),
         FAST_LAUNCHED(c);
@@ -1695,6 +1775,16 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
 
     // ---- sparse pairs: group-partitioned emission, per-row votes
     ea.label = label;
+    {  // flagged copy of the id lists: the pair passes then look up drop / label only for flagged ids
+        uint32_t *bits = nullptr, *fsid = nullptr;
+        const uint64_t n = (uint64_t)nb * N;
+        if ((st = alloc(&bits, (N + 31) / 32)) || (st = alloc(&fsid, n))) return fail(st);
+        k_flag_bits<<<std::max(1u, std::min<unsigned>(ceil_div((N + 31) / 32, 256), c->num_sms * 8)), 256, 0, s>>>(
+            tb->d_drop, label, N, bits), FAST_LAUNCHED(c);
+        k_flag_ids<<<std::max(1u, std::min<unsigned>(ceil_div(n / 4 + 1, 256), c->num_sms * 16)), 256, 0, s>>>(
+            tb->d_sid, n, bits, fsid), FAST_LAUNCHED(c);
+        ea.fsid = fsid;
+    }
     uint32_t *sp_cnt = nullptr, *sp_j = nullptr;
     uint64_t *sp_start = nullptr;
     uint8_t *sp_v = nullptr;
@@ -1706,7 +1796,8 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
         const double avg = (double)S_ub / (double)N;
         const uint32_t nbits = bits_for(N);
         uint32_t gshift = 0;
-        while (gshift < 12 && (double)(2ull << gshift) * avg <= kVTarget) gshift++;
+        const uint32_t target = c->group_pairs ? c->group_pairs : kVTargetDefault;
+        while (gshift < 12 && (double)(2ull << gshift) * avg <= target) gshift++;
         // 32-bit entries while entry + 1 cannot wrap to the empty key
         const fast_status r = gshift + nbits < 32
                                   ? sparse_groups<uint32_t>(c, ea, medium, nmedium, gshift, nbits, sp_cnt, sp_start,
@@ -1841,7 +1932,7 @@ fast_status history_groups(fast_ctx *c, const fast_tables *tb, const uint32_t *d
     uint4 *big = nullptr, *large = nullptr, *medium = nullptr;
     if ((st = dalloc_t(c, &big, big_cap, s))) return st;
     cudaMemsetAsync(scal, 0, sizeof(uint64_t) * kScal, s);
-    EnumArgs ea{tb->d_skey, tb->d_sid, tb->d_drop, nullptr, N, p.excl, 0, (uint32_t)N, 1, {tb->d_soff, tb->nst}};
+    EnumArgs ea{tb->d_skey, tb->d_sid, tb->d_drop, nullptr, nullptr, N, p.excl, 0, (uint32_t)N, 1, {tb->d_soff, tb->nst}};
     const dim3 eg(std::max(1u, std::min<unsigned>(ceil_div(N, 256), 2048)), nb);
     k_find_big<<<eg, 256, 0, s>>>(ea, big, scal + Scal::NBIG, big_cap, scal + Scal::SMALLPAIRS, c->d_err),
         FAST_LAUNCHED(c);
