@@ -79,9 +79,12 @@ __device__ __forceinline__ uint32_t u16_of(const uint4 &v, int s) {
 }
 
 // Signature kernel, walk variant.  Persistent CTAs loop over tiles of 32
-// fingerprints.  Shared memory: M[D] masks, vals[32][Wp] walk results.
+// fingerprints.  Shared memory: M[D] masks and, per fingerprint and walk, the
+// element x where the walk first hit it (16 bits; its hash value is computed
+// once, in the combine step).  The walks are latency-bound chains of
+// dependent loads, so the small footprint buys resident CTAs: three per SM.
 template <bool MINMAX>
-__global__ void __launch_bounds__(kSigThreads, 2)
+__global__ void __launch_bounds__(kSigThreads, 3)
     k_sig_walk(const uint16_t *__restrict__ idx, uint64_t N, uint32_t ld, uint32_t D, uint32_t K,
                const uint16_t *__restrict__ walk, uint32_t Dpad, uint32_t W, const uint64_t *__restrict__ ha,
                const uint64_t *__restrict__ hb, const uint64_t *__restrict__ zinit, uint32_t nb, uint32_t r,
@@ -89,8 +92,8 @@ __global__ void __launch_bounds__(kSigThreads, 2)
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t next_walk;
     uint32_t *M = smem;
-    const uint32_t Wp = W | 1u;  // odd row stride: vals[q][w] for 32 q hit 32 banks
-    uint32_t *vals = smem + ((D + 3) & ~3u);
+    const uint32_t Wp = W | 1u;  // odd row stride
+    uint16_t *vals = reinterpret_cast<uint16_t *>(smem + ((D + 3) & ~3u));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const uint64_t ntiles = (N + kTile - 1) / kTile;
     const uint32_t nk8 = Dpad / 8;
@@ -134,17 +137,8 @@ __global__ void __launch_bounds__(kSigThreads, 2)
         // 2. walks: lane-private state, walks handed out one at a time
         const uint32_t done_mask = nvalid == 32 ? 0u : (~0u << nvalid);
         uint32_t w = atomicAdd(&next_walk, 1u);
-        uint32_t found = done_mask, k8 = 0, a_lo = 0, a_hi = 0;
-        uint64_t bb = 0;
-        const uint4 *seq = nullptr;
-        if (w < W) {
-            uint32_t f = MINMAX ? (w >> 1) : w;
-            uint64_t a = __ldg(ha + f);
-            a_lo = (uint32_t)a;
-            a_hi = (uint32_t)(a >> 32);
-            bb = __ldg(hb + f);
-            seq = reinterpret_cast<const uint4 *>(walk + (size_t)w * Dpad);
-        }
+        uint32_t found = done_mask, k8 = 0;
+        const uint4 *seq = w < W ? reinterpret_cast<const uint4 *>(walk + (size_t)w * Dpad) : nullptr;
         uint4 nxt = w < W ? __ldg(seq) : make_uint4(0, 0, 0, 0);
         while (w < W) {
             const uint4 v = nxt;
@@ -155,10 +149,9 @@ __global__ void __launch_bounds__(kSigThreads, 2)
                 uint32_t m = M[x] & ~found;
                 if (m) {
                     found |= m;
-                    uint32_t h = hash_ab(a_lo, a_hi, bb, x);
                     do {
                         uint32_t q = __ffs(m) - 1;
-                        vals[q * Wp + w] = h;
+                        vals[q * Wp + w] = (uint16_t)x;
                         m &= m - 1;
                     } while (m);
                 }
@@ -170,11 +163,6 @@ __global__ void __launch_bounds__(kSigThreads, 2)
                 found = done_mask;
                 k8 = 0;
                 if (w < W) {
-                    uint32_t f = MINMAX ? (w >> 1) : w;
-                    uint64_t a = __ldg(ha + f);
-                    a_lo = (uint32_t)a;
-                    a_hi = (uint32_t)(a >> 32);
-                    bb = __ldg(hb + f);
                     seq = reinterpret_cast<const uint4 *>(walk + (size_t)w * Dpad);
                     nxt = __ldg(seq);
                 }
@@ -187,14 +175,13 @@ __global__ void __launch_bounds__(kSigThreads, 2)
             const uint32_t q = lane;
             for (uint32_t t = warp; t < nb; t += nwarps) {
                 uint64_t z = __ldg(zinit + t);
-                if (MINMAX) {
-                    const uint32_t qf = (r + 1) / 2;
-                    for (uint32_t c = 0; c < r; c++) {
-                        uint32_t f = t * qf + c / 2;
-                        z = mix64(z ^ (uint64_t)vals[q * Wp + 2 * f + (c & 1)]);
-                    }
-                } else {
-                    for (uint32_t c = 0; c < r; c++) z = mix64(z ^ (uint64_t)vals[q * Wp + t * r + c]);
+                const uint32_t qf = MINMAX ? (r + 1) / 2 : r;
+                for (uint32_t c = 0; c < r; c++) {
+                    const uint32_t f = MINMAX ? t * qf + c / 2 : t * r + c;
+                    const uint32_t x = vals[q * Wp + (MINMAX ? 2 * f + (c & 1) : f)];
+                    const uint64_t a = __ldg(ha + f);
+                    const uint32_t h = hash_ab((uint32_t)a, (uint32_t)(a >> 32), __ldg(hb + f), x);
+                    z = mix64(z ^ (uint64_t)h);
                 }
                 sig[(uint64_t)t * N + base + q] = (uint32_t)(z >> 32);
             }
@@ -242,7 +229,9 @@ __global__ void k_sig_direct(const uint16_t *__restrict__ idx, uint64_t N, uint3
     }
 }
 
-size_t walk_smem(const fast_ctx *c) { return (size_t)((c->p.D + 3) & ~3u) * 4 + (size_t)kTile * (c->W | 1u) * 4; }
+size_t walk_smem(const fast_ctx *c) {
+    return (size_t)((c->p.D + 3) & ~3u) * 4 + (((size_t)kTile * (c->W | 1u) * 2 + 15) & ~(size_t)15);
+}
 
 }  // namespace
 

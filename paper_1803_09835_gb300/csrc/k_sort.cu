@@ -7,7 +7,7 @@
 //   k_hist    per (segment, chunk) digit counts        -- reads keys
 //   scan      per segment exclusive scan, digit-major (k_scan.cu)
 //   k_scatter per chunk: stable rank of every key inside the chunk (warp
-//             match_any + per-warp counters), staging in shared memory in
+//             ballots + per-warp counters), staging in shared memory in
 //             digit order, then coalesced runs written to the digit's
 //             global position.
 // Stability makes the ids of a bucket come out ascending, i.e. the canonical
@@ -32,6 +32,19 @@ constexpr int kChunk = kSub * kSubPerChunk;  // 8192 keys per chunk
 template <typename KT>
 __device__ __forceinline__ uint32_t digit_of(KT k, uint32_t shift) {
     return (uint32_t)(k >> shift) & (kRadix - 1);
+}
+
+// Lanes of the warp holding the same 8-bit digit as this lane; digits >= 256
+// mark lanes without an item, which match no valid lane.  Eight ballots (one
+// per digit bit) instead of a match instruction, whose pipe is the narrow one.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t dig) {
+    uint32_t peers = __ballot_sync(~0u, dig < (uint32_t)kRadix);
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+        const uint32_t m = __ballot_sync(~0u, (dig >> b) & 1u);
+        peers &= ((dig >> b) & 1u) ? m : ~m;
+    }
+    return peers;
 }
 
 template <typename KT, bool STD = false>
@@ -125,14 +138,20 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const KT *__restrict__ kin
 
         KT key[kItems];
         uint32_t val[kItems], dig[kItems], rnk[kItems];
+        // all loads of the sub-tile first, so that they are in flight together
 #pragma unroll
         for (int j = 0; j < kItems; j++) {
             const uint32_t e = warp * (kItems * 32) + j * 32 + lane;
             const bool valid = e < nvalid;
             key[j] = valid ? ki[sbase + e] : (KT)0;
             if (HAS_VAL) val[j] = valid ? (IOTA ? (uint32_t)(sbase + e) : vi[sbase + e]) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kItems; j++) {
+            const uint32_t e = warp * (kItems * 32) + j * 32 + lane;
+            const bool valid = e < nvalid;
             dig[j] = valid ? (STD ? station_of(S, val[j]) : digit_of(key[j], shift)) : (uint32_t)kRadix;
-            const uint32_t peers = __match_any_sync(~0u, dig[j]);
+            const uint32_t peers = digit_peers(dig[j]);
             const uint32_t before = peers & lt_mask;
             uint32_t basec = 0;
             if (valid) basec = wcnt[warp][dig[j]];
