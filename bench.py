@@ -210,21 +210,79 @@ def weak_value(n_per_rank, ms_max: float) -> float:
 
 # ------------------------------------------------------------------- GB300 leg
 
-STAGES = ("sig", "sort", "filter", "enum", "dense", "sparse", "output", "pair_count", "pair_emit", "vote")
+STAGES = ("sig", "sort", "filter", "enum", "dense", "sparse", "output", "pair_count", "pair_emit", "vote",
+          "k_pairs", "k_vote")
 
 
-def stage_bytes(w, N, st):
-    """Algorithmic bytes per stage and launch (measurement)."""
-    b = w.b
-    return {
-        "sig": N * (2 * w.K + 4 * b),            # read the index lists, write b keys
-        "sort": N * b * (4 + 8),                 # read keys, write (key, id)
-        "filter": N * b * 4 + N,                 # read sorted keys, write the drop mask
-        "enum": N * b * 8,                       # read (key, id) of every table
-        "dense": st["n_dense_pairs"] * 0 + 1,    # compare-bound; no HBM traffic to speak of
-        "sparse": st["n_emissions"] * (4 + 9),   # read j, read-modify-write a 9-byte slot
-        "output": st["n_detections"] * 9 * 2,    # write + read (i, j, votes)
+def _kernel_source_hash(rel: str) -> str:
+    import hashlib
+    return hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest()[:16]
+
+
+def _traffic(kernel: str, units: float):
+    """DRAM bytes per launch from the committed ncu capture of this kernel
+    (profiles/dram_traffic.json: bytes per unit, scaled to this launch), or
+    None when there is none or the kernel's source changed since."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))[kernel]
+    except (OSError, ValueError, KeyError):
+        return None
+    if _kernel_source_hash(rec["source"]) != rec["source_sha256_16"]:
+        return None
+    return rec["bytes_per_unit"] * units
+
+
+def kernel_rooflines(w, per, st, peaks, n_sms):
+    """Per kernel: live ms per launch, algorithmic bytes per launch and the
+    HBM roofline fraction they reach.  Algorithmic bytes (per unit):
+      k_sig_walk      read K u16 indices + write b keys  = 2K + 4b  per fingerprint
+      radix sort      read key + write (key, id)         = 12       per table entry (all passes together)
+      k_pairs_grp<1>  read (key, flagged id) 8 per table entry + write 4 per small-bucket pair
+      k_group_vote    read 4 per pair emission + write 5 per kept sparse pair (not counted: small)
+      output          write (i, j, votes)                = 9        per detection"""
+    N, b, K = w.N, w.b, w.K
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    src = "measured" if "hbm_gbs" in peaks else "fallback"
+    out = {}
+
+    def put(name, ms, nbytes, single, traffic=None, **extra):
+        ach = nbytes / (ms / 1000) / 1e9 if ms > 0 else 0.0
+        out[name] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                     "traffic": traffic, "peak_source": src, "algorithmic_bytes": nbytes, "ms": ms,
+                     "single_kernel": single, **extra}
+
+    F = b * ((w.r + 1) // 2) if w.kind else b * w.r
+    clock = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    alu_peak = n_sms * 128 * clock  # int32 lanes x clock
+    put("k_sig_walk", per["sig"], N * (2 * K + 4 * b), True, _traffic("k_sig_walk", N),
+        alu_view={"definition": "direct evaluation: N*K*F hash evaluations x 4 int ops",
+                  "ops": N * K * F * 4, "peak_ops_per_s": alu_peak,
+                  "time_at_peak_ms": 1000 * N * K * F * 4 / alu_peak})
+    passes = max(1, st["sort_passes"])
+    put("radix sort", per["sort"], N * b * 12, False, None, passes=passes)
+    put("k_pairs_grp<1>", per["k_pairs"], N * b * 8 + st["n_pairs_small"] * 4, True,
+        _traffic("k_pairs_grp<1>", st["n_pairs_small"]))
+    put("k_group_vote", per["k_vote"], st["n_emissions"] * 4, True, _traffic("k_group_vote", st["n_emissions"]))
+    put("output", per["output"], st["n_detections"] * 9, False)
+    return out
+
+
+def path_sol(w, per, st, peaks, n_sms, ms_step):
+    """Speed-of-light time of the whole path by stage (each stage at the larger
+    of its HBM time and, for signatures, the direct-evaluation ALU time), over
+    the measured step time."""
+    N, b, K = w.N, w.b, w.K
+    hbm = float(peaks.get("hbm_gbs", 6800.0)) * 1e9
+    clock = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    F = b * ((w.r + 1) // 2) if w.kind else b * w.r
+    t = {
+        "sig": max(N * (2 * K + 4 * b) / hbm, N * K * F * 4 / (n_sms * 128 * clock)),
+        "sort_filter": N * b * 20 / hbm,  # read key 4, write (key, id) 8, read key 4 + id 4 again
+        "pairs_votes": st["n_emissions"] * 13 / hbm,
+        "output": st["n_detections"] * 9 / hbm,
     }
+    tsol = 1000 * sum(t.values())
+    return {"t_sol_ms": tsol, "frac": tsol / ms_step, "by_stage_ms": {k: 1000 * v for k, v in t.items()}}
 
 
 def gpu_arm(args, rank, world, local_rank):
@@ -297,22 +355,18 @@ def gpu_arm(args, rank, world, local_rank):
     assert m2 == M
     e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel (live CUDA-event times, algorithmic bytes)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     per = {k: acc[k] / args.steps for k in STAGES}
-    dom = max(("sig", "sort", "sparse", "enum", "output"), key=lambda k: per[k])
-    bytes_ = stage_bytes(w, w.N, last)[dom]
-    achieved = bytes_ / (per[dom] / 1000) / 1e9 if per[dom] > 0 else 0.0
-    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
-            "algorithmic_bytes": bytes_, "ms": per[dom]}
-
+    kernels = kernel_rooflines(w, per, last, peaks, torch.cuda.get_device_properties(local_rank).multi_processor_count)
+    dom = max((k for k in kernels if kernels[k]["single_kernel"]), key=lambda k: kernels[k]["ms"])
+    roof = dict(kernels[dom])
+    roof["kernel"] = dom
+    roof.pop("single_kernel")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
@@ -320,6 +374,10 @@ def gpu_arm(args, rank, world, local_rank):
             "e2e": {"value": n_total / (e2e_ms / 1000), "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": w.N * ld * 2, "d2h_bytes_per_step": M * 9},
             "gpu_launches": launches, "roofline": roof, "clocks": clk,
+            "kernels": {k: {kk: v[kk] for kk in ("ms", "bound", "achieved", "frac", "unit")}
+                        for k, v in kernels.items()},
+            "path_sol": path_sol(w, per, last, peaks, torch.cuda.get_device_properties(local_rank).multi_processor_count,
+                                 ms),
             "stage_ms": per,
             "counters": {k: last[k] for k in ("n_dropped", "n_emissions", "n_dense_pairs", "n_groups",
                                               "n_detections", "map_slots", "query_parts", "sort_passes",

@@ -117,6 +117,9 @@ typedef struct {
     /* the sparse stage of the row-partitioned search, split: counting the
        small/medium-bucket pairs per row group, writing them, voting */
     float ms_pair_count, ms_pair_emit, ms_vote;
+    /* single kernels inside those: the small-bucket pair writer, the group vote */
+    float ms_k_pairs, ms_k_vote;
+    uint64_t n_pairs_small;   /* of n_emissions: pairs of buckets with at most 32 entries */
 } fast_stats;
 
 /*

@@ -121,6 +121,8 @@ void stats_times(fast_ctx *c, bool whole) {
     s.ms_pair_count = stage_ms(c, 5, 10);
     s.ms_pair_emit = stage_ms(c, 10, 11);
     s.ms_vote = stage_ms(c, 11, 6);
+    s.ms_k_pairs = stage_ms(c, 10, 12);
+    s.ms_k_vote = stage_ms(c, 13, 14);
 }
 
 extern "C" {

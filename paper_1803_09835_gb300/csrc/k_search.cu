@@ -603,7 +603,7 @@ __device__ __forceinline__ PairWin pair_tile(const EnumArgs &a, const uint32_t *
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t x = T * 32 + lane, N = a.N;
     const bool valid = x < N;
-    const uint32_t key = valid ? K[x] : 0u;
+    const uint32_t key = valid ? __ldcs(K + x) : 0u;
     uint32_t kprev = __shfl_up_sync(~0u, key, 1);
     if (lane == 0 && valid && x > 0) kprev = K[x - 1];
     bool head = !valid || x == 0 || key != kprev;
@@ -612,7 +612,7 @@ __device__ __forceinline__ PairWin pair_tile(const EnumArgs &a, const uint32_t *
     w.heads = __ballot_sync(~0u, head);
     w.lab = kLabDrop;
     if (FS) {  // only flagged entries (dropped or in a dense group) need the random lookups
-        const uint32_t raw = valid ? FS[x] : 0u;
+        const uint32_t raw = valid ? __ldcs(FS + x) : 0u;
         w.id = raw & 0x7FFFFFFFu;
         if (valid) w.lab = !(raw >> 31) ? kNone : a.drop[w.id] ? kLabDrop : __ldg(a.label + w.id);
     } else {
@@ -662,7 +662,8 @@ struct PairSmem {  // one warp's tile window and its pair bookkeeping
 template <int MODE, typename PT>
 __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, uint32_t nbits, uint32_t tiles_per_warp,
                                                    uint32_t *__restrict__ gcnt, const uint64_t *__restrict__ goff,
-                                                   uint32_t *__restrict__ gcur, PT *__restrict__ ent) {
+                                                   uint32_t *__restrict__ gcur, PT *__restrict__ ent,
+                                                   unsigned long long *__restrict__ n_emit) {
     const uint32_t t = blockIdx.y, lane = threadIdx.x & 31;
     const uint64_t N = a.N, ntiles = (N + 31) / 32;
     const uint32_t *K = a.skey + (uint64_t)t * N;
@@ -676,6 +677,7 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
     PairSmem &W = ps[threadIdx.x / 32];
     uint32_t hp = T0 ? pair_tile(a, K, S, FS, T0 - 1).heads : ~0u;
     PairWin c = pair_tile(a, K, S, FS, T0);
+    unsigned long long emitted = 0;  // counting pass: pairs of this lane's entries
     for (uint64_t T = T0; T < T1; T++) {
         const PairWin n = pair_tile(a, K, S, FS, T + 1);
         // bucket of position L: first position s0 (window coordinates, previous
@@ -717,6 +719,7 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
             __syncwarp();
             const uint32_t cnt = W.cnt[lane], g = c.id >> gshift;
             if (MODE == 0) {
+                emitted += cnt;
                 if (cnt) atomicAdd(gcnt + g, cnt);
             } else if (__any_sync(~0u, cnt != 0)) {
                 W.base[lane] = cnt ? goff[g] + atomicAdd(gcur + g, cnt) : 0;
@@ -737,6 +740,10 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
         }
         hp = c.heads;
         c = n;
+    }
+    if (MODE == 0 && n_emit) {
+        for (int o = 16; o; o >>= 1) emitted += __shfl_down_sync(~0u, emitted, o);
+        if (lane == 0 && emitted) atomicAdd(n_emit, emitted);
     }
 }
 
@@ -1031,7 +1038,7 @@ __global__ void __launch_bounds__(512) k_long_vote(VoteArgs A, const PT *__restr
 __global__ void __launch_bounds__(256) k_dense_rowcount(const DenseTile *__restrict__ tiles, uint64_t ntiles,
                                                         const uint32_t *__restrict__ GT, const uint32_t *__restrict__ ids,
                                                         uint64_t nm, uint32_t nb, uint32_t v, uint32_t excl,
-                                                        uint32_t *__restrict__ dense_cnt) {
+                                                        uint32_t *__restrict__ dense_cnt, uchar4 *__restrict__ tv) {
     extern __shared__ uint32_t sd[];
     uint32_t *sA = sd, *sB = sd + (size_t)nb * kDT;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -1056,6 +1063,11 @@ __global__ void __launch_bounds__(256) k_dense_rowcount(const DenseTile *__restr
 #pragma unroll
                 for (int w = 0; w < 4; w++) acc[u][w] += A4[u] == B4[w];
         }
+        // the tile's votes, kept for the emit pass: row ty*4+u, columns tx*4 .. +3
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            tv[ti * (kDT * kDT / 4) + (ty * 4 + u) * (kDT / 4) + tx] =
+                make_uchar4((uint8_t)acc[u][0], (uint8_t)acc[u][1], (uint8_t)acc[u][2], (uint8_t)acc[u][3]);
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             const uint32_t ga = T.ta * kDT + ty * 4 + u;
@@ -1075,31 +1087,25 @@ __global__ void __launch_bounds__(256) k_dense_rowcount(const DenseTile *__restr
 
 // Dense groups, emit pass: one CTA per strip (group, row tile ta), column
 // tiles taken in increasing order so every row's detections are written in
-// increasing j at row_off[i] + (running count).
+// increasing j at row_off[i] + (running count).  The votes come from the
+// counting pass's tile buffer: tile (ta, tb) of a group with nt tiles per
+// side is number t0 + ta*nt - ta*(ta-1)/2 + (tb - ta).
 struct DenseStrip {
-    uint32_t g0, n, ta, pad;
+    uint32_t g0, n, ta, t0;
 };
 
 __global__ void __launch_bounds__(256) k_dense_rows(const DenseStrip *__restrict__ strips, uint64_t nstrips,
-                                                    const uint32_t *__restrict__ GT, const uint32_t *__restrict__ ids,
-                                                    uint64_t nm, uint32_t nb, uint32_t v, uint32_t excl,
-                                                    const uint64_t *__restrict__ row_off, uint32_t *__restrict__ oi,
-                                                    uint32_t *__restrict__ oj, uint8_t *__restrict__ ov) {
-    extern __shared__ uint32_t sd[];
+                                                    const uchar4 *__restrict__ tv, const uint32_t *__restrict__ ids,
+                                                    uint32_t v, uint32_t excl, const uint64_t *__restrict__ row_off,
+                                                    uint32_t *__restrict__ oi, uint32_t *__restrict__ oj,
+                                                    uint8_t *__restrict__ ov) {
     __shared__ uint32_t s_cur[kDT];
-    uint32_t *sA = sd, *sB = sd + (size_t)nb * kDT;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const uint32_t lane = threadIdx.x & 31;
     for (uint64_t si = blockIdx.x; si < nstrips; si += gridDim.x) {
         const DenseStrip S = strips[si];
         const uint32_t nt = (S.n + kDT - 1) / kDT;
-        const uint32_t a0 = S.g0 + S.ta * kDT;
-        const uint32_t na = min((uint32_t)kDT, S.n - S.ta * kDT);
         __syncthreads();
-        for (uint32_t x = threadIdx.x; x < nb * kDT; x += blockDim.x) {
-            const uint32_t t = x / kDT, c = x % kDT;
-            sA[x] = c < na ? GT[(uint64_t)t * nm + a0 + c] : 0xFFFFFFFFu;
-        }
         if (threadIdx.x < kDT) s_cur[threadIdx.x] = 0;
         uint32_t rid[4];
 #pragma unroll
@@ -1107,24 +1113,17 @@ __global__ void __launch_bounds__(256) k_dense_rows(const DenseStrip *__restrict
             const uint32_t ga = S.ta * kDT + ty * 4 + u;
             rid[u] = ga < S.n ? ids[S.g0 + ga] : 0;
         }
+        const uint64_t trow = (uint64_t)S.t0 + (uint64_t)S.ta * nt - (uint64_t)S.ta * (S.ta - 1) / 2 - S.ta;
+        __syncthreads();
         for (uint32_t tb = S.ta; tb < nt; tb++) {
-            const uint32_t b0 = S.g0 + tb * kDT;
-            const uint32_t nbb = min((uint32_t)kDT, S.n - tb * kDT);
-            __syncthreads();
-            for (uint32_t x = threadIdx.x; x < nb * kDT; x += blockDim.x) {
-                const uint32_t t = x / kDT, c = x % kDT;
-                sB[x] = c < nbb ? GT[(uint64_t)t * nm + b0 + c] : 0xFFFFFFFEu;
-            }
-            __syncthreads();
-            uint32_t acc[4][4] = {};
-            for (uint32_t t = 0; t < nb; t++) {
-                const uint4 av = *reinterpret_cast<const uint4 *>(sA + t * kDT + ty * 4);
-                const uint4 bv = *reinterpret_cast<const uint4 *>(sB + t * kDT + tx * 4);
-                const uint32_t A4[4] = {av.x, av.y, av.z, av.w}, B4[4] = {bv.x, bv.y, bv.z, bv.w};
+            uint32_t acc[4][4];
 #pragma unroll
-                for (int u = 0; u < 4; u++)
-#pragma unroll
-                    for (int w = 0; w < 4; w++) acc[u][w] += A4[u] == B4[w];
+            for (int u = 0; u < 4; u++) {
+                const uchar4 q = tv[(trow + tb) * (kDT * kDT / 4) + (ty * 4 + u) * (kDT / 4) + tx];
+                acc[u][0] = q.x;
+                acc[u][1] = q.y;
+                acc[u][2] = q.z;
+                acc[u][3] = q.w;
             }
             uint32_t jid[4];
 #pragma unroll
@@ -1571,18 +1570,24 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     const uint64_t nwarps = (ntiles + tpw - 1) / tpw;
     const dim3 eg((unsigned)std::max<uint64_t>(1, (nwarps + 7) / 8), p.b);
     const unsigned mg = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(nmedium, c->num_sms * 8));
-    k_pairs_grp<0, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, tpw, gcnt, nullptr, nullptr, nullptr), FAST_LAUNCHED(c);
+    cudaMemsetAsync(scal + Scal::NSMALLEMIT, 0, 8, s);
+    k_pairs_grp<0, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, tpw, gcnt, nullptr, nullptr, nullptr,
+                                          scal + Scal::NSMALLEMIT), FAST_LAUNCHED(c);
     if (nmedium)
         k_medium_grp<0, PT><<<mg, 256, 0, s>>>(ea, medium, scal + Scal::NMEDIUM, gshift, nbits, gcnt, nullptr, nullptr,
                                                nullptr), FAST_LAUNCHED(c);
     if ((st = scan_excl(c, gcnt, goff, ng, 1, goff + ng, s))) return st;
     uint64_t S = 0;
     cudaMemcpyAsync(&S, goff + ng, 8, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(c->h_scal + Scal::NSMALLEMIT, scal + Scal::NSMALLEMIT, 8, cudaMemcpyDeviceToHost, s);
     if ((st = sync_check(c, s, "pair count"))) return st;
     S_out = S;
+    c->stats.n_pairs_small = c->h_scal[Scal::NSMALLEMIT];
     if ((st = alloc(&ent, S))) return st;
     stage_mark(c, 10, s);
-    k_pairs_grp<1, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, tpw, nullptr, goff, gcur, ent), FAST_LAUNCHED(c);
+    k_pairs_grp<1, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, tpw, nullptr, goff, gcur, ent, nullptr),
+        FAST_LAUNCHED(c);
+    stage_mark(c, 12, s);
     if (nmedium)
         k_medium_grp<1, PT><<<mg, 256, 0, s>>>(ea, medium, scal + Scal::NMEDIUM, gshift, nbits, nullptr, goff, gcur,
                                                ent), FAST_LAUNCHED(c);
@@ -1611,9 +1616,11 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
         cudaMemsetAsync(sp_cnt, 0, N * 4, s);
         cudaMemsetAsync(scal + Scal::CUR_SPARSE, 0, 8, s);
         cudaMemsetAsync(scal + Scal::NLONG, 0, 8, s);
+        stage_mark(c, 13, s);
         k_group_vote<PT><<<(unsigned)std::max<uint64_t>(
                                1, std::min<uint64_t>(ng, (uint64_t)c->num_sms * std::max(vper, 1))),
                            256, vsm, s>>>(va, ent), FAST_LAUNCHED(c);
+        stage_mark(c, 14, s);
         if ((st = read_scal(c, s, "row votes"))) return st;
         const uint64_t nlong = c->h_scal[Scal::NLONG];
         if (nlong > N) return set_error(c, FAST_EINTERNAL, "long-row list overflow");
@@ -1709,6 +1716,7 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
     uint64_t nm = 0, dense_pairs = 0, ngroups = 0;
     std::vector<DenseTile> tiles;
     std::vector<DenseStrip> strips;
+    uchar4 *tvotes = nullptr;  // votes of every dense tile, 64 x 64 bytes each
     DenseTile *d_tiles = nullptr;
     DenseStrip *d_strips = nullptr;
     const size_t dsm = (size_t)2 * nb * kDT * 4;
@@ -1751,9 +1759,10 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
             const uint32_t n = (uint32_t)(g1 - g0);
             ngroups++;
             dense_pairs += (uint64_t)n * (n - 1) / 2;
+            const uint32_t gt0 = (uint32_t)tiles.size();  // the group's first tile
             const uint32_t nt = (n + kDT - 1) / kDT;
             for (uint32_t a = 0; a < nt; a++) {
-                strips.push_back({(uint32_t)g0, n, a, 0});
+                strips.push_back({(uint32_t)g0, n, a, gt0});
                 for (uint32_t b = a; b < nt; b++) tiles.push_back({(uint32_t)g0, n, a, b});
             }
             g0 = g1;
@@ -1765,11 +1774,11 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
         if ((st = alloc(&d_tiles, tiles.size())) || (st = alloc(&d_strips, strips.size()))) return fail(st);
         cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(DenseTile), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_strips, strips.data(), strips.size() * sizeof(DenseStrip), cudaMemcpyHostToDevice, s);
+        if ((st = alloc(&tvotes, tiles.size() * (kDT * kDT / 4)))) return fail(st);
         cudaFuncSetAttribute(k_dense_rowcount, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
-        cudaFuncSetAttribute(k_dense_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
         const unsigned dg = (unsigned)std::min<uint64_t>(tiles.size(), (uint64_t)c->num_sms * 4);
-        k_dense_rowcount<<<dg, 256, dsm, s>>>(d_tiles, tiles.size(), GT, ids, nm, nb, p.v, p.excl, dense_cnt),
-            FAST_LAUNCHED(c);
+        k_dense_rowcount<<<dg, 256, dsm, s>>>(d_tiles, tiles.size(), GT, ids, nm, nb, p.v, p.excl, dense_cnt,
+                                              tvotes), FAST_LAUNCHED(c);
     }
     stage_mark(c, 5, s);
 
@@ -1828,8 +1837,8 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
         return fail(st);
     }
     if (!strips.empty())
-        k_dense_rows<<<(unsigned)std::min<uint64_t>(strips.size(), (uint64_t)c->num_sms * 4), 256, dsm, s>>>(
-            d_strips, strips.size(), GT, ids, nm, nb, p.v, p.excl, row_off, res->d_i, res->d_j, res->d_votes),
+        k_dense_rows<<<(unsigned)std::min<uint64_t>(strips.size(), (uint64_t)c->num_sms * 8), 256, 0, s>>>(
+            d_strips, strips.size(), tvotes, ids, p.v, p.excl, row_off, res->d_i, res->d_j, res->d_votes),
             FAST_LAUNCHED(c);
     uint32_t *merge_rows = reinterpret_cast<uint32_t *>(long_rows);  // reuse: the long-row list is consumed
     uint64_t *mofs = nullptr;

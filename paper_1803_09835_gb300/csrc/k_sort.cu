@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kThreads) k_hist(const KT *__restrict__ keys, 
     const int warp = threadIdx.x >> 5;
     const uint32_t *vv = STD ? vals + (uint64_t)seg * len : nullptr;
     for (uint64_t e = lo + threadIdx.x; e < hi; e += kThreads)
-        atomicAdd(&h[warp][STD ? station_of(S, vv[e]) : digit_of(k[e], shift)], 1u);
+        atomicAdd(&h[warp][STD ? station_of(S, __ldcs(vv + e)) : digit_of(__ldcs(k + e), shift)], 1u);
     __syncthreads();
     uint32_t d = threadIdx.x, tot = 0;
 #pragma unroll
@@ -143,8 +143,9 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const KT *__restrict__ kin
         for (int j = 0; j < kItems; j++) {
             const uint32_t e = warp * (kItems * 32) + j * 32 + lane;
             const bool valid = e < nvalid;
-            key[j] = valid ? ki[sbase + e] : (KT)0;
-            if (HAS_VAL) val[j] = valid ? (IOTA ? (uint32_t)(sbase + e) : vi[sbase + e]) : 0u;
+            // streaming loads (evict-first): the L2 keeps the write frontier of the digit runs
+            key[j] = valid ? __ldcs(ki + sbase + e) : (KT)0;
+            if (HAS_VAL) val[j] = valid ? (IOTA ? (uint32_t)(sbase + e) : __ldcs(vi + sbase + e)) : 0u;
         }
 #pragma unroll
         for (int j = 0; j < kItems; j++) {
