@@ -748,56 +748,106 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
 }
 
 // Medium buckets (more than kSmall entries, fewer than large_min live): one
-// CTA per bucket, live members compacted in shared memory when they fit.
+// CTA per bucket.  Live members (id, group label) are compacted in shared
+// memory; a bucket whose members all lie in one dense group has no sparse
+// pairs and is skipped.  Rows x are handed to warps one at a time and a warp's
+// lanes take the row's partners y > x 32 at a time, so the triangle of pairs
+// is shared evenly.  Buckets too large for shared memory fall back to one
+// thread per row over global memory.
+constexpr uint32_t kMedCap = 4096;
+
 template <int MODE, typename PT>
 __global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, const uint4 *__restrict__ medium,
                                                     const unsigned long long *__restrict__ nmedium, uint32_t gshift,
                                                     uint32_t nbits, uint32_t *__restrict__ gcnt,
                                                     const uint64_t *__restrict__ goff, uint32_t *__restrict__ gcur,
                                                     PT *__restrict__ ent) {
-    __shared__ uint32_t s_m[kMedSmem];
+    __shared__ uint32_t s_id[kMedCap], s_lab[kMedCap];
     __shared__ uint32_t wsum[32];
+    __shared__ uint32_t s_next, s_mixed;
     const uint64_t n = *nmedium;
-    const uint32_t lmask = (1u << gshift) - 1;
+    const uint32_t lmask = (1u << gshift) - 1, lane = threadIdx.x & 31;
     for (uint64_t bi = blockIdx.x; bi < n; bi += gridDim.x) {
         const uint4 e = medium[bi];
         const uint32_t *s = a.sid + (uint64_t)e.x * a.N;
-        const bool in_smem = e.w <= kMedSmem;
-        uint32_t nl = 0;
-        if (in_smem) {
-            for (uint32_t q0 = e.y; q0 < e.z; q0 += blockDim.x) {
-                const uint32_t q = q0 + threadIdx.x;
-                uint32_t id = 0, live = 0;
-                if (q < e.z) {
-                    id = s[q];
-                    live = !a.drop[id];
+        if (e.w > kMedCap) {  // block-uniform: fallback over global memory
+            for (uint32_t x = e.y + threadIdx.x; x < e.z; x += blockDim.x) {
+                const uint32_t i = s[x];
+                if (a.drop[i]) continue;
+                uint32_t c = 0;
+                for (uint32_t y = x + 1; y < e.z; y++) {
+                    const uint32_t j = s[y];
+                    c += !a.drop[j] && pair_live(a, i, j);
                 }
-                uint32_t tot;
-                const uint32_t pos = block_excl_scan(live, wsum, &tot);
-                if (live && nl + pos < kMedSmem) s_m[nl + pos] = id;
-                nl += tot;
+                if (!c) continue;
+                const uint32_t g = i >> gshift;
+                if (MODE == 0) {
+                    atomicAdd(gcnt + g, c);
+                } else {
+                    uint64_t o = goff[g] + atomicAdd(gcur + g, c);
+                    for (uint32_t y = x + 1; y < e.z; y++) {
+                        const uint32_t j = s[y];
+                        if (!a.drop[j] && pair_live(a, i, j)) ent[o++] = pack_entry<PT>(i & lmask, j, nbits);
+                    }
+                }
             }
-            nl = min(nl, kMedSmem);
             __syncthreads();
+            continue;
         }
-        const uint32_t lo = in_smem ? 0 : e.y, hi = in_smem ? nl : e.z;
-        for (uint32_t x = lo + threadIdx.x; x < hi; x += blockDim.x) {
-            const uint32_t i = in_smem ? s_m[x] : s[x];
-            if (!in_smem && a.drop[i]) continue;
-            uint32_t c = 0;
-            for (uint32_t y = x + 1; y < hi; y++) {
-                const uint32_t j = in_smem ? s_m[y] : s[y];
-                c += (in_smem || !a.drop[j]) && pair_live(a, i, j);
+        uint32_t nl = 0;
+        if (threadIdx.x == 0) {
+            s_next = 0;
+            s_mixed = 0;
+        }
+        for (uint32_t q0 = e.y; q0 < e.z; q0 += blockDim.x) {
+            const uint32_t q = q0 + threadIdx.x;
+            uint32_t id = 0, live = 0;
+            if (q < e.z) {
+                id = s[q];
+                live = !a.drop[id];
             }
-            if (!c) continue;
-            const uint32_t g = i >> gshift;
-            if (MODE == 0) {
-                atomicAdd(gcnt + g, c);
-            } else {
-                uint64_t o = goff[g] + atomicAdd(gcur + g, c);
-                for (uint32_t y = x + 1; y < hi; y++) {
-                    const uint32_t j = in_smem ? s_m[y] : s[y];
-                    if ((in_smem || !a.drop[j]) && pair_live(a, i, j)) ent[o++] = pack_entry<PT>(i & lmask, j, nbits);
+            uint32_t tot;
+            const uint32_t pos = block_excl_scan(live, wsum, &tot);
+            if (live && nl + pos < kMedCap) {
+                s_id[nl + pos] = id;
+                s_lab[nl + pos] = a.label ? __ldg(a.label + id) : kNone;
+            }
+            nl += tot;
+        }
+        nl = min(nl, kMedCap);
+        __syncthreads();
+        for (uint32_t x = threadIdx.x; x < nl; x += blockDim.x)
+            if (s_lab[x] == kNone || s_lab[x] != s_lab[0]) s_mixed = 1;
+        __syncthreads();
+        if (s_mixed) {  // block-uniform
+            for (;;) {
+                uint32_t x = 0;
+                if (lane == 0) x = atomicAdd(&s_next, 1u);
+                x = __shfl_sync(~0u, x, 0);
+                if (x + 1 >= nl) break;  // warp-uniform
+                const uint32_t i = s_id[x], li = s_lab[x], g = i >> gshift;
+                uint32_t c = 0;
+                for (uint32_t y = x + 1 + lane; y < nl; y += 32) {
+                    const uint32_t lj = s_lab[y];
+                    c += s_id[y] - i > a.excl && (li == kNone || li != lj);
+                }
+#pragma unroll
+                for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(~0u, c, o);
+                if (!c) continue;
+                if (MODE == 0) {
+                    if (lane == 0) atomicAdd(gcnt + g, c);
+                } else {
+                    uint64_t o = 0;
+                    if (lane == 0) o = goff[g] + atomicAdd(gcur + g, c);
+                    o = __shfl_sync(~0u, o, 0);
+                    for (uint32_t y0 = x + 1; y0 < nl; y0 += 32) {
+                        const uint32_t y = y0 + lane;
+                        const uint32_t j = y < nl ? s_id[y] : 0u;
+                        const bool keep = y < nl && j - i > a.excl && (li == kNone || li != s_lab[y]);
+                        const uint32_t m = __ballot_sync(~0u, keep);
+                        if (keep) ent[o + __popc(m & ((1u << lane) - 1))] = pack_entry<PT>(i & lmask, j, nbits);
+                        o += __popc(m);
+                    }
                 }
             }
         }
