@@ -1289,44 +1289,72 @@ __global__ void k_add_u32(const uint32_t *__restrict__ a, const uint32_t *__rest
         out[x] = a[x] + b[x];
 }
 
-// Big buckets only (no pair work): the rows path counts pairs separately.
-__global__ void __launch_bounds__(256) k_find_big(EnumArgs a, uint4 *__restrict__ big,
+// Big buckets (more than kSmall entries) of every table, and the pairs of the
+// small ones (an upper bound of the sparse work).  A warp walks runs of
+// 32-entry tiles with the head bitmasks of the current and next tile: a
+// bucket starting at lane L ends at the next head; with no head in the two
+// tiles it is big and its end is found by galloping.
+__device__ __forceinline__ uint32_t head_bits(const uint32_t *__restrict__ K, const Stations &st, uint64_t N,
+                                              uint64_t T) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t x = T * 32 + lane;
+    const bool valid = x < N;
+    const uint32_t key = valid ? __ldcs(K + x) : 0u;
+    uint32_t kprev = __shfl_up_sync(~0u, key, 1);
+    if (lane == 0 && valid && x > 0) kprev = K[x - 1];
+    bool head = !valid || x == 0 || key != kprev;
+    if (st.nst > 1 && valid && !head) head = st.soff[station_of(st, x)] == x;
+    return __ballot_sync(~0u, head);
+}
+
+__global__ void __launch_bounds__(256) k_find_big(EnumArgs a, uint32_t tiles_per_warp, uint4 *__restrict__ big,
                                                   unsigned long long *__restrict__ nbig, uint64_t big_cap,
                                                   unsigned long long *__restrict__ small_pairs, uint32_t *err) {
-    const uint32_t t = blockIdx.y;
-    const uint64_t N = a.N;
+    const uint32_t t = blockIdx.y, lane = threadIdx.x & 31;
+    const uint64_t N = a.N, ntiles = (N + 31) / 32;
     const uint32_t *k = a.skey + (uint64_t)t * N;
+    const uint64_t T0 = ((uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32) * tiles_per_warp;
+    if (T0 >= ntiles) return;  // warp-uniform
+    const uint64_t T1 = min(T0 + tiles_per_warp, ntiles);
     unsigned long long pairs = 0;
-    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t sx = station_of(a.st, p);
-        const uint64_t s0 = a.st.soff[sx], s1 = a.st.soff[sx + 1];
-        const uint32_t key = k[p];
-        if (p > s0 && k[p - 1] == key) continue;
-        uint64_t e = p + 1;
-        while (e < s1 && e - p <= kSmall && k[e] == key) e++;
-        if (e - p <= kSmall) {  // small bucket: its pairs bound the sparse work
-            pairs += (e - p) * (e - p - 1) / 2;
-            continue;
+    uint32_t hc = head_bits(k, a.st, N, T0);
+    for (uint64_t T = T0; T < T1; T++) {
+        const uint32_t hn = head_bits(k, a.st, N, T + 1);
+        const uint64_t x = T * 32 + lane;
+        if (x < N && (hc >> lane & 1)) {
+            const uint64_t above = ((uint64_t)hn << 32 | hc) & ~((2ull << lane) - 1);
+            const uint32_t e = above ? (uint32_t)__ffsll((long long)above) - 1 : 64u;
+            const uint32_t size = e - lane;
+            if (e < 64 && size <= kSmall) {
+                pairs += (unsigned long long)size * (size - 1) / 2;
+            } else {
+                uint64_t hi = x + size;  // exact when the end lies in the window
+                if (e == 64) {  // gallop from the last position of the window, which is in the bucket
+                    const uint64_t s1 = a.st.soff[station_of(a.st, x) + 1];
+                    const uint32_t key = k[x];
+                    uint64_t lo = x + size - 1, step = 1;
+                    for (;;) {
+                        hi = lo + step;
+                        if (hi >= s1 || k[hi] != key) break;
+                        lo = hi;
+                        step <<= 1;
+                    }
+                    if (hi > s1) hi = s1;
+                    while (hi - lo > 1) {
+                        const uint64_t mid = lo + (hi - lo) / 2;
+                        if (k[mid] == key) lo = mid;
+                        else hi = mid;
+                    }
+                }
+                const unsigned long long slot = atomicAdd(nbig, 1ull);
+                if (slot < big_cap) big[slot] = make_uint4(t, (uint32_t)x, (uint32_t)hi, 0);
+                else set_err(err, ERR_OVERFLOW);
+            }
         }
-        uint64_t lo = p + kSmall, step = 1, hi;
-        for (;;) {
-            hi = lo + step;
-            if (hi >= s1 || k[hi] != key) break;
-            lo = hi;
-            step <<= 1;
-        }
-        if (hi > s1) hi = s1;
-        while (hi - lo > 1) {
-            uint64_t mid = lo + (hi - lo) / 2;
-            if (k[mid] == key) lo = mid;
-            else hi = mid;
-        }
-        unsigned long long slot = atomicAdd(nbig, 1ull);
-        if (slot < big_cap) big[slot] = make_uint4(t, (uint32_t)p, (uint32_t)hi, 0);
-        else set_err(err, ERR_OVERFLOW);
+        hc = hn;
     }
     for (int o = 16; o; o >>= 1) pairs += __shfl_down_sync(~0u, pairs, o);
-    if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(small_pairs, pairs);
+    if (lane == 0 && pairs) atomicAdd(small_pairs, pairs);
 }
 
 uint32_t bits_for(uint64_t N) {
@@ -1345,6 +1373,13 @@ uint32_t large_min_for(const fast_ctx *c, uint64_t N) {
     if (c->large_min) return c->large_min;
     const double ptop = std::pow((double)c->p.K / c->p.D, (double)c->p.r);
     return (uint32_t)std::max(512.0, std::min(1e9, 8.0 * N * ptop));
+}
+
+// Tiles of 32 table entries per warp for the warp-window passes: enough warps
+// for ~16 resident per SM slot over all tables, at most 64 tiles each.
+static uint32_t tiles_per_warp(const fast_ctx *c, uint64_t N, uint32_t nb) {
+    const uint64_t ntiles = (N + 31) / 32;
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(64, ntiles * nb / ((uint64_t)c->num_sms * 64 * 16)));
 }
 
 // ------------------------------------------------------------ host side
@@ -1613,10 +1648,9 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     if ((st = alloc(&gcnt, ng)) || (st = alloc(&gcur, ng)) || (st = alloc(&goff, ng + 1))) return st;
     cudaMemsetAsync(gcnt, 0, ng * 4, s);
     cudaMemsetAsync(gcur, 0, ng * 4, s);
-    // small-bucket pairs: warps over runs of 32-entry tiles, about 16 warps per SM slot in all
+    // small-bucket pairs: warps over runs of 32-entry tiles
     const uint64_t ntiles = (N + 31) / 32;
-    const uint32_t tpw = (uint32_t)std::max<uint64_t>(
-        1, std::min<uint64_t>(64, ntiles * p.b / ((uint64_t)c->num_sms * 64 * 16)));
+    const uint32_t tpw = tiles_per_warp(c, N, p.b);
     const uint64_t nwarps = (ntiles + tpw - 1) / tpw;
     const dim3 eg((unsigned)std::max<uint64_t>(1, (nwarps + 7) / 8), p.b);
     const unsigned mg = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(nmedium, c->num_sms * 8));
@@ -1748,8 +1782,9 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
     uint4 *big = nullptr, *large = nullptr, *medium = nullptr;
     if ((st = alloc(&big, big_cap))) return fail(st);
     EnumArgs ea{tb->d_skey, tb->d_sid, tb->d_drop, nullptr, nullptr, N, p.excl, 0, (uint32_t)N, 1, {tb->d_soff, tb->nst}};
-    const dim3 eg(std::max(1u, std::min<unsigned>(ceil_div(N, 256), 2048)), nb);
-    k_find_big<<<eg, 256, 0, s>>>(ea, big, scal + Scal::NBIG, big_cap, scal + Scal::SMALLPAIRS, c->d_err),
+    const uint32_t ftpw = tiles_per_warp(c, N, nb);
+    const dim3 eg((unsigned)std::max<uint64_t>(1, (((N + 31) / 32 + ftpw - 1) / ftpw + 7) / 8), nb);
+    k_find_big<<<eg, 256, 0, s>>>(ea, ftpw, big, scal + Scal::NBIG, big_cap, scal + Scal::SMALLPAIRS, c->d_err),
         FAST_LAUNCHED(c);
     if ((st = read_scal(c, s, "bucket scan"))) return fail(st);
     const uint64_t nbig = c->h_scal[Scal::NBIG];
@@ -1992,8 +2027,9 @@ fast_status history_groups(fast_ctx *c, const fast_tables *tb, const uint32_t *d
     if ((st = dalloc_t(c, &big, big_cap, s))) return st;
     cudaMemsetAsync(scal, 0, sizeof(uint64_t) * kScal, s);
     EnumArgs ea{tb->d_skey, tb->d_sid, tb->d_drop, nullptr, nullptr, N, p.excl, 0, (uint32_t)N, 1, {tb->d_soff, tb->nst}};
-    const dim3 eg(std::max(1u, std::min<unsigned>(ceil_div(N, 256), 2048)), nb);
-    k_find_big<<<eg, 256, 0, s>>>(ea, big, scal + Scal::NBIG, big_cap, scal + Scal::SMALLPAIRS, c->d_err),
+    const uint32_t ftpw = tiles_per_warp(c, N, nb);
+    const dim3 eg((unsigned)std::max<uint64_t>(1, (((N + 31) / 32 + ftpw - 1) / ftpw + 7) / 8), nb);
+    k_find_big<<<eg, 256, 0, s>>>(ea, ftpw, big, scal + Scal::NBIG, big_cap, scal + Scal::SMALLPAIRS, c->d_err),
         FAST_LAUNCHED(c);
     if ((st = read_scal(c, s, "history buckets"))) {
         dfree(c, big, big_cap * 16, s);
