@@ -107,17 +107,30 @@ __global__ void __launch_bounds__(1024) k_scan(const uint32_t *__restrict__ coun
     }
 }
 
+// Dynamic shared memory of k_scatter: the whole chunk staged in digit order.
+template <typename KT, bool HAS_VAL>
+constexpr size_t scatter_smem() {
+    return (size_t)kChunk * (sizeof(KT) + (HAS_VAL ? 4 : 0));
+}
+
+// One chunk (8192 keys) per CTA.  The chunk's digit starts come from its
+// k_hist counts; its four sub-tiles of 2048 are ranked one after another
+// (stable: warp ballots, per-warp counters, running per-digit counts) into a
+// shared-memory copy of the chunk in digit order, which is then written out
+// once: each digit's run (~32 keys, 128 bytes) goes to run[d] onwards.
 template <typename KT, bool HAS_VAL, bool IOTA, bool STD = false>
-__global__ void __launch_bounds__(kThreads) k_scatter(const KT *__restrict__ kin, const uint32_t *__restrict__ vin,
+__global__ void __launch_bounds__(kThreads, 3) k_scatter(const KT *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                       KT *__restrict__ kout, uint32_t *__restrict__ vout, uint64_t len,
                                                       uint32_t nchunks, uint32_t shift,
+                                                      const uint32_t *__restrict__ counts,
                                                       const uint64_t *__restrict__ offsets,
                                                       Stations S = Stations{nullptr, 1}) {
+    extern __shared__ unsigned long long sc_raw[];
+    KT *sk = reinterpret_cast<KT *>(sc_raw);                         // [kChunk]
+    uint32_t *sv = reinterpret_cast<uint32_t *>(sk + kChunk);        // [kChunk] when HAS_VAL
     __shared__ uint64_t run[kRadix];
-    __shared__ uint32_t wcnt[kWarps][kRadix];
-    __shared__ uint32_t tot[kRadix], dstart[kRadix], wscan[kWarps];
-    __shared__ KT sk[kSub];
-    __shared__ uint32_t sv[HAS_VAL ? kSub : 1];
+    __shared__ uint16_t wcnt[kWarps][kRadix];  // <= 2048 per sub-tile: 16 bits; small enough for 3 CTAs per SM
+    __shared__ uint32_t tot[kRadix], cstart[kRadix], crun[kRadix], wscan[kWarps];
 
     const uint32_t seg = blockIdx.y, chunk = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -126,11 +139,29 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const KT *__restrict__ kin
     const uint32_t *vi = HAS_VAL && !IOTA ? vin + (uint64_t)seg * len : nullptr;
     KT *ko = kout + (uint64_t)seg * len;
     uint32_t *vo = HAS_VAL ? vout + (uint64_t)seg * len : nullptr;
-    run[threadIdx.x] = offsets[((uint64_t)seg * kRadix + threadIdx.x) * nchunks + chunk];
+    const uint64_t cbase = (uint64_t)chunk * kChunk;
+    const uint32_t cvalid = (uint32_t)std::min<uint64_t>(kChunk, len - cbase);
+    {   // the chunk's digit starts: exclusive scan of its counts over the 256 digits
+        const uint32_t d = threadIdx.x;
+        run[d] = offsets[((uint64_t)seg * kRadix + d) * nchunks + chunk];
+        const uint32_t cnt = counts[((uint64_t)seg * kRadix + d) * nchunks + chunk];
+        uint32_t x = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(~0u, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wscan[warp] = x;
+        __syncthreads();
+        uint32_t add = 0;
+        for (int w = 0; w < warp; w++) add += wscan[w];
+        cstart[d] = x - cnt + add;
+        crun[d] = 0;
+    }
 
     for (int sub = 0; sub < kSubPerChunk; sub++) {
-        const uint64_t sbase = (uint64_t)chunk * kChunk + (uint64_t)sub * kSub;
-        if (sbase >= len) break;
+        const uint64_t sbase = cbase + (uint64_t)sub * kSub;
+        if (sbase >= len) break;  // block-uniform
         const uint32_t nvalid = (uint32_t)std::min<uint64_t>(kSub, len - sbase);
 #pragma unroll
         for (int w = 0; w < kWarps; w++) wcnt[w][threadIdx.x] = 0;
@@ -157,57 +188,68 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const KT *__restrict__ kin
             uint32_t basec = 0;
             if (valid) basec = wcnt[warp][dig[j]];
             __syncwarp();
-            if (valid && before == 0) wcnt[warp][dig[j]] = basec + __popc(peers);
+            if (valid && before == 0) wcnt[warp][dig[j]] = (uint16_t)(basec + __popc(peers));
             __syncwarp();
             rnk[j] = basec + __popc(before);
         }
         __syncthreads();
-        {   // per digit: exclusive prefix over warps, sub-tile totals
+        {   // per digit: exclusive prefix over warps; the sub-tile's total
             const uint32_t d = threadIdx.x;
             uint32_t r = 0;
 #pragma unroll
             for (int w = 0; w < kWarps; w++) {
-                uint32_t c = wcnt[w][d];
-                wcnt[w][d] = r;
+                const uint32_t c = wcnt[w][d];
+                wcnt[w][d] = (uint16_t)r;
                 r += c;
             }
             tot[d] = r;
-            // exclusive scan of tot over the 256 digits
-            uint32_t x = r;
-#pragma unroll
-            for (int s = 1; s < 32; s <<= 1) {
-                uint32_t y = __shfl_up_sync(~0u, x, s);
-                if (lane >= s) x += y;
-            }
-            if (lane == 31) wscan[warp] = x;
-            __syncthreads();
-            uint32_t add = 0;
-            for (int w = 0; w < warp; w++) add += wscan[w];
-            dstart[d] = x - r + add;
         }
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < kItems; j++) {
             if (dig[j] < (uint32_t)kRadix) {
-                uint32_t pos = dstart[dig[j]] + wcnt[warp][dig[j]] + rnk[j];
+                const uint32_t pos = cstart[dig[j]] + crun[dig[j]] + wcnt[warp][dig[j]] + rnk[j];
                 sk[pos] = key[j];
                 if (HAS_VAL) sv[pos] = val[j];
             }
         }
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < nvalid; i += kThreads) {
-            KT k = sk[i];
-            uint32_t d;
-            if constexpr (STD) d = station_of(S, sv[i]);
-            else d = digit_of(k, shift);
-            uint64_t o = run[d] + (i - dstart[d]);
-            ko[o] = k;
-            if (HAS_VAL) vo[o] = sv[i];
-        }
-        __syncthreads();
-        run[threadIdx.x] += tot[threadIdx.x];
-        __syncthreads();
+        crun[threadIdx.x] += tot[threadIdx.x];
     }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < cvalid; i += kThreads) {
+        const KT k = sk[i];
+        uint32_t d;
+        if constexpr (STD) d = station_of(S, sv[i]);
+        else d = digit_of(k, shift);
+        const uint64_t o = run[d] + (i - cstart[d]);
+        ko[o] = k;
+        if (HAS_VAL) vo[o] = sv[i];
+    }
+}
+
+// Opt every k_scatter instantiation into its dynamic shared memory (once per
+// process and device; the attribute outlives the call).
+void scatter_attrs() {
+    static std::mutex mu;
+    static std::vector<int> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+    cudaFuncSetAttribute(k_scatter<uint32_t, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)scatter_smem<uint32_t, true>());
+    cudaFuncSetAttribute(k_scatter<uint32_t, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)scatter_smem<uint32_t, true>());
+    cudaFuncSetAttribute(k_scatter<uint32_t, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)scatter_smem<uint32_t, true>());
+    cudaFuncSetAttribute(k_scatter<uint64_t, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)scatter_smem<uint64_t, false>());
+    cudaFuncSetAttribute(k_scatter<uint64_t, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)scatter_smem<uint64_t, true>());
+    cudaFuncSetAttribute(k_scatter<uint64_t, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)scatter_smem<uint64_t, true>());
+    done.push_back(dev);
 }
 
 template <typename KT, bool HAS_VAL>
@@ -236,6 +278,7 @@ fast_status sort_impl(fast_ctx *c, uint32_t nseg, uint64_t len, const KT *keys_i
     const KT *src_k = keys_in;
     const uint32_t *src_v = vals_in;
     dim3 grid(nchunks, nseg);
+    scatter_attrs();
     for (uint32_t pass = 0; pass < npass; pass++) {
         const uint32_t shift = bit0 + 8 * pass;
         KT *dk = (pass & 1) ? kb : ka;
@@ -243,12 +286,14 @@ fast_status sort_impl(fast_ctx *c, uint32_t nseg, uint64_t len, const KT *keys_i
         k_hist<KT><<<grid, kThreads, 0, s>>>(src_k, len, nchunks, shift, counts), FAST_LAUNCHED(c);
         if ((st = scan_excl(c, counts, offs, (uint64_t)kRadix * nchunks, nseg, nullptr, s))) break;
         if (HAS_VAL && pass == 0 && src_v == nullptr)
-            k_scatter<KT, true, true><<<grid, kThreads, 0, s>>>(src_k, nullptr, dk, dv, len, nchunks, shift, offs), FAST_LAUNCHED(c);
+            k_scatter<KT, true, true><<<grid, kThreads, scatter_smem<KT, true>(), s>>>(
+                src_k, nullptr, dk, dv, len, nchunks, shift, counts, offs), FAST_LAUNCHED(c);
         else if (HAS_VAL)
-            k_scatter<KT, true, false><<<grid, kThreads, 0, s>>>(src_k, src_v, dk, dv, len, nchunks, shift, offs), FAST_LAUNCHED(c);
+            k_scatter<KT, true, false><<<grid, kThreads, scatter_smem<KT, true>(), s>>>(
+                src_k, src_v, dk, dv, len, nchunks, shift, counts, offs), FAST_LAUNCHED(c);
         else
-            k_scatter<KT, false, false><<<grid, kThreads, 0, s>>>(src_k, nullptr, dk, nullptr, len, nchunks, shift,
-                                                                 offs), FAST_LAUNCHED(c);
+            k_scatter<KT, false, false><<<grid, kThreads, scatter_smem<KT, false>(), s>>>(
+                src_k, nullptr, dk, nullptr, len, nchunks, shift, counts, offs), FAST_LAUNCHED(c);
         src_k = dk;
         src_v = dv;
     }
@@ -285,11 +330,12 @@ fast_status sort_station_pass(fast_ctx *c, uint32_t nseg, uint64_t len, const ui
         return st;
     }
     const dim3 grid(nchunks, nseg);
+    scatter_attrs();
     k_hist<uint32_t, true><<<grid, kThreads, 0, s>>>(keys_in, len, nchunks, 0, counts, vals_in, S), FAST_LAUNCHED(c);
     st = scan_excl(c, counts, offs, (uint64_t)kRadix * nchunks, nseg, nullptr, s);
     if (!st)
-        k_scatter<uint32_t, true, false, true><<<grid, kThreads, 0, s>>>(keys_in, vals_in, keys_out, vals_out, len,
-                                                                         nchunks, 0, offs, S), FAST_LAUNCHED(c);
+        k_scatter<uint32_t, true, false, true><<<grid, kThreads, scatter_smem<uint32_t, true>(), s>>>(
+            keys_in, vals_in, keys_out, vals_out, len, nchunks, 0, counts, offs, S), FAST_LAUNCHED(c);
     dfree(c, counts, entries * 4, s);
     dfree(c, offs, entries * 8, s);
     if (st) return st;
@@ -372,6 +418,7 @@ extern "C" fast_status fast_table_sort_static(const uint32_t *d_keys, uint64_t n
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t nchunks = (uint32_t)((n + kChunk - 1) / kChunk);
     const dim3 grid(nchunks, 1);
+    scatter_attrs();
     // four 8-bit passes: keys -> scratch -> out -> scratch -> out
     const uint32_t *src_k = d_keys, *src_v = nullptr;
     for (uint32_t pass = 0; pass < 4; pass++) {
@@ -381,9 +428,11 @@ extern "C" fast_status fast_table_sort_static(const uint32_t *d_keys, uint64_t n
         k_hist<uint32_t><<<grid, kThreads, 0, s>>>(src_k, n, nchunks, shift, counts);
         k_scan<<<1, 1024, 0, s>>>(counts, offs, nchunks);
         if (pass == 0)
-            k_scatter<uint32_t, true, true><<<grid, kThreads, 0, s>>>(src_k, nullptr, dk, dv, n, nchunks, shift, offs);
+            k_scatter<uint32_t, true, true><<<grid, kThreads, scatter_smem<uint32_t, true>(), s>>>(
+                src_k, nullptr, dk, dv, n, nchunks, shift, counts, offs);
         else
-            k_scatter<uint32_t, true, false><<<grid, kThreads, 0, s>>>(src_k, src_v, dk, dv, n, nchunks, shift, offs);
+            k_scatter<uint32_t, true, false><<<grid, kThreads, scatter_smem<uint32_t, true>(), s>>>(
+                src_k, src_v, dk, dv, n, nchunks, shift, counts, offs);
         src_k = dk;
         src_v = dv;
     }
