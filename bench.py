@@ -346,6 +346,7 @@ def gpu_arm(args, rank, world, local_rank):
     h_j = torch.empty(M, dtype=torch.int32, pin_memory=True)
     h_v = torch.empty(M, dtype=torch.uint8, pin_memory=True)
     from paper_1803_09835_gb300 import fast_detect_host
+    fast_detect_host(s.ctx, h_idx, w.N, ld, h_i, h_j, h_v, M)  # warm-up: the library's pool grows once
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):

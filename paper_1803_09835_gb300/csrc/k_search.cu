@@ -896,10 +896,16 @@ __device__ __forceinline__ bool vadd(uint32_t *K, uint32_t *C, uint32_t slots, u
 // concurrent write frontiers in the emission pass, smaller ones more resident
 // CTAs in the vote.
 constexpr uint32_t kVTargetDefault = 1536;
+// Counting filter in front of the hash: 16-bit counters (never wrap: a group
+// holds at most vcap <= 16384 entries) indexed by a second hash of the entry.
+// An entry whose counter is below v cannot have v copies, so only the few
+// that pass are counted exactly.
+constexpr uint32_t kVFilter = 8192;
+constexpr int kVRegs = 8;  // entries per thread held in registers (groups of up to 2048 at 256 threads)
 
 template <typename PT>
 size_t group_vote_smem(uint32_t vcap) {
-    return (size_t)2 * vcap * sizeof(PT) + (size_t)2 * vcap / 4 * 4;
+    return (size_t)2 * vcap * sizeof(PT) + (size_t)2 * vcap / 4 * 4 + (size_t)kVFilter * 2;
 }
 
 // Slot of a key in a table of 2^lg slots: multiplicative (Fibonacci) hashing,
@@ -908,21 +914,38 @@ __device__ __forceinline__ uint32_t ghash(uint32_t key, uint32_t lg) { return (k
 __device__ __forceinline__ uint32_t ghash(unsigned long long key, uint32_t lg) {
     return (uint32_t)(mix64(key) >> (64 - lg));
 }
+// The counting filter's index: another multiplier, so that filter and hash
+// collisions are independent.
+__device__ __forceinline__ uint32_t fhash(uint32_t key, uint32_t lg) { return (key * 0x85EBCA6Bu) >> (32 - lg); }
+__device__ __forceinline__ uint32_t fhash(unsigned long long key, uint32_t lg) {
+    return (uint32_t)((key * 0xC2B2AE3D27D4EB4Full) >> (64 - lg));
+}
 
 // One CTA per group: every entry (local row, j) of the group counted in one
 // shared-memory hash of >= 2n slots; entries seen at least v times are the
 // group's detections, ordered by (local row, j) -- i.e. by (i, j) -- by rank.
+// One row group of the vote (see k_group_vote): counting filter, exact counts
+// of the entries that pass, kept pairs in (i, j) order.
+#define VOTE_FOR_ENTRIES(raw, BODY)                                                   \
+    if (regs) {                                                                       \
+        _Pragma("unroll") for (int u_ = 0; u_ < kVRegs; u_++) {                      \
+            if (threadIdx.x + (uint64_t)u_ * blockDim.x >= n) continue;              \
+            const PT raw = cur[u_];                                                   \
+            BODY                                                                      \
+        }                                                                             \
+    } else {                                                                          \
+        for (uint64_t x_ = threadIdx.x; x_ < n; x_ += blockDim.x) {                   \
+            const PT raw = ent[e0 + x_];                                              \
+            BODY                                                                      \
+        }                                                                             \
+    }
+
 template <typename PT>
-__global__ void __launch_bounds__(256) k_group_vote(VoteArgs A, const PT *__restrict__ ent) {
-    extern __shared__ unsigned long long vsm_raw[];
-    PT *K = reinterpret_cast<PT *>(vsm_raw);                             // [<= 2 vcap] keys (entry + 1)
-    uint32_t *C = reinterpret_cast<uint32_t *>(K + 2 * A.vcap);          // [<= 2 vcap / 4] byte counts
-    __shared__ uint32_t wsum[32];
-    __shared__ unsigned long long s_b0;
-    const PT jmask = ((PT)1 << A.nbits) - 1;
-    for (uint64_t g = blockIdx.x; g < A.ngroups; g += gridDim.x) {
-        const uint64_t e0 = A.goff[g], n = A.goff[g + 1] - e0;
-        if (n < A.v) continue;  // block-uniform
+__device__ __forceinline__ void vote_one(const VoteArgs &A, const PT *__restrict__ ent, uint64_t g, uint64_t e0,
+                                         uint64_t n, const PT (&cur)[kVRegs], PT *K, uint32_t *C, uint32_t *F,
+                                         uint32_t &s_pass, uint32_t *wsum, unsigned long long &s_b0, PT jmask) {
+    const bool regs = n <= (uint64_t)kVRegs * blockDim.x;
+        if (n < A.v) return;  // block-uniform
         const uint64_t row0 = g << A.gshift;
         if (n > A.vcap) {  // every row of the group is voted one CTA each
             for (uint32_t r = threadIdx.x; r < (1u << A.gshift); r += blockDim.x) {
@@ -930,15 +953,41 @@ __global__ void __launch_bounds__(256) k_group_vote(VoteArgs A, const PT *__rest
                 unsigned long long q = atomicAdd(A.n_long, 1ull);
                 if (q < A.long_cap) A.long_rows[q] = make_uint2((uint32_t)(row0 + r), (uint32_t)n);
             }
-            continue;
+            return;
         }
+        // 1. counting filter
+        uint32_t fc = 64, flg = 6;
+        while (fc < 2 * n && fc < kVFilter) fc <<= 1, flg++;
+        for (uint32_t x = threadIdx.x; x < fc / 2; x += blockDim.x) F[x] = 0;
+        if (threadIdx.x == 0) s_pass = 0;
+        __syncthreads();
+        VOTE_FOR_ENTRIES(raw, {
+            const uint32_t f = fhash(raw, flg);
+            atomicAdd(F + (f >> 1), 1u << (16 * (f & 1)));
+        })
+        __syncthreads();
+        uint32_t mine = 0;
+        VOTE_FOR_ENTRIES(raw, {
+            const uint32_t f = fhash(raw, flg);
+            mine += (F[f >> 1] >> (16 * (f & 1)) & 0xFFFF) >= A.v;
+        })
+        if (mine) atomicAdd(&s_pass, mine);
+        __syncthreads();
+        const uint32_t npass = s_pass;
+        if (npass < A.v) {  // block-uniform: nothing can reach v votes
+            __syncthreads();
+            return;
+        }
+        // 2. exact counts of the entries that pass, in a hash of >= 2 npass slots
         uint32_t slots = 64, lg = 6;
-        while (slots < 2 * n) slots <<= 1, lg++;
+        while (slots < 2 * npass) slots <<= 1, lg++;
         for (uint32_t x = threadIdx.x; x < slots; x += blockDim.x) K[x] = 0;
         for (uint32_t x = threadIdx.x; x < slots / 4; x += blockDim.x) C[x] = 0;
         __syncthreads();
-        for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) {
-            const PT want = ent[e0 + x] + 1;
+        VOTE_FOR_ENTRIES(raw, {
+            const uint32_t f = fhash(raw, flg);
+            if ((F[f >> 1] >> (16 * (f & 1)) & 0xFFFF) < A.v) continue;
+            const PT want = raw + 1;
             uint32_t h = ghash(want, lg);
             for (uint32_t probe = 0; probe < slots; probe++) {
                 PT kk = K[h];
@@ -952,7 +1001,7 @@ __global__ void __launch_bounds__(256) k_group_vote(VoteArgs A, const PT *__rest
                 }
                 h = (h + 1) & (slots - 1);
             }
-        }
+        })
         __syncthreads();
         // kept entries compacted to the front of each warp's slot segment (a
         // kept slot's new position never exceeds its old one, and every lane
@@ -983,7 +1032,7 @@ __global__ void __launch_bounds__(256) k_group_vote(VoteArgs A, const PT *__rest
         for (uint32_t w = 0; w < nw; w++) nk += wsum[w];
         if (!nk) {  // block-uniform
             __syncthreads();
-            continue;
+            return;
         }
         if (threadIdx.x == 0) s_b0 = atomicAdd(A.sp_cursor, (unsigned long long)nk);
         __syncthreads();
@@ -1013,6 +1062,45 @@ __global__ void __launch_bounds__(256) k_group_vote(VoteArgs A, const PT *__rest
             }
         }
         __syncthreads();
+}
+#undef VOTE_FOR_ENTRIES
+
+template <typename PT>
+__global__ void __launch_bounds__(256) k_group_vote(VoteArgs A, const PT *__restrict__ ent) {
+    extern __shared__ unsigned long long vsm_raw[];
+    PT *K = reinterpret_cast<PT *>(vsm_raw);                             // [<= 2 vcap] keys (entry + 1)
+    uint32_t *C = reinterpret_cast<uint32_t *>(K + 2 * A.vcap);          // [<= 2 vcap / 4] byte counts
+    uint32_t *F = C + 2 * A.vcap / 4;                                    // [kVFilter / 2] 16-bit counters
+    __shared__ uint32_t s_pass;
+    __shared__ uint32_t wsum[32];
+    __shared__ unsigned long long s_b0;
+    const PT jmask = ((PT)1 << A.nbits) - 1;
+    // A group's entries stay in registers (kVRegs per thread) when they fit,
+    // and the next group's are loaded while this one is counted.
+    PT cur[kVRegs], nxt[kVRegs];
+    uint64_t e0 = 0, n = 0, e0n = 0, nn = 0;
+    auto fetch = [&](uint64_t gg, PT (&buf)[kVRegs], uint64_t &s0, uint64_t &cnt) {
+        s0 = 0;
+        cnt = 0;
+        if (gg < A.ngroups) {
+            s0 = A.goff[gg];
+            cnt = A.goff[gg + 1] - s0;
+        }
+        const bool regs = cnt >= A.v && cnt <= A.vcap && cnt <= (uint64_t)kVRegs * blockDim.x;
+#pragma unroll
+        for (int u = 0; u < kVRegs; u++) {
+            const uint64_t x = threadIdx.x + (uint64_t)u * blockDim.x;
+            buf[u] = regs && x < cnt ? __ldcs(ent + s0 + x) : (PT)0;
+        }
+    };
+    fetch(blockIdx.x, cur, e0, n);
+    for (uint64_t g = blockIdx.x; g < A.ngroups; g += gridDim.x) {
+        fetch(g + gridDim.x, nxt, e0n, nn);
+        vote_one(A, ent, g, e0, n, cur, K, C, F, s_pass, wsum, s_b0, jmask);
+#pragma unroll
+        for (int u = 0; u < kVRegs; u++) cur[u] = nxt[u];
+        e0 = e0n;
+        n = nn;
     }
 }
 
