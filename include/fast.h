@@ -263,7 +263,7 @@ fast_status fast_get_stats(const fast_ctx *ctx, fast_stats *out);
  *                comparison inside groups instead of the vote map (0 = auto)
  *   "map_load"   target load factor of the vote map, in (0.05, 0.95)
  *   "group_pairs" expected sparse pairs per row group of the row-partitioned
- *                vote, 0 (= 1536) or in [64, 8192]
+ *                vote, 0 (= 1024) or in [64, 8192]
  *   "timing"     1 = record per-stage CUDA events (default), 0 = off
  *   "vote_map"   1 = sum sparse votes in one global open-addressing map of
  *                packed (i, j) -> votes and order the list by a radix sort;

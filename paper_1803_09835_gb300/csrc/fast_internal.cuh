@@ -159,7 +159,7 @@ struct fast_ctx {
     bool capturing = false;     // no host synchronisation while a graph is being captured
     // tuning
     uint32_t large_min = 0;     // live bucket size from which a bucket goes to the dense path (0 = auto)
-    uint32_t group_pairs = 0;   // expected sparse pairs per row group of the vote (0 = 1536)
+    uint32_t group_pairs = 0;   // expected sparse pairs per row group of the vote (0 = 1024)
     float map_load = 0.5f;      // vote-map load factor target
     bool vote_map = false;      // sum sparse votes in one global hash map instead of per row
     // instrumentation
@@ -270,7 +270,7 @@ fast_status history_groups(fast_ctx *c, const fast_tables *tb, const uint32_t *d
 uint32_t large_min_for(const fast_ctx *c, uint64_t N);  // the dense-group threshold (option or automatic)
 struct Scal {  // device scalar slots (ctx->d_scal)
     enum { NBIG, NLARGE, NMEDIUM, NHEAVY, NDROP, NMEMB, CUR_DENSE, CUR_SPARSE, CHANGED, NLONG, NMERGE, NMERGE_TOT,
-           NCAND, NMID, SMALLPAIRS, NSMALLEMIT, PART0 };
+           NCAND, NMID, SMALLPAIRS, NSMALLEMIT, NSLOW, PART0 };
 };
 void history_groups_free(HistGroups *g);
 

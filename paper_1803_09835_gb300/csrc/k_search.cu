@@ -891,11 +891,11 @@ __device__ __forceinline__ bool vadd(uint32_t *K, uint32_t *C, uint32_t slots, u
 
 // A row group's pairs are counted in one shared-memory hash of >= 2n slots
 // when n <= vcap (larger groups: one CTA per row).  The expected pairs per
-// group (`group_pairs`, default 1536) sets the group size 2^gshift rows, and
+// group (`group_pairs`, default 1024) sets the group size 2^gshift rows, and
 // vcap is twice the power of two above it: larger groups mean fewer
 // concurrent write frontiers in the emission pass, smaller ones more resident
 // CTAs in the vote.
-constexpr uint32_t kVTargetDefault = 1536;
+constexpr uint32_t kVTargetDefault = 1024;
 // Counting filter in front of the hash: 16-bit counters (never wrap: a group
 // holds at most vcap <= 16384 entries) indexed by a second hash of the entry.
 // An entry whose counter is below v cannot have v copies, so only the few
@@ -931,18 +931,21 @@ __device__ __forceinline__ uint32_t fhash(unsigned long long key, uint32_t lg) {
         _Pragma("unroll") for (int u_ = 0; u_ < kVRegs; u_++) {                      \
             if (threadIdx.x + (uint64_t)u_ * blockDim.x >= n) continue;              \
             const PT raw = cur[u_];                                                   \
+            if ((uint32_t)(raw >> A.nbits) - r0 >= r1 - r0) continue;                 \
             BODY                                                                      \
         }                                                                             \
     } else {                                                                          \
         for (uint64_t x_ = threadIdx.x; x_ < n; x_ += blockDim.x) {                   \
             const PT raw = ent[e0 + x_];                                              \
+            if ((uint32_t)(raw >> A.nbits) - r0 >= r1 - r0) continue;                 \
             BODY                                                                      \
         }                                                                             \
     }
 
 template <typename PT>
 __device__ __forceinline__ void vote_one(const VoteArgs &A, const PT *__restrict__ ent, uint64_t g, uint64_t e0,
-                                         uint64_t n, const PT (&cur)[kVRegs], PT *K, uint32_t *C, uint32_t *F,
+                                         uint64_t n, uint32_t r0, uint32_t r1, const PT (&cur)[kVRegs], PT *K,
+                                         uint32_t *C, uint32_t *F,
                                          uint32_t &s_pass, uint32_t *wsum, unsigned long long &s_b0, PT jmask) {
     const bool regs = n <= (uint64_t)kVRegs * blockDim.x;
         if (n < A.v) return;  // block-uniform
@@ -1066,7 +1069,9 @@ __device__ __forceinline__ void vote_one(const VoteArgs &A, const PT *__restrict
 #undef VOTE_FOR_ENTRIES
 
 template <typename PT>
-__global__ void __launch_bounds__(256) k_group_vote(VoteArgs A, const PT *__restrict__ ent) {
+__global__ void __launch_bounds__(256) k_group_vote(VoteArgs A, const PT *__restrict__ ent,
+                                                    const uint2 *__restrict__ list,
+                                                    const unsigned long long *__restrict__ nlist) {
     extern __shared__ unsigned long long vsm_raw[];
     PT *K = reinterpret_cast<PT *>(vsm_raw);                             // [<= 2 vcap] keys (entry + 1)
     uint32_t *C = reinterpret_cast<uint32_t *>(K + 2 * A.vcap);          // [<= 2 vcap / 4] byte counts
@@ -1093,14 +1098,202 @@ __global__ void __launch_bounds__(256) k_group_vote(VoteArgs A, const PT *__rest
             buf[u] = regs && x < cnt ? __ldcs(ent + s0 + x) : (PT)0;
         }
     };
-    fetch(blockIdx.x, cur, e0, n);
-    for (uint64_t g = blockIdx.x; g < A.ngroups; g += gridDim.x) {
-        fetch(g + gridDim.x, nxt, e0n, nn);
-        vote_one(A, ent, g, e0, n, cur, K, C, F, s_pass, wsum, s_b0, jmask);
+    const uint64_t count = list ? *nlist : A.ngroups;
+    auto gid = [&](uint64_t k) { return list ? (uint64_t)list[k].x : k; };
+    // rows [r0, r1) of the group (all of them without a list)
+    auto rng = [&](uint64_t k) { return list ? list[k].y : (1u << A.gshift); };
+    fetch(blockIdx.x < count ? gid(blockIdx.x) : A.ngroups, cur, e0, n);
+    for (uint64_t k = blockIdx.x; k < count; k += gridDim.x) {
+        fetch(k + gridDim.x < count ? gid(k + gridDim.x) : A.ngroups, nxt, e0n, nn);
+        const uint32_t rr = rng(k);
+        vote_one(A, ent, gid(k), e0, n, rr >> 16, rr & 0xFFFF, cur, K, C, F, s_pass, wsum, s_b0, jmask);
 #pragma unroll
         for (int u = 0; u < kVRegs; u++) cur[u] = nxt[u];
         e0 = e0n;
         n = nn;
+    }
+}
+
+// Warp-per-group vote for the common case, no block barriers: each warp has
+// its own counting filter (kWF 16-bit counters) and a small exact hash (kWS
+// slots) in shared memory.  Groups too large for them (more than kWF / 2
+// entries, or more than kWS / 2 entries passing the filter) are appended to
+// `slow` for the block kernel; groups beyond vcap are split into long rows as
+// the block kernel does.
+constexpr uint32_t kWF = 4096, kWS = 256, kVW = 6;  // kVW warps per CTA: four CTAs per SM fit
+
+template <typename PT>
+constexpr size_t warp_vote_smem() {
+    return (size_t)kVW * (kWF * 2 + kWS * sizeof(PT) + kWS);
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(kVW * 32) k_warp_vote(VoteArgs A, const PT *__restrict__ ent, uint2 *__restrict__ slow,
+                                                   unsigned long long *__restrict__ nslow) {
+    extern __shared__ unsigned long long wv_raw[];
+    const uint32_t warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+    char *base = reinterpret_cast<char *>(wv_raw) + (size_t)warp * (kWF * 2 + kWS * sizeof(PT) + kWS);
+    PT *K = reinterpret_cast<PT *>(base);                                // [kWS] keys (entry + 1)
+    uint32_t *F = reinterpret_cast<uint32_t *>(base + kWS * sizeof(PT)); // [kWF / 2] 16-bit counters
+    uint8_t *V = reinterpret_cast<uint8_t *>(F + kWF / 2);               // [kWS] counts
+    const PT jmask = ((PT)1 << A.nbits) - 1;
+    const uint32_t lt = (1u << lane) - 1;
+    for (uint64_t g = (uint64_t)blockIdx.x * kVW + warp; g < A.ngroups; g += (uint64_t)gridDim.x * kVW) {
+        const uint64_t e0 = A.goff[g], n = A.goff[g + 1] - e0;
+        if (n < A.v) continue;  // warp-uniform
+        const uint64_t row0 = g << A.gshift;
+        if (n > A.vcap) {  // every row of the group is voted one CTA each
+            for (uint32_t r = lane; r < (1u << A.gshift); r += 32) {
+                if (row0 + r >= A.N) break;
+                const unsigned long long q = atomicAdd(A.n_long, 1ull);
+                if (q < A.long_cap) A.long_rows[q] = make_uint2((uint32_t)(row0 + r), (uint32_t)n);
+            }
+            continue;
+        }
+        // a group larger than the filter is voted in parts: row ranges of about
+        // kWF / 4 entries each (one part when it fits)
+        const uint32_t rows = 1u << A.gshift;
+        const uint32_t P = n <= kWF / 2 ? 1u : min(min(rows, 8u), (uint32_t)((n + kWF / 4 - 1) / (kWF / 4)));
+        uint32_t pc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (P > 1) {
+            for (uint32_t x0 = lane; x0 < n; x0 += 8 * 32) {
+                PT b8[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) b8[u] = x0 + 32 * u < n ? ent[e0 + x0 + 32 * u] : (PT)0;
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const uint32_t part = x0 + 32 * u < n ? (uint32_t)(b8[u] >> A.nbits) * P / rows : 8u;
+#pragma unroll
+                    for (int q = 0; q < 8; q++) pc[q] += part == (uint32_t)q;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+#pragma unroll
+                for (int o = 16; o; o >>= 1) pc[q] += __shfl_xor_sync(~0u, pc[q], o);
+        } else {
+            pc[0] = (uint32_t)n;
+        }
+        bool fits = true;
+#pragma unroll
+        for (int q = 0; q < 8; q++) fits &= pc[q] <= kWF / 2;
+        if (!fits) {  // uneven rows: the whole group to the block kernel
+            if (lane == 0) slow[atomicAdd(nslow, 1ull)] = make_uint2((uint32_t)g, rows);
+            continue;
+        }
+        for (uint32_t p = 0; p < P; p++) {
+        // part of row r is r * P / rows, so part p holds rows [ceil(p rows / P), ceil((p + 1) rows / P))
+        const uint32_t r0 = (p * rows + P - 1) / P, r1 = ((p + 1) * rows + P - 1) / P, np = pc[min(p, 7u)];
+        if (np < A.v) continue;
+        // 1. counting filter
+        uint32_t fc = 64, flg = 6;
+        while (fc < 2 * np) fc <<= 1, flg++;
+        for (uint32_t x = lane; x < fc / 2; x += 32) F[x] = 0;
+        __syncwarp();
+        // entries in batches of 8 per lane, all loads of a batch issued before its atomics
+        for (uint32_t x0 = lane; x0 < n; x0 += 8 * 32) {
+            PT b8[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) b8[u] = x0 + 32 * u < n ? __ldcs(ent + e0 + x0 + 32 * u) : (PT)0;
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (x0 + 32 * u < n && (uint32_t)(b8[u] >> A.nbits) - r0 < r1 - r0) {
+                    const uint32_t f = fhash(b8[u], flg);
+                    atomicAdd(F + (f >> 1), 1u << (16 * (f & 1)));
+                }
+        }
+        __syncwarp();
+        uint32_t npass = 0;
+        for (uint32_t x0 = lane; x0 < n; x0 += 8 * 32) {
+            PT b8[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) b8[u] = x0 + 32 * u < n ? ent[e0 + x0 + 32 * u] : (PT)0;
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (x0 + 32 * u < n && (uint32_t)(b8[u] >> A.nbits) - r0 < r1 - r0) {
+                    const uint32_t f = fhash(b8[u], flg);
+                    npass += (F[f >> 1] >> (16 * (f & 1)) & 0xFFFF) >= A.v;
+                }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) npass += __shfl_xor_sync(~0u, npass, o);
+        if (npass < A.v) continue;  // nothing can reach v votes
+        if (npass > kWS / 2) {  // this part's rows to the block kernel
+            if (lane == 0) slow[atomicAdd(nslow, 1ull)] = make_uint2((uint32_t)g, r0 << 16 | r1);
+            continue;
+        }
+        // 2. exact counts of the passing entries
+        uint32_t slots = 32, lg = 5;
+        while (slots < 2 * npass) slots <<= 1, lg++;
+        for (uint32_t x = lane; x < slots; x += 32) {
+            K[x] = 0;
+            V[x] = 0;
+        }
+        __syncwarp();
+        for (uint32_t x0 = lane; x0 < n; x0 += 8 * 32) {
+            PT b8[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) b8[u] = x0 + 32 * u < n ? ent[e0 + x0 + 32 * u] : (PT)0;
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                if (x0 + 32 * u >= n || (uint32_t)(b8[u] >> A.nbits) - r0 >= r1 - r0) continue;
+                const uint32_t f = fhash(b8[u], flg);
+                if ((F[f >> 1] >> (16 * (f & 1)) & 0xFFFF) < A.v) continue;
+                const PT want = b8[u] + 1;
+                uint32_t h = ghash(want, lg);
+                for (uint32_t probe = 0; probe < slots; probe++) {
+                    PT kk = K[h];
+                    if (kk == 0) {
+                        kk = atomicCAS(K + h, (PT)0, want);
+                        if (kk == 0) kk = want;
+                    }
+                    if (kk == want) {
+                        atomicAdd(reinterpret_cast<uint32_t *>(V) + (h >> 2), 1u << (8 * (h & 3)));
+                        break;
+                    }
+                    h = (h + 1) & (slots - 1);
+                }
+            }
+        }
+        __syncwarp();
+        // 3. kept entries compacted to the front (positions never pass the read point)
+        uint32_t nk = 0;
+        for (uint32_t b = 0; b < slots; b += 32) {
+            const uint32_t x = b + lane;
+            const PT kk = K[x];
+            const uint32_t cc = V[x];
+            const bool keep = kk != 0 && cc >= A.v;
+            const uint32_t m = __ballot_sync(~0u, keep);
+            if (keep) {
+                const uint32_t pos = nk + __popc(m & lt);
+                K[pos] = kk - 1;
+                V[pos] = (uint8_t)cc;
+            }
+            nk += __popc(m);
+        }
+        __syncwarp();
+        if (!nk) continue;
+        unsigned long long b0 = 0;
+        if (lane == 0) b0 = atomicAdd(A.sp_cursor, (unsigned long long)nk);
+        b0 = __shfl_sync(~0u, b0, 0);
+        for (uint32_t q = lane; q < nk; q += 32) {
+            const PT kx = K[q];
+            uint32_t rank = 0, first = 1;
+            for (uint32_t y = 0; y < nk; y++) {
+                const PT ky = K[y];
+                rank += ky < kx;
+                first &= (uint32_t)((ky >> A.nbits) != (kx >> A.nbits) || ky >= kx);
+            }
+            const uint64_t i = row0 + (uint32_t)(kx >> A.nbits);
+            if (b0 + nk <= A.sp_cap) {
+                A.sp_j[b0 + rank] = (uint32_t)(kx & jmask);
+                A.sp_v[b0 + rank] = V[q];
+            }
+            atomicAdd(A.sp_cnt + i, 1u);
+            if (first) A.sp_start[i] = b0 + rank;
+        }
+        __syncwarp();
+        }  // parts
     }
 }
 
@@ -1765,14 +1958,20 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
                                                ent), FAST_LAUNCHED(c);
 
     stage_mark(c, 11, s);
-    // hash capacity: twice the power of two above the target (group sizes vary)
+    // hash capacity: twice the power of two above the target (group sizes vary), at least 4096
     uint32_t vcap = 64;
     while (vcap < (c->group_pairs ? c->group_pairs : kVTargetDefault)) vcap <<= 1;
-    vcap = std::min<uint32_t>(2 * vcap, sizeof(PT) == 4 ? 1u << 14 : 1u << 13);
+    vcap = std::min<uint32_t>(std::max<uint32_t>(2 * vcap, 4096), sizeof(PT) == 4 ? 1u << 14 : 1u << 13);
     const size_t vsm = group_vote_smem<PT>(vcap);
     cudaFuncSetAttribute(k_group_vote<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
     int vper = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&vper, k_group_vote<PT>, 256, vsm);
+    const size_t wsm = warp_vote_smem<PT>();
+    cudaFuncSetAttribute(k_warp_vote<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);
+    int wper = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper, k_warp_vote<PT>, kVW * 32, wsm);
+    uint2 *slow = nullptr;  // (group, rows r0 << 16 | r1) left to the block kernel
+    if ((st = alloc(&slow, 8 * ng))) return st;
     uint64_t sp_cap = std::max<uint64_t>(N, 1 << 20);
     VoteArgs va{goff, ng, N, gshift, nbits, p.v, vcap, sp_cnt, sp_start, nullptr, nullptr, 0, scal + Scal::CUR_SPARSE,
                 long_rows, scal + Scal::NLONG, N};
@@ -1788,11 +1987,14 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
         cudaMemsetAsync(sp_cnt, 0, N * 4, s);
         cudaMemsetAsync(scal + Scal::CUR_SPARSE, 0, 8, s);
         cudaMemsetAsync(scal + Scal::NLONG, 0, 8, s);
+        cudaMemsetAsync(scal + Scal::NSLOW, 0, 8, s);
         stage_mark(c, 13, s);
-        k_group_vote<PT><<<(unsigned)std::max<uint64_t>(
-                               1, std::min<uint64_t>(ng, (uint64_t)c->num_sms * std::max(vper, 1))),
-                           256, vsm, s>>>(va, ent), FAST_LAUNCHED(c);
+        k_warp_vote<PT><<<(unsigned)std::max<uint64_t>(
+                              1, std::min<uint64_t>((ng + kVW - 1) / kVW, (uint64_t)c->num_sms * std::max(wper, 1))),
+                          kVW * 32, wsm, s>>>(va, ent, slow, scal + Scal::NSLOW), FAST_LAUNCHED(c);
         stage_mark(c, 14, s);
+        k_group_vote<PT><<<(unsigned)std::max<uint64_t>(1, (uint64_t)c->num_sms * std::max(vper, 1)), 256, vsm,
+                           s>>>(va, ent, slow, scal + Scal::NSLOW), FAST_LAUNCHED(c);
         if ((st = read_scal(c, s, "row votes"))) return st;
         const uint64_t nlong = c->h_scal[Scal::NLONG];
         if (nlong > N) return set_error(c, FAST_EINTERNAL, "long-row list overflow");
