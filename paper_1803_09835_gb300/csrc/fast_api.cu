@@ -125,6 +125,15 @@ void stats_times(fast_ctx *c, bool whole) {
     s.ms_k_vote = stage_ms(c, 13, 14);
 }
 
+// Tables and search over keys already in d_sig ([b][N]); the rest of fast_detect.
+static fast_status detect_from_sig(fast_ctx *c, const uint32_t *sig, uint64_t N, fast_result **out, cudaStream_t s) {
+    fast_tables *tb = nullptr;
+    fast_status st = build_tables(c, sig, N, nullptr, 1, &tb, s);  // synchronises: reports bad indices too
+    if (!st) st = search_run(c, tb, sig, out, s);
+    fast_tables_free(tb);
+    return st;
+}
+
 extern "C" {
 
 fast_status fast_create(const fast_params *p, uint64_t hbm_budget_bytes, fast_ctx **out) {
@@ -184,6 +193,9 @@ void fast_destroy(fast_ctx *c) {
     if (c->h_scal) cudaFreeHost(c->h_scal);
     for (auto &ev : c->ev)
         if (ev) cudaEventDestroy(ev);
+    for (auto &ev : c->cev)
+        if (ev) cudaEventDestroy(ev);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     cudaGetLastError();
     delete c;
@@ -322,10 +334,7 @@ fast_status fast_detect(fast_ctx *c, const uint16_t *d_idx, uint64_t N, uint32_t
     if (st) return st;
     st = sig_launch(c, d_idx, N, ld, sig, s);
     stage_mark(c, 1, s);
-    fast_tables *tb = nullptr;
-    if (!st) st = build_tables(c, sig, N, nullptr, 1, &tb, s);  // synchronises: reports bad indices too
-    if (!st) st = search_run(c, tb, sig, out, s);
-    fast_tables_free(tb);
+    if (!st) st = detect_from_sig(c, sig, N, out, s);
     dfree(c, sig, n * 4, s);
     if (!st) stats_times(c, true);
     c->stats.n_fingerprints = N;
@@ -448,16 +457,47 @@ fast_status fast_detect_host(fast_ctx *c, const uint16_t *h_idx, uint64_t N, uin
                              uint32_t *h_i, uint32_t *h_j, uint8_t *h_votes, uint64_t cap, void *stream) {
     if (!c || !M || (N && !h_idx) || (cap && (!h_i || !h_j || !h_votes))) return FAST_EINVAL;
     c->err.clear();
+    if (ld < c->p.K) return set_error(c, FAST_EINVAL, "fast_detect_host: ld < K");
+    if (N > (1ull << 28) - 1) return set_error(c, FAST_EINVAL, "N must be < 2^28");
     cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (!c->copy_stream) {
+        if ((e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking))) return cuda_fail(c, e, "copy stream");
+        for (auto &ev : c->cev)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming))) return cuda_fail(c, e, "copy events");
+    }
+    g_marked = 0;
+    c->stats.n_launches = 0;
+    stage_mark(c, 0, s);
     uint16_t *d_idx = nullptr;
-    const size_t bytes = (size_t)N * ld * 2;
+    uint32_t *sig = nullptr;
+    const size_t bytes = (size_t)N * ld * 2, nsig = (size_t)c->p.b * N;
     fast_status st = dalloc(c, (void **)&d_idx, bytes, s);
     if (st) return st;
-    if (N) cudaMemcpyAsync(d_idx, h_idx, bytes, cudaMemcpyHostToDevice, s);
+    if ((st = dalloc_t(c, &sig, nsig ? nsig : 1, s))) {
+        dfree(c, d_idx, bytes, s);
+        return st;
+    }
+    // chunks of whole 32-row tiles: chunk k is copied on the copy stream while
+    // the signature kernel works on chunk k - 1
+    const uint64_t per = std::max<uint64_t>(32, ((N + kCopyChunks - 1) / kCopyChunks + 31) / 32 * 32);
+    cudaEventRecord(c->cev[kCopyChunks], s);  // the buffers' allocations, ordered on s
+    cudaStreamWaitEvent(c->copy_stream, c->cev[kCopyChunks], 0);
+    for (uint64_t r0 = 0, k = 0; r0 < N && !st; r0 += per, k++) {
+        const uint64_t rows = std::min<uint64_t>(per, N - r0);
+        cudaMemcpyAsync(d_idx + r0 * ld, h_idx + r0 * ld, rows * ld * 2, cudaMemcpyHostToDevice, c->copy_stream);
+        cudaEventRecord(c->cev[k], c->copy_stream);
+        cudaStreamWaitEvent(s, c->cev[k], 0);
+        st = sig_launch_rows(c, d_idx + r0 * ld, rows, ld, sig + r0, N, s);
+    }
+    stage_mark(c, 1, s);
     fast_result *res = nullptr;
-    st = fast_detect(c, d_idx, N, ld, &res, stream);
+    if (!st) st = detect_from_sig(c, sig, N, &res, s);
+    dfree(c, sig, nsig * 4, s);
     dfree(c, d_idx, bytes, s);
     if (st) return st;
+    stats_times(c, true);
+    c->stats.n_fingerprints = N;
     *M = res->M;
     const uint64_t m = std::min<uint64_t>(cap, res->M);
     if (m) {

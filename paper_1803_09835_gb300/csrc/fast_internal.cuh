@@ -129,6 +129,8 @@ struct DevBuf {
 
 }  // namespace fastgb
 
+constexpr int kCopyChunks = 8;
+
 struct fast_ctx {
     fast_params p{};
     int device = 0;
@@ -165,6 +167,9 @@ struct fast_ctx {
     // instrumentation
     fast_stats stats{};
     cudaEvent_t ev[16] = {};
+    // host entry: input copied in chunks on a second stream while the signature kernel runs
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t cev[kCopyChunks + 1] = {};
     bool timing = true;
     std::string err;
 };
@@ -221,6 +226,10 @@ inline unsigned ceil_div(uint64_t a, uint64_t b) { return (unsigned)((a + b - 1)
 fast_status sig_setup(fast_ctx *c);
 fast_status sig_launch(fast_ctx *c, const uint16_t *d_idx, uint64_t N, uint32_t ld, uint32_t *d_sig,
                        cudaStream_t s);
+// N rows of d_idx whose keys go to columns [0, N) of a [b][Nst] key array
+// (d_sig already offset to the first column): one chunk of a larger batch.
+fast_status sig_launch_rows(fast_ctx *c, const uint16_t *d_idx, uint64_t N, uint32_t ld, uint32_t *d_sig, uint64_t Nst,
+                            cudaStream_t s);
 
 // k_sort.cu: stable LSD radix sort of `nseg` equal segments of length `len`.
 // Keys in/out, optional 32-bit values (vals_in == nullptr -> values are the

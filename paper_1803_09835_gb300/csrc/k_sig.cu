@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kSigThreads, 3)
     k_sig_walk(const uint16_t *__restrict__ idx, uint64_t N, uint32_t ld, uint32_t D, uint32_t K,
                const uint16_t *__restrict__ walk, uint32_t Dpad, uint32_t W, const uint64_t *__restrict__ ha,
                const uint64_t *__restrict__ hb, const uint64_t *__restrict__ zinit, uint32_t nb, uint32_t r,
-               uint32_t *__restrict__ sig, uint32_t *err, int vec16) {
+               uint32_t *__restrict__ sig, uint64_t Nst, uint32_t *err, int vec16) {
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t next_walk;
     uint32_t *M = smem;
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kSigThreads, 3)
                     const uint32_t h = hash_ab((uint32_t)a, (uint32_t)(a >> 32), __ldg(hb + f), x);
                     z = mix64(z ^ (uint64_t)h);
                 }
-                sig[(uint64_t)t * N + base + q] = (uint32_t)(z >> 32);
+                sig[(uint64_t)t * Nst + base + q] = (uint32_t)(z >> 32);
             }
         }
         __syncthreads();
@@ -196,7 +196,7 @@ template <bool MINMAX>
 __global__ void k_sig_direct(const uint16_t *__restrict__ idx, uint64_t N, uint32_t ld, uint32_t D, uint32_t K,
                              const uint64_t *__restrict__ ha, const uint64_t *__restrict__ hb,
                              const uint64_t *__restrict__ zinit, uint32_t nb, uint32_t r, uint32_t *__restrict__ sig,
-                             uint32_t *err) {
+                             uint64_t Nst, uint32_t *err) {
     for (uint64_t i = blockIdx.x; i < N; i += gridDim.x) {
         const uint16_t *row = idx + i * (uint64_t)ld;
         for (uint32_t t = threadIdx.x; t < nb; t += blockDim.x) {
@@ -224,7 +224,7 @@ __global__ void k_sig_direct(const uint16_t *__restrict__ idx, uint64_t N, uint3
                     ++c;
                 }
             }
-            sig[(uint64_t)t * N + i] = (uint32_t)(z >> 32);
+            sig[(uint64_t)t * Nst + i] = (uint32_t)(z >> 32);
         }
     }
 }
@@ -275,8 +275,8 @@ fast_status sig_setup(fast_ctx *c) {
     return FAST_OK;
 }
 
-fast_status sig_launch(fast_ctx *c, const uint16_t *d_idx, uint64_t N, uint32_t ld, uint32_t *d_sig,
-                       cudaStream_t s) {
+fast_status sig_launch_rows(fast_ctx *c, const uint16_t *d_idx, uint64_t N, uint32_t ld, uint32_t *d_sig, uint64_t Nst,
+                            cudaStream_t s) {
     if (N == 0) return FAST_OK;
     const fast_params &p = c->p;
     const bool mm = p.kind == FAST_MINMAX;
@@ -293,23 +293,28 @@ fast_status sig_launch(fast_ctx *c, const uint16_t *d_idx, uint64_t N, uint32_t 
         if (mm)
             k_sig_walk<true><<<(unsigned)grid, kSigThreads, sms, s>>>(d_idx, N, ld, p.D, p.K, c->d_walk, c->Dpad,
                                                                       c->W, c->d_a, c->d_b, c->d_zinit, p.b, p.r,
-                                                                      d_sig, c->d_err, vec16), FAST_LAUNCHED(c);
+                                                                      d_sig, Nst, c->d_err, vec16), FAST_LAUNCHED(c);
         else
             k_sig_walk<false><<<(unsigned)grid, kSigThreads, sms, s>>>(d_idx, N, ld, p.D, p.K, c->d_walk, c->Dpad,
                                                                        c->W, c->d_a, c->d_b, c->d_zinit, p.b, p.r,
-                                                                       d_sig, c->d_err, vec16), FAST_LAUNCHED(c);
+                                                                       d_sig, Nst, c->d_err, vec16), FAST_LAUNCHED(c);
     } else {
         unsigned grid = (unsigned)std::min<uint64_t>(N, (uint64_t)c->num_sms * 16);
         unsigned thr = std::min<uint32_t>(256, (p.b + 31) & ~31u);
         if (mm)
             k_sig_direct<true><<<grid, thr, 0, s>>>(d_idx, N, ld, p.D, p.K, c->d_a, c->d_b, c->d_zinit, p.b, p.r,
-                                                    d_sig, c->d_err), FAST_LAUNCHED(c);
+                                                    d_sig, Nst, c->d_err), FAST_LAUNCHED(c);
         else
             k_sig_direct<false><<<grid, thr, 0, s>>>(d_idx, N, ld, p.D, p.K, c->d_a, c->d_b, c->d_zinit, p.b, p.r,
-                                                     d_sig, c->d_err), FAST_LAUNCHED(c);
+                                                     d_sig, Nst, c->d_err), FAST_LAUNCHED(c);
     }
     cudaError_t e = cudaGetLastError();
     return e ? cuda_fail(c, e, "sig kernel") : FAST_OK;
+}
+
+fast_status sig_launch(fast_ctx *c, const uint16_t *d_idx, uint64_t N, uint32_t ld, uint32_t *d_sig,
+                       cudaStream_t s) {
+    return sig_launch_rows(c, d_idx, N, ld, d_sig, N, s);
 }
 
 }  // namespace fastgb
