@@ -120,6 +120,7 @@ typedef struct {
     /* single kernels inside those: the small-bucket pair writer, the group vote */
     float ms_k_pairs, ms_k_vote;
     uint64_t n_pairs_small;   /* of n_emissions: pairs of buckets with at most 32 entries */
+    uint64_t peak_bytes;      /* most device memory held at once during the call    */
 } fast_stats;
 
 /*

@@ -327,6 +327,7 @@ fast_status fast_detect(fast_ctx *c, const uint16_t *d_idx, uint64_t N, uint32_t
     cudaStream_t s = (cudaStream_t)stream;
     g_marked = 0;
     c->stats.n_launches = 0;
+    c->peak = c->live;
     stage_mark(c, 0, s);
     uint32_t *sig = nullptr;
     const size_t n = (size_t)c->p.b * N;
@@ -338,6 +339,7 @@ fast_status fast_detect(fast_ctx *c, const uint16_t *d_idx, uint64_t N, uint32_t
     dfree(c, sig, n * 4, s);
     if (!st) stats_times(c, true);
     c->stats.n_fingerprints = N;
+    c->stats.peak_bytes = c->peak;
     return st;
 }
 
@@ -433,6 +435,7 @@ fast_status fast_detect_batch(fast_ctx *c, const uint16_t *d_idx, const uint64_t
     cudaStream_t s = (cudaStream_t)stream;
     g_marked = 0;
     c->stats.n_launches = 0;
+    c->peak = c->live;
     stage_mark(c, 0, s);
     uint32_t *sig = nullptr;
     const size_t n = (size_t)c->p.b * N;

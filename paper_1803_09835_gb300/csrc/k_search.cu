@@ -654,6 +654,13 @@ __global__ void __launch_bounds__(256) k_flag_ids(const uint32_t *__restrict__ s
     if (tid < n - n4 * 4) fsid[n4 * 4 + tid] = flag_id(sid[n4 * 4 + tid], bits);
 }
 
+// Row groups [g_lo, g_hi) written by one emission pass; their entries start at
+// goff[g] - ebase in that pass's buffer (all groups, ebase 0, when unsplit).
+struct GroupRange {
+    uint64_t g_lo, g_hi, ebase;
+    __device__ __forceinline__ bool has(uint64_t g) const { return g >= g_lo && g < g_hi; }
+};
+
 struct PairSmem {  // one warp's tile window and its pair bookkeeping
     uint32_t id[64], lab[64], pre[32], cnt[32];
     uint64_t base[32];
@@ -663,7 +670,7 @@ template <int MODE, typename PT>
 __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, uint32_t nbits, uint32_t tiles_per_warp,
                                                    uint32_t *__restrict__ gcnt, const uint64_t *__restrict__ goff,
                                                    uint32_t *__restrict__ gcur, PT *__restrict__ ent,
-                                                   unsigned long long *__restrict__ n_emit) {
+                                                   unsigned long long *__restrict__ n_emit, GroupRange gr) {
     const uint32_t t = blockIdx.y, lane = threadIdx.x & 31;
     const uint64_t N = a.N, ntiles = (N + 31) / 32;
     const uint32_t *K = a.skey + (uint64_t)t * N;
@@ -714,7 +721,8 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
                     if (W.pre[L + step] <= k) L += step;
                 const uint32_t y = L + 1 + (k - W.pre[L]);
                 const uint32_t i = W.id[L], li = W.lab[L], j = W.id[y], lj = W.lab[y];
-                if (lj != kLabDrop && j - i > a.excl && (li == kNone || li != lj)) atomicAdd(&W.cnt[L], 1u);
+                if (lj != kLabDrop && j - i > a.excl && (li == kNone || li != lj) && (MODE == 0 || gr.has(i >> gshift)))
+                    atomicAdd(&W.cnt[L], 1u);
             }
             __syncwarp();
             const uint32_t cnt = W.cnt[lane], g = c.id >> gshift;
@@ -722,7 +730,7 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
                 emitted += cnt;
                 if (cnt) atomicAdd(gcnt + g, cnt);
             } else if (__any_sync(~0u, cnt != 0)) {
-                W.base[lane] = cnt ? goff[g] + atomicAdd(gcur + g, cnt) : 0;
+                W.base[lane] = cnt ? goff[g] - gr.ebase + atomicAdd(gcur + g, cnt) : 0;
                 W.cnt[lane] = 0;
                 __syncwarp();
                 for (uint32_t k = lane; k < P; k += 32) {
@@ -732,7 +740,7 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
                         if (W.pre[L + step] <= k) L += step;
                     const uint32_t y = L + 1 + (k - W.pre[L]);
                     const uint32_t i = W.id[L], li = W.lab[L], j = W.id[y], lj = W.lab[y];
-                    if (lj != kLabDrop && j - i > a.excl && (li == kNone || li != lj))
+                    if (lj != kLabDrop && j - i > a.excl && (li == kNone || li != lj) && gr.has(i >> gshift))
                         ent[W.base[L] + atomicAdd(&W.cnt[L], 1u)] = pack_entry<PT>(i & lmask, j, nbits);
                 }
             }
@@ -761,7 +769,7 @@ __global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, const uint4 *__r
                                                     const unsigned long long *__restrict__ nmedium, uint32_t gshift,
                                                     uint32_t nbits, uint32_t *__restrict__ gcnt,
                                                     const uint64_t *__restrict__ goff, uint32_t *__restrict__ gcur,
-                                                    PT *__restrict__ ent) {
+                                                    PT *__restrict__ ent, GroupRange gr) {
     __shared__ uint32_t s_id[kMedCap], s_lab[kMedCap];
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t s_next, s_mixed;
@@ -773,7 +781,7 @@ __global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, const uint4 *__r
         if (e.w > kMedCap) {  // block-uniform: fallback over global memory
             for (uint32_t x = e.y + threadIdx.x; x < e.z; x += blockDim.x) {
                 const uint32_t i = s[x];
-                if (a.drop[i]) continue;
+                if (a.drop[i] || (MODE == 1 && !gr.has(i >> gshift))) continue;
                 uint32_t c = 0;
                 for (uint32_t y = x + 1; y < e.z; y++) {
                     const uint32_t j = s[y];
@@ -784,7 +792,7 @@ __global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, const uint4 *__r
                 if (MODE == 0) {
                     atomicAdd(gcnt + g, c);
                 } else {
-                    uint64_t o = goff[g] + atomicAdd(gcur + g, c);
+                    uint64_t o = goff[g] - gr.ebase + atomicAdd(gcur + g, c);
                     for (uint32_t y = x + 1; y < e.z; y++) {
                         const uint32_t j = s[y];
                         if (!a.drop[j] && pair_live(a, i, j)) ent[o++] = pack_entry<PT>(i & lmask, j, nbits);
@@ -826,6 +834,7 @@ __global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, const uint4 *__r
                 x = __shfl_sync(~0u, x, 0);
                 if (x + 1 >= nl) break;  // warp-uniform
                 const uint32_t i = s_id[x], li = s_lab[x], g = i >> gshift;
+                if (MODE == 1 && !gr.has(g)) continue;  // warp-uniform: one row per warp
                 uint32_t c = 0;
                 for (uint32_t y = x + 1 + lane; y < nl; y += 32) {
                     const uint32_t lj = s_lab[y];
@@ -838,7 +847,7 @@ __global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, const uint4 *__r
                     if (lane == 0) atomicAdd(gcnt + g, c);
                 } else {
                     uint64_t o = 0;
-                    if (lane == 0) o = goff[g] + atomicAdd(gcur + g, c);
+                    if (lane == 0) o = goff[g] - gr.ebase + atomicAdd(gcur + g, c);
                     o = __shfl_sync(~0u, o, 0);
                     for (uint32_t y0 = x + 1; y0 < nl; y0 += 32) {
                         const uint32_t y = y0 + lane;
@@ -858,6 +867,7 @@ __global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, const uint4 *__r
 struct VoteArgs {
     const uint64_t *goff;
     uint64_t ngroups, N;
+    uint64_t g_lo, g_hi, ebase;  // the groups of this pass and the buffer offset of group g_lo
     uint32_t gshift, nbits, v, vcap;
     uint32_t *sp_cnt;
     uint64_t *sp_start;
@@ -1088,8 +1098,8 @@ __global__ void __launch_bounds__(256) k_group_vote(VoteArgs A, const PT *__rest
         s0 = 0;
         cnt = 0;
         if (gg < A.ngroups) {
-            s0 = A.goff[gg];
-            cnt = A.goff[gg + 1] - s0;
+            s0 = A.goff[gg] - A.ebase;
+            cnt = A.goff[gg + 1] - A.goff[gg];
         }
         const bool regs = cnt >= A.v && cnt <= A.vcap && cnt <= (uint64_t)kVRegs * blockDim.x;
 #pragma unroll
@@ -1138,8 +1148,8 @@ __global__ void __launch_bounds__(kVW * 32) k_warp_vote(VoteArgs A, const PT *__
     uint8_t *V = reinterpret_cast<uint8_t *>(F + kWF / 2);               // [kWS] counts
     const PT jmask = ((PT)1 << A.nbits) - 1;
     const uint32_t lt = (1u << lane) - 1;
-    for (uint64_t g = (uint64_t)blockIdx.x * kVW + warp; g < A.ngroups; g += (uint64_t)gridDim.x * kVW) {
-        const uint64_t e0 = A.goff[g], n = A.goff[g + 1] - e0;
+    for (uint64_t g = A.g_lo + (uint64_t)blockIdx.x * kVW + warp; g < A.g_hi; g += (uint64_t)gridDim.x * kVW) {
+        const uint64_t e0 = A.goff[g] - A.ebase, n = A.goff[g + 1] - A.goff[g];
         if (n < A.v) continue;  // warp-uniform
         const uint64_t row0 = g << A.gshift;
         if (n > A.vcap) {  // every row of the group is voted one CTA each
@@ -1194,7 +1204,7 @@ __global__ void __launch_bounds__(kVW * 32) k_warp_vote(VoteArgs A, const PT *__
         for (uint32_t x0 = lane; x0 < n; x0 += 8 * 32) {
             PT b8[8];
 #pragma unroll
-            for (int u = 0; u < 8; u++) b8[u] = x0 + 32 * u < n ? __ldcs(ent + e0 + x0 + 32 * u) : (PT)0;
+            for (int u = 0; u < 8; u++) b8[u] = x0 + 32 * u < n ? ent[e0 + x0 + 32 * u] : (PT)0;
 #pragma unroll
             for (int u = 0; u < 8; u++)
                 if (x0 + 32 * u < n && (uint32_t)(b8[u] >> A.nbits) - r0 < r1 - r0) {
@@ -1233,7 +1243,8 @@ __global__ void __launch_bounds__(kVW * 32) k_warp_vote(VoteArgs A, const PT *__
         for (uint32_t x0 = lane; x0 < n; x0 += 8 * 32) {
             PT b8[8];
 #pragma unroll
-            for (int u = 0; u < 8; u++) b8[u] = x0 + 32 * u < n ? ent[e0 + x0 + 32 * u] : (PT)0;
+            for (int u = 0; u < 8; u++)
+                b8[u] = x0 + 32 * u < n ? (p + 1 == P ? __ldcs(ent + e0 + x0 + 32 * u) : ent[e0 + x0 + 32 * u]) : (PT)0;
 #pragma unroll
             for (int u = 0; u < 8; u++) {
                 if (x0 + 32 * u >= n || (uint32_t)(b8[u] >> A.nbits) - r0 >= r1 - r0) continue;
@@ -1325,7 +1336,7 @@ __global__ void __launch_bounds__(512) k_long_vote(VoteArgs A, const PT *__restr
         __syncthreads();
         const uint64_t g = i >> A.gshift;
         const uint32_t local = i & ((1u << A.gshift) - 1);
-        for (uint64_t e = A.goff[g] + threadIdx.x; e < A.goff[g + 1]; e += blockDim.x) {
+        for (uint64_t e = A.goff[g] - A.ebase + threadIdx.x; e < A.goff[g + 1] - A.ebase; e += blockDim.x) {
             const PT en = ent[e];
             if ((uint32_t)(en >> A.nbits) == local) vadd(K, C, slots, (uint32_t)(en & jmask));
         }
@@ -1936,11 +1947,12 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     const dim3 eg((unsigned)std::max<uint64_t>(1, (nwarps + 7) / 8), p.b);
     const unsigned mg = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(nmedium, c->num_sms * 8));
     cudaMemsetAsync(scal + Scal::NSMALLEMIT, 0, 8, s);
+    const GroupRange all{0, ng, 0};
     k_pairs_grp<0, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, tpw, gcnt, nullptr, nullptr, nullptr,
-                                          scal + Scal::NSMALLEMIT), FAST_LAUNCHED(c);
+                                          scal + Scal::NSMALLEMIT, all), FAST_LAUNCHED(c);
     if (nmedium)
         k_medium_grp<0, PT><<<mg, 256, 0, s>>>(ea, medium, scal + Scal::NMEDIUM, gshift, nbits, gcnt, nullptr, nullptr,
-                                               nullptr), FAST_LAUNCHED(c);
+                                               nullptr, all), FAST_LAUNCHED(c);
     if ((st = scan_excl(c, gcnt, goff, ng, 1, goff + ng, s))) return st;
     uint64_t S = 0;
     cudaMemcpyAsync(&S, goff + ng, 8, cudaMemcpyDeviceToHost, s);
@@ -1948,16 +1960,36 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     if ((st = sync_check(c, s, "pair count"))) return st;
     S_out = S;
     c->stats.n_pairs_small = c->h_scal[Scal::NSMALLEMIT];
-    if ((st = alloc(&ent, S))) return st;
-    stage_mark(c, 10, s);
-    k_pairs_grp<1, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, tpw, nullptr, goff, gcur, ent, nullptr),
-        FAST_LAUNCHED(c);
-    stage_mark(c, 12, s);
-    if (nmedium)
-        k_medium_grp<1, PT><<<mg, 256, 0, s>>>(ea, medium, scal + Scal::NMEDIUM, gshift, nbits, nullptr, goff, gcur,
-                                               ent), FAST_LAUNCHED(c);
 
-    stage_mark(c, 11, s);
+    // Query partitions (§6.4): consecutive row-group ranges of about equal
+    // pair counts, each written and voted in turn, so the pair buffer holds
+    // one range.  As many as query_part asks for, or as the HBM budget needs.
+    uint32_t nparts = std::max<uint32_t>(1, p.query_part);
+    if (c->budget) {
+        const uint64_t room = c->budget > c->live ? (c->budget - c->live) / 2 : 0;
+        const uint64_t need = S * sizeof(PT);
+        if (room && need > room) nparts = std::max<uint64_t>(nparts, (need + room - 1) / room);
+    }
+    nparts = (uint32_t)std::min<uint64_t>(nparts, std::max<uint64_t>(1, ng));
+    std::vector<uint64_t> cut{0, ng};  // group boundaries of the partitions
+    uint64_t part_max = S;
+    if (nparts > 1) {
+        std::vector<uint64_t> hg(ng + 1);
+        cudaMemcpyAsync(hg.data(), goff, (ng + 1) * 8, cudaMemcpyDeviceToHost, s);
+        if ((st = sync_check(c, s, "partition offsets"))) return st;
+        cut.assign(1, 0);
+        for (uint32_t q = 1; q < nparts; q++) {
+            const uint64_t want = S * q / nparts;
+            const uint64_t g = std::lower_bound(hg.begin(), hg.end(), want) - hg.begin();
+            if (g > cut.back() && g < ng) cut.push_back(g);
+        }
+        cut.push_back(ng);
+        part_max = 0;
+        for (size_t q = 0; q + 1 < cut.size(); q++) part_max = std::max(part_max, hg[cut[q + 1]] - hg[cut[q]]);
+    }
+    c->stats.query_parts = (uint32_t)(cut.size() - 1);
+    if ((st = alloc(&ent, part_max))) return st;
+
     // hash capacity: twice the power of two above the target (group sizes vary), at least 4096
     uint32_t vcap = 64;
     while (vcap < (c->group_pairs ? c->group_pairs : kVTargetDefault)) vcap <<= 1;
@@ -1972,9 +2004,16 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper, k_warp_vote<PT>, kVW * 32, wsm);
     uint2 *slow = nullptr;  // (group, rows r0 << 16 | r1) left to the block kernel
     if ((st = alloc(&slow, 8 * ng))) return st;
+    const size_t rsm = (size_t)2 * kRowBlockSlots * 4;
+    cudaFuncSetAttribute(k_long_vote<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
     uint64_t sp_cap = std::max<uint64_t>(N, 1 << 20);
-    VoteArgs va{goff, ng, N, gshift, nbits, p.v, vcap, sp_cnt, sp_start, nullptr, nullptr, 0, scal + Scal::CUR_SPARSE,
-                long_rows, scal + Scal::NLONG, N};
+    VoteArgs va{goff, ng, N, 0, ng, 0, gshift, nbits, p.v, vcap, sp_cnt, sp_start, nullptr, nullptr, 0,
+                scal + Scal::CUR_SPARSE, long_rows, scal + Scal::NLONG, N};
+    std::vector<uint64_t> hgb(cut.size());  // goff at the cuts
+    if (cut.size() > 2) {
+        for (size_t q = 0; q < cut.size(); q++) cudaMemcpyAsync(&hgb[q], goff + cut[q], 8, cudaMemcpyDeviceToHost, s);
+        if ((st = sync_check(c, s, "partition bases"))) return st;
+    }
     for (int attempt = 0; attempt < 2; attempt++) {
         uint32_t *sp_j = nullptr;
         uint8_t *sp_v = nullptr;
@@ -1986,46 +2025,62 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
         va.sp_cap = sp_cap;
         cudaMemsetAsync(sp_cnt, 0, N * 4, s);
         cudaMemsetAsync(scal + Scal::CUR_SPARSE, 0, 8, s);
-        cudaMemsetAsync(scal + Scal::NLONG, 0, 8, s);
-        cudaMemsetAsync(scal + Scal::NSLOW, 0, 8, s);
-        stage_mark(c, 13, s);
-        k_warp_vote<PT><<<(unsigned)std::max<uint64_t>(
-                              1, std::min<uint64_t>((ng + kVW - 1) / kVW, (uint64_t)c->num_sms * std::max(wper, 1))),
-                          kVW * 32, wsm, s>>>(va, ent, slow, scal + Scal::NSLOW), FAST_LAUNCHED(c);
-        stage_mark(c, 14, s);
-        k_group_vote<PT><<<(unsigned)std::max<uint64_t>(1, (uint64_t)c->num_sms * std::max(vper, 1)), 256, vsm,
-                           s>>>(va, ent, slow, scal + Scal::NSLOW), FAST_LAUNCHED(c);
-        if ((st = read_scal(c, s, "row votes"))) return st;
-        const uint64_t nlong = c->h_scal[Scal::NLONG];
-        if (nlong > N) return set_error(c, FAST_EINTERNAL, "long-row list overflow");
-        c->stats.n_long_rows = nlong;
-        c->stats.n_huge_rows = 0;
-        if (nlong) {
-            std::vector<uint2> hl(nlong);
-            cudaMemcpyAsync(hl.data(), long_rows, nlong * sizeof(uint2), cudaMemcpyDeviceToHost, s);
-            if ((st = sync_check(c, s, "long rows"))) return st;
-            std::vector<uint64_t> gofs(nlong);
-            uint64_t gtot = 0;
-            for (uint64_t r = 0; r < nlong; r++) {
-                uint64_t slots = 32;
-                while (slots < 2ull * hl[r].y) slots <<= 1;
-                c->stats.max_row = std::max<uint64_t>(c->stats.max_row, hl[r].y);
-                gofs[r] = gtot;
-                if (slots > kRowBlockSlots) {
-                    gtot += 2 * slots;
-                    c->stats.n_huge_rows++;
-                }
-            }
-            uint32_t *gscr = nullptr;
-            uint64_t *d_gofs = nullptr;
-            if ((st = alloc(&gscr, gtot)) || (st = alloc(&d_gofs, nlong))) return st;
-            cudaMemcpyAsync(d_gofs, gofs.data(), nlong * 8, cudaMemcpyHostToDevice, s);
-            const size_t rsm = (size_t)2 * kRowBlockSlots * 4;
-            cudaFuncSetAttribute(k_long_vote<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
-            k_long_vote<PT><<<(unsigned)std::min<uint64_t>(nlong, c->num_sms * 2), 512, rsm, s>>>(va, ent, long_rows,
-                                                                                                 nlong, gscr, d_gofs),
+        c->stats.n_long_rows = c->stats.n_huge_rows = 0;
+        for (size_t q = 0; q + 1 < cut.size(); q++) {
+            const GroupRange gr{cut[q], cut[q + 1], cut.size() > 2 ? hgb[q] : 0};
+            va.g_lo = gr.g_lo;
+            va.g_hi = gr.g_hi;
+            va.ebase = gr.ebase;
+            // write the range's pairs (gcur restarts per range: every group is in exactly one)
+            if (cut.size() > 2 || attempt > 0) cudaMemsetAsync(gcur + gr.g_lo, 0, (gr.g_hi - gr.g_lo) * 4, s);
+            stage_mark(c, 10, s);
+            k_pairs_grp<1, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, tpw, nullptr, goff, gcur, ent, nullptr, gr),
                 FAST_LAUNCHED(c);
-            if ((st = read_scal(c, s, "long rows"))) return st;
+            stage_mark(c, 12, s);
+            if (nmedium)
+                k_medium_grp<1, PT><<<mg, 256, 0, s>>>(ea, medium, scal + Scal::NMEDIUM, gshift, nbits, nullptr, goff,
+                                                       gcur, ent, gr), FAST_LAUNCHED(c);
+            stage_mark(c, 11, s);
+            // vote the range
+            cudaMemsetAsync(scal + Scal::NLONG, 0, 8, s);
+            cudaMemsetAsync(scal + Scal::NSLOW, 0, 8, s);
+            stage_mark(c, 13, s);
+            const uint64_t ngr = gr.g_hi - gr.g_lo;
+            k_warp_vote<PT><<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>((ngr + kVW - 1) / kVW,
+                                                                                  (uint64_t)c->num_sms *
+                                                                                      std::max(wper, 1))),
+                              kVW * 32, wsm, s>>>(va, ent, slow, scal + Scal::NSLOW), FAST_LAUNCHED(c);
+            stage_mark(c, 14, s);
+            k_group_vote<PT><<<(unsigned)std::max<uint64_t>(1, (uint64_t)c->num_sms * std::max(vper, 1)), 256, vsm,
+                               s>>>(va, ent, slow, scal + Scal::NSLOW), FAST_LAUNCHED(c);
+            if ((st = read_scal(c, s, "row votes"))) return st;
+            const uint64_t nlong = c->h_scal[Scal::NLONG];
+            if (nlong > N) return set_error(c, FAST_EINTERNAL, "long-row list overflow");
+            c->stats.n_long_rows += nlong;
+            if (nlong) {
+                std::vector<uint2> hl(nlong);
+                cudaMemcpyAsync(hl.data(), long_rows, nlong * sizeof(uint2), cudaMemcpyDeviceToHost, s);
+                if ((st = sync_check(c, s, "long rows"))) return st;
+                std::vector<uint64_t> gofs(nlong);
+                uint64_t gtot = 0;
+                for (uint64_t r = 0; r < nlong; r++) {
+                    uint64_t slots = 32;
+                    while (slots < 2ull * hl[r].y) slots <<= 1;
+                    c->stats.max_row = std::max<uint64_t>(c->stats.max_row, hl[r].y);
+                    gofs[r] = gtot;
+                    if (slots > kRowBlockSlots) {
+                        gtot += 2 * slots;
+                        c->stats.n_huge_rows++;
+                    }
+                }
+                uint32_t *gscr = nullptr;
+                uint64_t *d_gofs = nullptr;
+                if ((st = alloc(&gscr, gtot)) || (st = alloc(&d_gofs, nlong))) return st;
+                cudaMemcpyAsync(d_gofs, gofs.data(), nlong * 8, cudaMemcpyHostToDevice, s);
+                k_long_vote<PT><<<(unsigned)std::min<uint64_t>(nlong, c->num_sms * 2), 512, rsm, s>>>(
+                    va, ent, long_rows, nlong, gscr, d_gofs), FAST_LAUNCHED(c);
+                if ((st = read_scal(c, s, "long rows"))) return st;
+            }
         }
         const uint64_t used = c->h_scal[Scal::CUR_SPARSE];
         if (used <= sp_cap) return FAST_OK;
@@ -2062,6 +2117,7 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
     c->stats.n_fingerprints = N;
     c->stats.n_dropped = tb->n_dropped;
     c->stats.n_long_rows = c->stats.n_huge_rows = c->stats.max_row = 0;
+    c->stats.query_parts = 1;
     const uint32_t large_min = large_min_for(c, N);
     const unsigned blocksN = std::max(1u, std::min<unsigned>(ceil_div(N, 256), c->num_sms * 8));
 
@@ -2250,7 +2306,6 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
     c->stats.n_dense_pairs = dense_pairs;
     c->stats.n_groups = ngroups;
     c->stats.n_detections = M;
-    c->stats.query_parts = 1;
     c->stats.map_slots = 0;
     *out = res;
     return FAST_OK;

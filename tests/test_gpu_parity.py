@@ -96,7 +96,8 @@ DETECT_CASES = [
     ("c0", 8192, dict(v=1, excl=0), dict(large_min=6)),
     ("c1", 60_000, dict(), dict()),
     ("c1", 60_000, dict(), dict(large_min=16)),               # dense groups on every large bucket
-    ("c1", 60_000, dict(query_part=3), dict(map_load=0.8)),   # partitioned vote map
+    ("c1", 60_000, dict(query_part=3), dict(map_load=0.8)),   # three row partitions of the pair buffer
+    ("c1", 60_000, dict(query_part=7), dict(large_min=16)),   # seven partitions, dense groups everywhere
     ("c1", 40_000, dict(occ_num=0), dict(large_min=64)),      # no filter: the 60 s source stays
     ("c1", 20_000, dict(kind=0, r=2, b=40, v=3), dict()),     # MinHash on the C1 shape
     ("c1", 60_000, dict(), dict(vote_map=1)),                 # global vote map instead of per-row votes
@@ -122,6 +123,50 @@ def test_detections_bit_exact(name, n, over, opts):
     assert st["n_detections"] == len(want[0])
     res.free()
     s.close()
+
+
+def test_row_partitions_identical_and_forced_by_budget():
+    # §6.4: the partitioned search yields the same list; a budget too small
+    # for the whole pair buffer splits it without being asked
+    from paper_1803_09835_gb300 import FastError, Searcher
+    w = synth.scaled("c1", 40_000)
+    idx = torch.from_numpy(synth.generate(w, ld=_pad(w.K))).cuda()
+    p = w.params()
+    s = _searcher(p)
+    ref = s.detect(idx).numpy()
+    st = s.stats()
+    assert st["query_parts"] == 1
+    peak, need = st["peak_bytes"], st["n_emissions"] * 4
+    s.close()
+    for qp in (2, 5):
+        sq = _searcher(dict(p, query_part=qp))
+        _assert_lists(sq.detect(idx).numpy(), ref)
+        assert sq.stats()["query_parts"] == qp
+        sq.close()
+    # a budget-driven split needs the pair buffer to dominate memory: few
+    # single-function MinHash tables collide often (~2.5 % per table here)
+    from dataclasses import replace
+    wb = replace(synth.scaled("c1", 20_000), n_templates=0, periods=(), kind=0, r=1, b=10, v=3, excl=0, occ_num=0)
+    idxb = torch.from_numpy(synth.generate(wb, ld=_pad(wb.K))).cuda()
+    pb = wb.params()
+    s = _searcher(pb, large_min=10**9)  # no dense groups: every pair goes through the pair buffer
+    refb = s.detect(idxb).numpy()
+    st = s.stats()
+    peak, need = st["peak_bytes"], st["n_emissions"] * 4
+    assert need > peak / 2 and len(refb[0]) > 0
+    s.close()
+    split = 0
+    for frac in (0.3, 0.45, 0.6):
+        sb = Searcher(pb, hbm_budget_bytes=int(peak - frac * need), large_min=10**9)
+        try:
+            got = sb.detect(idxb).numpy()
+        except FastError:
+            sb.close()
+            continue
+        _assert_lists(got, refb)
+        split += sb.stats()["query_parts"] >= 2
+        sb.close()
+    assert split >= 1
 
 
 def test_dense_and_sparse_paths_agree():
