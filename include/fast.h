@@ -210,10 +210,11 @@ fast_status fast_detect_batch(fast_ctx *ctx, const uint16_t *d_idx, const uint64
 typedef struct fast_plan fast_plan;
 
 typedef struct {
-    uint32_t vote_map;   /* 1 = global vote map, 0 = row-partitioned votes */
-    uint32_t large_min;  /* dense-group threshold (0 = automatic)          */
-    float map_load;      /* vote-map load factor                           */
-    float ms;            /* measured search time of this choice            */
+    uint32_t vote_map;    /* 1 = global vote map, 0 = row-partitioned votes  */
+    uint32_t large_min;   /* dense-group threshold (0 = automatic)           */
+    float map_load;       /* vote-map load factor                            */
+    float ms;             /* measured search time of this choice             */
+    uint32_t group_pairs; /* pairs per row group of the row votes (0 = default) */
 } fast_plan_choice;
 
 typedef struct {
@@ -229,7 +230,7 @@ fast_status fast_plan_create(fast_ctx *ctx, const uint16_t *d_idx, const uint64_
 
 /* Replays the build graph and searches; out[x] as fast_detect_batch gives.
  * The first run times every candidate option set (vote path, dense-group
- * threshold, map load) and keeps the fastest for later runs; the context's
+ * threshold, row-group size, map load) and keeps the fastest for later runs; the context's
  * own options are left as they were.  Every candidate gives the same list. */
 fast_status fast_plan_run(fast_plan *plan, fast_result **out, void *stream);
 

@@ -49,7 +49,7 @@ class fast_stats(ctypes.Structure):
 
 class fast_plan_choice(ctypes.Structure):
     _fields_ = [("vote_map", ctypes.c_uint32), ("large_min", ctypes.c_uint32), ("map_load", ctypes.c_float),
-                ("ms", ctypes.c_float)]
+                ("ms", ctypes.c_float), ("group_pairs", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

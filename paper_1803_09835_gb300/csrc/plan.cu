@@ -6,8 +6,8 @@
 // -- the signature launch, the radix passes (4 key passes + the station
 // pass), the occurrence filter -- into a graph with every buffer inside the
 // arena, so replays allocate nothing.  The first run times the search under
-// each candidate option set (vote path, dense-group threshold, map load) and
-// keeps the fastest; every option set gives the same detections.
+// each candidate option set (vote path, dense-group threshold, row-group size,
+// map load) and keeps the fastest; every option set gives the same detections.
 #include <algorithm>
 
 #include "fast_internal.cuh"
@@ -39,6 +39,7 @@ fast_status apply(fast_ctx *c, const fast_plan_choice &o) {
     c->vote_map = o.vote_map != 0;
     c->large_min = o.large_min;
     c->map_load = o.map_load;
+    c->group_pairs = o.group_pairs;
     return FAST_OK;
 }
 
@@ -152,7 +153,7 @@ fast_status fast_plan_run(fast_plan *P, fast_result **out, void *stream) {
     if (!P || !out) return FAST_EINVAL;
     fast_ctx *c = P->c;
     // the context's own options come back after the run
-    const fast_plan_choice saved{c->vote_map ? 1u : 0u, c->large_min, c->map_load, 0.f};
+    const fast_plan_choice saved{c->vote_map ? 1u : 0u, c->large_min, c->map_load, 0.f, c->group_pairs};
     const fast_status st = plan_run(P, out, (cudaStream_t)stream);
     apply(c, saved);
     return st;
@@ -182,8 +183,9 @@ static fast_status plan_run(fast_plan *P, fast_result **out, cudaStream_t s) {
     if (!P->tuned) {
         c->large_min = 0;
         const uint32_t lm = large_min_for(c, P->N);
-        const fast_plan_choice cand[] = {
-            {0, 0, 0.5f, 0.f}, {0, 2 * lm, 0.5f, 0.f}, {0, 8 * lm, 0.5f, 0.f}, {1, 0, 0.5f, 0.f}, {1, 0, 0.85f, 0.f}};
+        const fast_plan_choice cand[] = {{0, 0, 0.5f, 0.f, 0},      {0, 0, 0.5f, 0.f, 512},   {0, 0, 0.5f, 0.f, 2048},
+                                         {0, 2 * lm, 0.5f, 0.f, 0}, {0, 8 * lm, 0.5f, 0.f, 0}, {1, 0, 0.5f, 0.f, 0},
+                                         {1, 0, 0.85f, 0.f, 0}};
         float best_ms = 1e30f;
         cudaEvent_t a, b;
         cudaEventCreate(&a);
