@@ -17,6 +17,7 @@
 // Requests of one station run in admission order, so request q sees history,
 // every earlier batch of its station and itself; stations run concurrently,
 // each on its own stream, as HBM budget admits them.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -544,20 +545,65 @@ fast_status process(fast_server *S, fast_station *st, fast_request *r) {
     return sync_check(c, s, "request");
 }
 
+// Continuous batching: a worker takes the request at the head of its
+// station's queue together with the requests queued right behind it (their
+// window ids follow on, admission order), up to kMergeWindows windows, and
+// searches them as one batch.  Pair (i, j) then belongs to the request whose
+// windows hold j; that request would have found it alone too, because every
+// window of the earlier requests precedes j and would have been in the delta.
+constexpr uint64_t kMergeWindows = 16384;
+
+void finish(fast_request *r, fast_status res, const std::string &msg) {
+    {
+        std::lock_guard<std::mutex> lk(r->mu);
+        r->status = res;
+        r->msg = msg;
+        r->state = res ? 2 : 1;
+        r->t_done = std::chrono::steady_clock::now();
+    }
+    r->cv.notify_all();
+}
+
 void worker_main(fast_server *S, fast_station *st) {
     cudaSetDevice(S->device);
     for (;;) {
-        fast_request *r = nullptr;
+        std::vector<fast_request *> grp;
         {
             std::unique_lock<std::mutex> lk(st->mu);
             st->cv.wait(lk, [&] { return S->stop.load() || !st->queue.empty(); });
             if (st->queue.empty()) return;  // stopping
-            r = st->queue.front();
+            grp.push_back(st->queue.front());
             st->queue.pop_front();
+            uint64_t ntot = grp[0]->n;
+            while (S->fail_at.load() != grp[0]->id && !st->queue.empty()) {
+                fast_request *q = st->queue.front();
+                const fast_request *last = grp.back();
+                if (q->ld != grp[0]->ld || S->fail_at.load() == q->id || ntot + q->n > kMergeWindows ||
+                    q->first_id != last->first_id + last->n)
+                    break;
+                if (S->budget && S->resident + request_bytes(S->p, (uint32_t)(ntot + q->n), q->ld) > S->budget) break;
+                grp.push_back(q);
+                st->queue.pop_front();
+                ntot += q->n;
+            }
+        }
+        fast_request *r = grp[0];
+        fast_request merged;
+        fast_request *work = r;
+        if (grp.size() > 1) {  // one input, ids from the first request on
+            merged.id = r->id;
+            merged.station = r->station;
+            merged.ld = r->ld;
+            merged.first_id = r->first_id;
+            for (const fast_request *q : grp) {
+                merged.n += q->n;
+                merged.idx.insert(merged.idx.end(), q->idx.begin(), q->idx.end());
+            }
+            work = &merged;
         }
         fast_status res = FAST_OK;
         std::string msg;
-        const uint64_t need = request_bytes(S->p, r->n, r->ld);
+        const uint64_t need = request_bytes(S->p, work->n, work->ld);
         if (S->fail_at.load() == r->id) {
             res = FAST_EINTERNAL;  // injected failure
             msg = "injected request failure";
@@ -576,20 +622,29 @@ void worker_main(fast_server *S, fast_station *st) {
                 res = FAST_ETIMEOUT;
                 msg = "server stopped";
             } else {
-                res = process(S, st, r);
+                res = process(S, st, work);
                 if (res) msg = st->ctx->err;
             }
             S->in_flight -= need;
             S->adm_cv.notify_all();
         }
-        {
-            std::lock_guard<std::mutex> lk(r->mu);
-            r->status = res;
-            r->msg = msg;
-            r->state = res ? 2 : 1;
-            r->t_done = std::chrono::steady_clock::now();
+        if (grp.size() > 1 && !res) {  // each request takes the pairs whose j lies in its windows
+            for (fast_request *q : grp) {
+                q->ri.clear();
+                q->rj.clear();
+                q->rv.clear();
+            }
+            std::vector<uint64_t> starts;
+            for (const fast_request *q : grp) starts.push_back(q->first_id);
+            for (size_t e = 0; e < merged.ri.size(); e++) {
+                const uint64_t j = merged.rj[e];
+                const size_t k = std::upper_bound(starts.begin(), starts.end(), j) - starts.begin() - 1;
+                grp[k]->ri.push_back(merged.ri[e]);
+                grp[k]->rj.push_back(merged.rj[e]);
+                grp[k]->rv.push_back(merged.rv[e]);
+            }
         }
-        r->cv.notify_all();
+        for (fast_request *q : grp) finish(q, res, msg);
     }
 }
 
