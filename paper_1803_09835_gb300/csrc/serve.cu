@@ -551,7 +551,7 @@ fast_status process(fast_server *S, fast_station *st, fast_request *r) {
 // searches them as one batch.  Pair (i, j) then belongs to the request whose
 // windows hold j; that request would have found it alone too, because every
 // window of the earlier requests precedes j and would have been in the delta.
-constexpr uint64_t kMergeWindows = 16384;
+constexpr uint64_t kMergeWindows = 65536;
 
 void finish(fast_request *r, fast_status res, const std::string &msg) {
     {
