@@ -104,6 +104,8 @@ struct EnumArgs {
     uint32_t i_lo, i_hi;  // query partition [i_lo, i_hi)
     uint32_t nparts;      // counting: partition of i is i * nparts / N
     Stations st;          // station ranges: buckets never cross them
+    const uint32_t *fbits;  // flag bitmap over ids (dropped or in a dense group); with fsid_out:
+    uint32_t *fsid_out;     // the counting pass writes fsid while it reads sid
 };
 
 __device__ __forceinline__ bool pair_live(const EnumArgs &a, uint32_t i, uint32_t j) {
@@ -599,7 +601,7 @@ struct PairWin {
 
 __device__ __forceinline__ PairWin pair_tile(const EnumArgs &a, const uint32_t *__restrict__ K,
                                              const uint32_t *__restrict__ S, const uint32_t *__restrict__ FS,
-                                             uint64_t T) {
+                                             uint32_t *__restrict__ FO, uint64_t T, bool own) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t x = T * 32 + lane, N = a.N;
     const bool valid = x < N;
@@ -611,8 +613,15 @@ __device__ __forceinline__ PairWin pair_tile(const EnumArgs &a, const uint32_t *
     PairWin w;
     w.heads = __ballot_sync(~0u, head);
     w.lab = kLabDrop;
-    if (FS) {  // only flagged entries (dropped or in a dense group) need the random lookups
-        const uint32_t raw = valid ? __ldcs(FS + x) : 0u;
+    if (FS || FO) {  // only flagged entries (dropped or in a dense group) need the random lookups
+        uint32_t raw = 0;
+        if (FS) {
+            raw = valid ? __ldcs(FS + x) : 0u;
+        } else if (valid) {  // counting pass: flag the id from the bitmap and keep the flagged copy
+            const uint32_t id = __ldcs(S + x);
+            raw = id | (__ldg(a.fbits + (id >> 5)) >> (id & 31)) << 31;
+            if (own) FO[x] = raw;
+        }
         w.id = raw & 0x7FFFFFFFu;
         if (valid) w.lab = !(raw >> 31) ? kNone : a.drop[w.id] ? kLabDrop : __ldg(a.label + w.id);
     } else {
@@ -636,23 +645,7 @@ __global__ void __launch_bounds__(256) k_flag_bits(const uint8_t *__restrict__ d
     }
 }
 
-// fsid = sid with bit 31 = flag bit of the id, for all n table entries
-// (sid and fsid 16-byte aligned; four entries per load, the ragged tail alone).
-__device__ __forceinline__ uint32_t flag_id(uint32_t id, const uint32_t *__restrict__ bits) {
-    return id | (bits[id >> 5] >> (id & 31)) << 31;
-}
 
-__global__ void __launch_bounds__(256) k_flag_ids(const uint32_t *__restrict__ sid, uint64_t n,
-                                                  const uint32_t *__restrict__ bits, uint32_t *__restrict__ fsid) {
-    const uint64_t n4 = n / 4, tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint4 *s4 = reinterpret_cast<const uint4 *>(sid);
-    uint4 *f4 = reinterpret_cast<uint4 *>(fsid);
-    for (uint64_t q = tid; q < n4; q += (uint64_t)gridDim.x * blockDim.x) {
-        const uint4 v = s4[q];
-        f4[q] = make_uint4(flag_id(v.x, bits), flag_id(v.y, bits), flag_id(v.z, bits), flag_id(v.w, bits));
-    }
-    if (tid < n - n4 * 4) fsid[n4 * 4 + tid] = flag_id(sid[n4 * 4 + tid], bits);
-}
 
 // Row groups [g_lo, g_hi) written by one emission pass; their entries start at
 // goff[g] - ebase in that pass's buffer (all groups, ebase 0, when unsplit).
@@ -675,18 +668,19 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
     const uint64_t N = a.N, ntiles = (N + 31) / 32;
     const uint32_t *K = a.skey + (uint64_t)t * N;
     const uint32_t *S = a.sid + (uint64_t)t * N;
-    const uint32_t *FS = a.fsid ? a.fsid + (uint64_t)t * N : nullptr;
+    const uint32_t *FS = MODE == 1 && a.fsid ? a.fsid + (uint64_t)t * N : nullptr;
+    uint32_t *FO = MODE == 0 && a.fsid_out ? a.fsid_out + (uint64_t)t * N : nullptr;
     const uint32_t lmask = (1u << gshift) - 1;
     const uint64_t T0 = ((uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32) * tiles_per_warp;
     if (T0 >= ntiles) return;  // warp-uniform
     const uint64_t T1 = min(T0 + tiles_per_warp, ntiles);
     __shared__ PairSmem ps[8];
     PairSmem &W = ps[threadIdx.x / 32];
-    uint32_t hp = T0 ? pair_tile(a, K, S, FS, T0 - 1).heads : ~0u;
-    PairWin c = pair_tile(a, K, S, FS, T0);
+    uint32_t hp = T0 ? pair_tile(a, K, S, FS, FO, T0 - 1, false).heads : ~0u;
+    PairWin c = pair_tile(a, K, S, FS, FO, T0, true);
     unsigned long long emitted = 0;  // counting pass: pairs of this lane's entries
     for (uint64_t T = T0; T < T1; T++) {
-        const PairWin n = pair_tile(a, K, S, FS, T + 1);
+        const PairWin n = pair_tile(a, K, S, FS, FO, T + 1, T + 1 < T1);
         // bucket of position L: first position s0 (window coordinates, previous
         // tile = 0..31) and end e (coordinates of current + next = 0..63)
         const uint64_t hpc = (uint64_t)c.heads << 32 | hp;
@@ -2215,14 +2209,14 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
 
     // ---- sparse pairs: group-partitioned emission, per-row votes
     ea.label = label;
-    {  // flagged copy of the id lists: the pair passes then look up drop / label only for flagged ids
+    {  // flagged copy of the id lists (made by the counting pass): the pair passes look up drop / label only for flagged ids
         uint32_t *bits = nullptr, *fsid = nullptr;
         const uint64_t n = (uint64_t)nb * N;
         if ((st = alloc(&bits, (N + 31) / 32)) || (st = alloc(&fsid, n))) return fail(st);
         k_flag_bits<<<std::max(1u, std::min<unsigned>(ceil_div((N + 31) / 32, 256), c->num_sms * 8)), 256, 0, s>>>(
             tb->d_drop, label, N, bits), FAST_LAUNCHED(c);
-        k_flag_ids<<<std::max(1u, std::min<unsigned>(ceil_div(n / 4 + 1, 256), c->num_sms * 16)), 256, 0, s>>>(
-            tb->d_sid, n, bits, fsid), FAST_LAUNCHED(c);
+        ea.fbits = bits;      // the counting pass fills fsid,
+        ea.fsid_out = fsid;   // the writing pass reads it
         ea.fsid = fsid;
     }
     uint32_t *sp_cnt = nullptr, *sp_j = nullptr;
