@@ -7,8 +7,16 @@
 // GB300 design.  Every bucket pair is one "emission"; emissions from all b
 // tables must be summed per pair.  Buckets come in two very different kinds:
 //   * sparse: the background, sizes ~2..50, almost every pair seen once.
-//     Their pairs are summed in a device open-addressing hash map of packed
-//     (i, j) -> uint8 votes (one 64-bit slot: i:28 | j:28 | votes:8).
+//     Default (row-partitioned) path: a counting pass sizes, per row group
+//     (2^gshift consecutive ids i), the region its pairs take; a writing pass
+//     appends every pair (i, j) there as a packed (row-in-group, j) word; a
+//     warp per group then counts the votes of its pairs in shared memory (a
+//     counting filter first, an exact hash for the few that pass) and keeps
+//     those with votes >= v in (i, j) order.  The rows are assembled into the
+//     canonical list with one scan, no global sort.  Alternative path
+//     (`vote_map`): one device open-addressing map of packed (i, j) -> votes
+//     (a 64-bit slot: i:28 | j:28 | votes:8) per query partition, then a radix
+//     sort of the kept pairs.
 //   * dense: a repeating source (e.g. periodic noise) puts thousands of
 //     near-copies in one bucket in most tables, so the same pairs recur in
 //     every table -- ~10^10 emissions for ~10^8 distinct pairs.  Buckets with
