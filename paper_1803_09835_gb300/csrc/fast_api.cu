@@ -302,6 +302,8 @@ void fast_tables_free(fast_tables *tb) {
     dfree(c, tb->d_sid, n * 4, tb->stream);
     dfree(c, tb->d_drop, tb->N ? tb->N : 1, tb->stream);
     dfree(c, tb->d_soff, (tb->nst + 1) * 8, tb->stream);
+    dfree(c, tb->d_big, tb->big_cap * sizeof(uint4), tb->stream);
+    dfree(c, tb->d_bigcnt, 16, tb->stream);
     delete tb;
 }
 

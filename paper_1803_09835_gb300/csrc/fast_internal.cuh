@@ -186,6 +186,11 @@ struct fast_tables {
     uint32_t *d_sid = nullptr;   // [b][N]
     uint8_t *d_drop = nullptr;   // [N]
     uint64_t n_dropped = 0;
+    // buckets of more than 32 entries (table, start, end, 0), found once by
+    // the filter and reused by the search; d_bigcnt = {count, small-bucket pairs}
+    uint4 *d_big = nullptr;
+    uint64_t big_cap = 0;
+    unsigned long long *d_bigcnt = nullptr;
     cudaStream_t stream = nullptr;
 };
 

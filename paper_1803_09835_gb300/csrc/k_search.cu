@@ -42,8 +42,9 @@ constexpr uint32_t kSmall = 32;  // buckets up to this size are enumerated by on
 
 // -------------------------------------------------------------- filter
 
-// Heavy bucket starts: size >= smin, i.e. occ_den * size > occ_num * N_s,
-// N_s the size of the bucket's station.
+// Heavy bucket starts by a scan of the keys, for thresholds within the small
+// bucket sizes: size >= smin, i.e. occ_den * size > occ_num * N_s, N_s the size
+// of the bucket's station.
 __global__ void k_heavy_find(const uint32_t *__restrict__ skey, uint64_t N, Stations S, uint32_t occ_num,
                              uint32_t occ_den, uint4 *__restrict__ list, unsigned long long *__restrict__ count,
                              uint64_t cap, uint32_t *err) {
@@ -76,11 +77,28 @@ __global__ void k_heavy_find(const uint32_t *__restrict__ skey, uint64_t N, Stat
     }
 }
 
-__global__ void k_heavy_mark(const uint4 *__restrict__ list, const unsigned long long *__restrict__ count,
-                             uint64_t cap, const uint32_t *__restrict__ sid, uint64_t N, uint32_t *__restrict__ heavy) {
+// Heavy buckets, from the list of big ones: occ_den * size > occ_num * N_s
+// (N_s the size of the bucket's station); every id in a heavy bucket counts
+// one more table.
+__global__ void k_heavy_mark_list(const uint4 *__restrict__ list, const unsigned long long *__restrict__ count,
+                                  uint64_t cap, const uint32_t *__restrict__ sid, uint64_t N, uint32_t *__restrict__ heavy) {
     const uint64_t n = min((uint64_t)*count, cap);
     for (uint64_t b = blockIdx.x; b < n; b += gridDim.x) {
         uint4 e = list[b];
+        const uint32_t *s = sid + (uint64_t)e.x * N;
+        for (uint32_t q = e.y + threadIdx.x; q < e.z; q += blockDim.x) atomicAdd(&heavy[s[q]], 1u);
+    }
+}
+
+__global__ void k_heavy_mark(const uint4 *__restrict__ big, const unsigned long long *__restrict__ count,
+                             uint64_t cap, Stations S, uint32_t occ_num, uint32_t occ_den,
+                             const uint32_t *__restrict__ sid, uint64_t N, uint32_t *__restrict__ heavy) {
+    const uint64_t n = min((uint64_t)*count, cap);
+    for (uint64_t bi = blockIdx.x; bi < n; bi += gridDim.x) {
+        const uint4 e = big[bi];
+        const uint32_t sx = station_of(S, e.y);
+        const uint64_t ns = S.soff[sx + 1] - S.soff[sx];
+        if ((uint64_t)occ_den * (e.z - e.y) <= (uint64_t)occ_num * ns) continue;  // block-uniform
         const uint32_t *s = sid + (uint64_t)e.x * N;
         for (uint32_t q = e.y + threadIdx.x; q < e.z; q += blockDim.x) atomicAdd(&heavy[s[q]], 1u);
     }
@@ -1684,26 +1702,43 @@ fast_status filter_launch(fast_ctx *c, fast_tables *tb, cudaStream_t s) {
     fast_status st;
     unsigned long long *scal = reinterpret_cast<unsigned long long *>(c->d_scal);
     cudaMemsetAsync(scal, 0, sizeof(uint64_t) * kScal, s);
+    // big buckets of every table (the search takes the list over)
+    tb->big_cap = (uint64_t)p.b * (N / (kSmall + 1) + tb->nst);
+    if ((st = dalloc_t(c, &tb->d_big, tb->big_cap ? tb->big_cap : 1, s)) || (st = dalloc_t(c, &tb->d_bigcnt, 2, s)))
+        return st;
+    cudaMemsetAsync(tb->d_bigcnt, 0, 16, s);
+    if (N) {
+        EnumArgs ea{tb->d_skey, tb->d_sid, tb->d_drop, nullptr, nullptr, N, p.excl, 0, (uint32_t)N, 1,
+                    {tb->d_soff, tb->nst}};
+        const uint32_t ftpw = tiles_per_warp(c, N, p.b);
+        const dim3 eg((unsigned)std::max<uint64_t>(1, (((N + 31) / 32 + ftpw - 1) / ftpw + 7) / 8), p.b);
+        k_find_big<<<eg, 256, 0, s>>>(ea, ftpw, tb->d_big, tb->d_bigcnt, tb->big_cap, tb->d_bigcnt + 1, c->d_err),
+            FAST_LAUNCHED(c);
+    }
     uint32_t *heavy = nullptr;
     if (p.occ_num > 0 && N > 0) {
         uint64_t smin = ~0ull;  // smallest heavy size over the stations
         for (uint32_t x = 0; x < tb->nst; x++)
             if (tb->soff[x + 1] > tb->soff[x])
                 smin = std::min<uint64_t>(smin, (uint64_t)p.occ_num * (tb->soff[x + 1] - tb->soff[x]) / p.occ_den + 1);
-        const uint64_t cap = (uint64_t)p.b * (N / smin + tb->nst);
-        if (cap > (1ull << 26)) return set_error(c, FAST_EBUDGET, "occurrence threshold too small for this N");
-        uint4 *list = nullptr;
         if ((st = dalloc_t(c, &heavy, N, s))) return st;
-        if ((st = dalloc_t(c, &list, cap, s))) {
-            dfree(c, heavy, N * 4, s);
-            return st;
-        }
         cudaMemsetAsync(heavy, 0, N * 4, s);
-        dim3 g(std::max(1u, std::min<unsigned>(ceil_div(N, 256), 4096)), p.b);
-        k_heavy_find<<<g, 256, 0, s>>>(tb->d_skey, N, Stations{tb->d_soff, tb->nst}, p.occ_num, p.occ_den, list,
-                                       scal + Scal::NHEAVY, cap, c->d_err), FAST_LAUNCHED(c);
-        k_heavy_mark<<<c->num_sms * 4, 256, 0, s>>>(list, scal + Scal::NHEAVY, cap, tb->d_sid, N, heavy), FAST_LAUNCHED(c);
-        dfree(c, list, cap * sizeof(uint4), s);
+        if (smin > kSmall) {  // every heavy bucket is a big one
+            k_heavy_mark<<<c->num_sms * 4, 256, 0, s>>>(tb->d_big, tb->d_bigcnt, tb->big_cap,
+                                                        Stations{tb->d_soff, tb->nst}, p.occ_num, p.occ_den, tb->d_sid,
+                                                        N, heavy), FAST_LAUNCHED(c);
+        } else {  // small stations: heavy buckets among the small ones too, found by a scan
+            const uint64_t cap = (uint64_t)p.b * (N / smin + tb->nst);
+            if (cap > (1ull << 26)) return set_error(c, FAST_EBUDGET, "occurrence threshold too small for this N");
+            uint4 *list = nullptr;
+            if ((st = dalloc_t(c, &list, cap, s))) return st;
+            dim3 g(std::max(1u, std::min<unsigned>(ceil_div(N, 256), 4096)), p.b);
+            k_heavy_find<<<g, 256, 0, s>>>(tb->d_skey, N, Stations{tb->d_soff, tb->nst}, p.occ_num, p.occ_den, list,
+                                           scal + Scal::NHEAVY, cap, c->d_err), FAST_LAUNCHED(c);
+            k_heavy_mark_list<<<c->num_sms * 4, 256, 0, s>>>(list, scal + Scal::NHEAVY, cap, tb->d_sid, N, heavy),
+                FAST_LAUNCHED(c);
+            dfree(c, list, cap * sizeof(uint4), s);
+        }
     }
     k_drop<<<std::max(1u, std::min<unsigned>(ceil_div(N, 256), c->num_sms * 8)), 256, 0, s>>>(heavy, N, p.b, tb->d_drop,
                                                                                              scal + Scal::NDROP), FAST_LAUNCHED(c);
@@ -2126,14 +2161,12 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
     // ---- big buckets
     stage_mark(c, 3, s);
     cudaMemsetAsync(scal, 0, sizeof(uint64_t) * kScal, s);
-    const uint64_t big_cap = (uint64_t)nb * (N / (kSmall + 1) + 1);
-    uint4 *big = nullptr, *large = nullptr, *medium = nullptr;
-    if ((st = alloc(&big, big_cap))) return fail(st);
+    // big buckets: found with the filter when the tables were built
+    const uint64_t big_cap = tb->big_cap;
+    uint4 *big = tb->d_big, *large = nullptr, *medium = nullptr;
     EnumArgs ea{tb->d_skey, tb->d_sid, tb->d_drop, nullptr, nullptr, N, p.excl, 0, (uint32_t)N, 1, {tb->d_soff, tb->nst}};
-    const uint32_t ftpw = tiles_per_warp(c, N, nb);
-    const dim3 eg((unsigned)std::max<uint64_t>(1, (((N + 31) / 32 + ftpw - 1) / ftpw + 7) / 8), nb);
-    k_find_big<<<eg, 256, 0, s>>>(ea, ftpw, big, scal + Scal::NBIG, big_cap, scal + Scal::SMALLPAIRS, c->d_err),
-        FAST_LAUNCHED(c);
+    cudaMemcpyAsync(scal + Scal::NBIG, tb->d_bigcnt, 8, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(scal + Scal::SMALLPAIRS, tb->d_bigcnt + 1, 8, cudaMemcpyDeviceToDevice, s);
     if ((st = read_scal(c, s, "bucket scan"))) return fail(st);
     const uint64_t nbig = c->h_scal[Scal::NBIG];
     if ((st = alloc(&large, nbig)) || (st = alloc(&medium, nbig))) return fail(st);
