@@ -395,6 +395,99 @@ def gpu_arm(args, rank, world, local_rank):
     return 0
 
 
+# ------------------------------------------------------------- batched stations
+
+C2_GROUPS = ((12,), (11,), (10,), (9,), (8,), (7,), (6, 1), (5, 2), (4, 3))  # stations by months, ~<= 31M windows
+
+
+def batch_arm(args):
+    """The 12-station workload (stations of 1..12 months, 202,176,000 windows),
+    searched as batches of whole stations that fit the device: one
+    fast_detect_batch per group, device time by CUDA events, inputs resident.
+    The (4, 3)-month group is also run as a batch plan (graph-replayed build,
+    autotuned search), and its stations are checked against single-station
+    searches (a batch must find exactly what each station finds alone)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1803_09835_gb300 import Searcher
+    base = synth.workload("c2", station=0)
+    ld = ((base.K + 7) // 8) * 8
+    s = Searcher(dict(base.params(), query_part=args.query_part))
+    warm = min(args.warmup, 1)
+    groups = C2_GROUPS if not args.n else ((2, 1),)
+    if args.groups:
+        groups = tuple(tuple(int(m) for m in g.split("+")) for g in args.groups.split(","))
+    rows, tot_ms, tot_win, tot_det = [], 0.0, 0, 0
+    for grp in groups:
+        ws = [synth.workload("c2", station=m - 1) for m in grp]
+        if args.n:
+            ws = [synth.scaled("c2", args.n * m, station=m - 1) for m in grp]
+        t0 = time.perf_counter()
+        host = np.concatenate([synth.generate(w, ld=ld) for w in ws])
+        gen_s = time.perf_counter() - t0
+        d_idx = torch.from_numpy(host).cuda()
+        del host
+        lens = [w.N for w in ws]
+        for _ in range(warm):
+            for r in s.detect_batch(d_idx, lens):
+                r.free()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        res = s.detect_batch(d_idx, lens)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        det = [r.M for r in res]
+        row = {"months": list(grp), "windows": sum(lens), "ms": ms, "detections": det, "gen_s": gen_s}
+        if grp == (4, 3) or args.n:
+            # exactness across batching: each station alone
+            same = True
+            off = 0
+            for k, w in enumerate(ws):
+                alone = s.detect(d_idx[off:off + w.N])
+                same &= all(np.array_equal(a, b) for a, b in zip(alone.numpy(), res[k].numpy()))
+                alone.free()
+                off += w.N
+            row["batch_equals_alone"] = bool(same)
+            st = torch.cuda.Stream()
+            torch.cuda.synchronize()
+            plan = s.plan(d_idx, lens, st)
+            for r in plan.run():  # first run: the autotuner times its candidates
+                r.free()
+            torch.cuda.synchronize()
+            p0 = time.perf_counter()
+            pres = plan.run()
+            torch.cuda.synchronize()
+            info = plan.info()
+            row["plan"] = {"ms_wall": 1000 * (time.perf_counter() - p0), "build_graph_ms": info["build_ms"],
+                           "graph_kernels": info["graph_kernels"], "best": info["best"],
+                           "same": bool(all(all(np.array_equal(a, b) for a, b in zip(x.numpy(), y.numpy()))
+                                            for x, y in zip(pres, res)))}
+            for r in pres:
+                r.free()
+            plan.close()
+        for r in res:
+            r.free()
+        del d_idx
+        torch.cuda.empty_cache()
+        rows.append(row)
+        tot_ms += ms
+        tot_win += sum(lens)
+        tot_det += sum(det)
+        print(json.dumps(row), flush=True)
+    line = {"metric": "fingerprints/sec searched, stations batched", "value": tot_win / (tot_ms / 1000),
+            "unit": UNIT, "n_gpus": 1, "data": "synthetic", "dtype": "u32",
+            "config": {"workload": "c2: 12 stations of 1..12 months (N_s = s x 2,592,000), shared templates",
+                       "windows": tot_win, "batches": [list(g) for g in groups], "query_part": args.query_part},
+            "ms_total": tot_ms, "detections": tot_det}
+    print(json.dumps(line), flush=True)
+    s.close()
+    return 0
+
+
 # ------------------------------------------------------------------ serving leg
 
 def serving_arm(args):
@@ -500,9 +593,14 @@ def main():
     ap.add_argument("--duration", type=float, default=5.0)
     ap.add_argument("--budget-gb", type=int, default=150)
     ap.add_argument("--plain-requests", type=int, default=3)
+    ap.add_argument("--batch", action="store_true", help="12-station workload (c2) searched in station batches")
+    ap.add_argument("--query-part", type=int, default=4, help="query partitions of the pair buffer for --batch")
+    ap.add_argument("--groups", default="", help="--batch station groups by months, e.g. '12,6+1'")
     args = ap.parse_args()
     if args.serving:
         return serving_arm(args)
+    if args.batch:
+        return batch_arm(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -42,7 +42,9 @@ fast_status dalloc(fast_ctx *c, void **p, size_t bytes, cudaStream_t s) {
     cudaError_t e = cudaMallocFromPoolAsync(p, bytes, c->pool, s);
     if (e != cudaSuccess) {
         *p = nullptr;
-        return cuda_fail(c, e, "device allocation");
+        const std::string what = "device allocation of " + std::to_string(bytes) + " bytes (" +
+                                 std::to_string(c->live) + " held)";
+        return cuda_fail(c, e, what.c_str());
     }
     c->live += bytes;
     c->peak = std::max(c->peak, c->live);
@@ -377,6 +379,10 @@ namespace fastgb {
 fast_status split_stations(fast_ctx *c, fast_result *all, const std::vector<uint64_t> &soff, fast_result **out,
                            cudaStream_t s) {
     const uint32_t n_st = (uint32_t)soff.size() - 1;
+    if (n_st == 1) {  // one station: its ids are already local
+        out[0] = all;
+        return FAST_OK;
+    }
     unsigned long long *first = nullptr;
     uint64_t *d_soff = nullptr;
     fast_status st;
