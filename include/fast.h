@@ -372,7 +372,7 @@ fast_status fast_server_inject_failure(fast_server *srv, uint64_t req_id);
  *
  * The caller passes the input and both outputs (n uint32 each, device
  * memory, not overlapping).  The scratch (one ping-pong pair of keys and ids
- * plus digit counts, about 8.4 MB) is a fixed array inside the library: every
+ * plus digit counts, about 8.9 MB) is a fixed array inside the library: every
  * GPU that loads the library holds it until the process exits.
  *   - n <= 1048576 (2^20); larger n returns FAST_EINVAL and does nothing.
  *   - The first call on a device looks up the array's device address (once
