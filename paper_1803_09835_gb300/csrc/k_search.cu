@@ -622,21 +622,23 @@ __device__ __forceinline__ PT pack_entry(uint32_t local, uint32_t j, uint32_t nb
 constexpr uint32_t kLabDrop = 0xFFFFFFFEu;  // window label of a dropped (or absent) entry
 
 struct PairWin {
-    uint32_t id, lab, heads;
+    uint32_t id, lab, heads, key;
 };
 
+// kprev0: the key at position 32 T - 1 (the previous tile's last), unused for T = 0.
 __device__ __forceinline__ PairWin pair_tile(const EnumArgs &a, const uint32_t *__restrict__ K,
                                              const uint32_t *__restrict__ S, const uint32_t *__restrict__ FS,
-                                             uint32_t *__restrict__ FO, uint64_t T, bool own) {
+                                             uint32_t *__restrict__ FO, uint64_t T, bool own, uint32_t kprev0) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t x = T * 32 + lane, N = a.N;
     const bool valid = x < N;
     const uint32_t key = valid ? __ldcs(K + x) : 0u;
     uint32_t kprev = __shfl_up_sync(~0u, key, 1);
-    if (lane == 0 && valid && x > 0) kprev = K[x - 1];
+    if (lane == 0) kprev = kprev0;
     bool head = !valid || x == 0 || key != kprev;
     if (a.st.nst > 1 && valid && !head) head = a.st.soff[station_of(a.st, x)] == x;
     PairWin w;
+    w.key = key;
     w.heads = __ballot_sync(~0u, head);
     w.lab = kLabDrop;
     if (FS || FO) {  // only flagged entries (dropped or in a dense group) need the random lookups
@@ -702,11 +704,16 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
     const uint64_t T1 = min(T0 + tiles_per_warp, ntiles);
     __shared__ PairSmem ps[8];
     PairSmem &W = ps[threadIdx.x / 32];
-    uint32_t hp = T0 ? pair_tile(a, K, S, FS, FO, T0 - 1, false).heads : ~0u;
-    PairWin c = pair_tile(a, K, S, FS, FO, T0, true);
+    uint32_t hp = ~0u, kp0 = 0;
+    if (T0) {
+        const PairWin pw = pair_tile(a, K, S, FS, FO, T0 - 1, false, T0 > 1 ? K[(T0 - 1) * 32 - 1] : 0u);
+        hp = pw.heads;
+        kp0 = __shfl_sync(~0u, pw.key, 31);
+    }
+    PairWin c = pair_tile(a, K, S, FS, FO, T0, true, kp0);
     unsigned long long emitted = 0;  // counting pass: pairs of this lane's entries
     for (uint64_t T = T0; T < T1; T++) {
-        const PairWin n = pair_tile(a, K, S, FS, FO, T + 1, T + 1 < T1);
+        const PairWin n = pair_tile(a, K, S, FS, FO, T + 1, T + 1 < T1, __shfl_sync(~0u, c.key, 31));
         // bucket of position L: first position s0 (window coordinates, previous
         // tile = 0..31) and end e (coordinates of current + next = 0..63)
         const uint64_t hpc = (uint64_t)c.heads << 32 | hp;
@@ -1606,18 +1613,23 @@ __global__ void k_add_u32(const uint32_t *__restrict__ a, const uint32_t *__rest
 // 32-entry tiles with the head bitmasks of the current and next tile: a
 // bucket starting at lane L ends at the next head; with no head in the two
 // tiles it is big and its end is found by galloping.
-__device__ __forceinline__ uint32_t head_bits(const uint32_t *__restrict__ K, const Stations &st, uint64_t N,
-                                              uint64_t T) {
+// Head bitmask of tile T from its keys (one per lane) and the key before the
+// tile (kprev0, position 32 T - 1; unused for T = 0).
+__device__ __forceinline__ uint32_t heads_of(uint32_t key, uint32_t kprev0, const Stations &st, uint64_t N,
+                                             uint64_t T) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t x = T * 32 + lane;
     const bool valid = x < N;
-    const uint32_t key = valid ? __ldcs(K + x) : 0u;
     uint32_t kprev = __shfl_up_sync(~0u, key, 1);
-    if (lane == 0 && valid && x > 0) kprev = K[x - 1];
+    if (lane == 0) kprev = kprev0;
     bool head = !valid || x == 0 || key != kprev;
     if (st.nst > 1 && valid && !head) head = st.soff[station_of(st, x)] == x;
     return __ballot_sync(~0u, head);
 }
+
+// Tiles are read in batches of kFB + 1 (the last one is the next batch's
+// first), so a warp has kFB loads in flight instead of one.
+constexpr int kFB = 8;
 
 __global__ void __launch_bounds__(256) k_find_big(EnumArgs a, uint32_t tiles_per_warp, uint4 *__restrict__ big,
                                                   unsigned long long *__restrict__ nbig, uint64_t big_cap,
@@ -1629,41 +1641,58 @@ __global__ void __launch_bounds__(256) k_find_big(EnumArgs a, uint32_t tiles_per
     if (T0 >= ntiles) return;  // warp-uniform
     const uint64_t T1 = min(T0 + tiles_per_warp, ntiles);
     unsigned long long pairs = 0;
-    uint32_t hc = head_bits(k, a.st, N, T0);
-    for (uint64_t T = T0; T < T1; T++) {
-        const uint32_t hn = head_bits(k, a.st, N, T + 1);
-        const uint64_t x = T * 32 + lane;
-        if (x < N && (hc >> lane & 1)) {
-            const uint64_t above = ((uint64_t)hn << 32 | hc) & ~((2ull << lane) - 1);
-            const uint32_t e = above ? (uint32_t)__ffsll((long long)above) - 1 : 64u;
-            const uint32_t size = e - lane;
-            if (e < 64 && size <= kSmall) {
-                pairs += (unsigned long long)size * (size - 1) / 2;
-            } else {
-                uint64_t hi = x + size;  // exact when the end lies in the window
-                if (e == 64) {  // gallop from the last position of the window, which is in the bucket
-                    const uint64_t s1 = a.st.soff[station_of(a.st, x) + 1];
-                    const uint32_t key = k[x];
-                    uint64_t lo = x + size - 1, step = 1;
-                    for (;;) {
-                        hi = lo + step;
-                        if (hi >= s1 || k[hi] != key) break;
-                        lo = hi;
-                        step <<= 1;
+    uint32_t carry = T0 ? k[T0 * 32 - 1] : 0u;  // the key before the batch's first tile
+    for (uint64_t B = T0; B < T1; B += kFB) {
+        uint32_t kk[kFB + 1], h[kFB + 1];
+#pragma unroll
+        for (int u = 0; u <= kFB; u++) {
+            const uint64_t x = (B + u) * 32 + lane;
+            kk[u] = x < N ? __ldcs(k + x) : 0u;
+        }
+        uint32_t kp = carry;
+#pragma unroll
+        for (int u = 0; u <= kFB; u++) {
+            h[u] = heads_of(kk[u], kp, a.st, N, B + u);
+            kp = __shfl_sync(~0u, kk[u], 31);
+        }
+        carry = __shfl_sync(~0u, kk[kFB - 1], 31);
+#pragma unroll
+        for (int u = 0; u < kFB; u++) {
+            const uint64_t T = B + u;
+            if (T >= T1) break;  // warp-uniform
+            const uint32_t hc = h[u], hn = h[u + 1];
+            const uint64_t x = T * 32 + lane;
+            if (x < N && (hc >> lane & 1)) {
+                const uint64_t above = ((uint64_t)hn << 32 | hc) & ~((2ull << lane) - 1);
+                const uint32_t e = above ? (uint32_t)__ffsll((long long)above) - 1 : 64u;
+                const uint32_t size = e - lane;
+                if (e < 64 && size <= kSmall) {
+                    pairs += (unsigned long long)size * (size - 1) / 2;
+                } else {
+                    uint64_t hi = x + size;  // exact when the end lies in the window
+                    if (e == 64) {  // gallop from the last position of the window, which is in the bucket
+                        const uint64_t s1 = a.st.soff[station_of(a.st, x) + 1];
+                        const uint32_t key = k[x];
+                        uint64_t lo = x + size - 1, step = 1;
+                        for (;;) {
+                            hi = lo + step;
+                            if (hi >= s1 || k[hi] != key) break;
+                            lo = hi;
+                            step <<= 1;
+                        }
+                        if (hi > s1) hi = s1;
+                        while (hi - lo > 1) {
+                            const uint64_t mid = lo + (hi - lo) / 2;
+                            if (k[mid] == key) lo = mid;
+                            else hi = mid;
+                        }
                     }
-                    if (hi > s1) hi = s1;
-                    while (hi - lo > 1) {
-                        const uint64_t mid = lo + (hi - lo) / 2;
-                        if (k[mid] == key) lo = mid;
-                        else hi = mid;
-                    }
+                    const unsigned long long slot = atomicAdd(nbig, 1ull);
+                    if (slot < big_cap) big[slot] = make_uint4(t, (uint32_t)x, (uint32_t)hi, 0);
+                    else set_err(err, ERR_OVERFLOW);
                 }
-                const unsigned long long slot = atomicAdd(nbig, 1ull);
-                if (slot < big_cap) big[slot] = make_uint4(t, (uint32_t)x, (uint32_t)hi, 0);
-                else set_err(err, ERR_OVERFLOW);
             }
         }
-        hc = hn;
     }
     for (int o = 16; o; o >>= 1) pairs += __shfl_down_sync(~0u, pairs, o);
     if (lane == 0 && pairs) atomicAdd(small_pairs, pairs);

@@ -103,6 +103,8 @@ DETECT_CASES = [
     ("c1", 60_000, dict(), dict(vote_map=1)),                 # global vote map instead of per-row votes
     ("c1", 60_000, dict(query_part=4), dict(vote_map=1, large_min=10**9)),
     ("c1", 30_000, dict(occ_num=0), dict(large_min=10**9)),   # no dense groups: long rows per fingerprint
+    ("c4", 50_000, dict(), dict()),                           # C4 shape: 30/60/90/3600 s sources, 200-repeat templates
+    ("c4", 50_000, dict(query_part=5), dict(large_min=32)),   # C4 shape, five row partitions, dense groups
 ]
 
 
