@@ -547,28 +547,6 @@ __global__ void k_unpack(const unsigned long long *__restrict__ in, uint64_t M, 
 
 __device__ __forceinline__ uint32_t row_hash(uint32_t j) { return (uint32_t)(mix64(j) >> 32); }
 
-// Hash insert of one occurrence of j (key j+1, 0 = empty); counts are bytes
-// packed four to a word (votes never exceed b <= 255).
-__device__ __forceinline__ bool gadd8(uint32_t *K, uint32_t *C32, uint32_t slots, uint32_t j) {
-    const uint32_t want = j + 1;
-    uint32_t h = row_hash(j) & (slots - 1);
-    for (uint32_t probe = 0; probe < slots; probe++) {
-        uint32_t kk = K[h];
-        if (kk == 0) {
-            kk = atomicCAS(K + h, 0u, want);
-            if (kk == 0) kk = want;
-        }
-        if (kk == want) {
-            atomicAdd(C32 + (h >> 2), 1u << (8 * (h & 3)));
-            return true;
-        }
-        h = (h + 1) & (slots - 1);
-    }
-    return false;
-}
-
-__device__ __forceinline__ uint32_t cnt8(const uint32_t *C32, uint32_t h) { return (C32[h >> 2] >> (8 * (h & 3))) & 0xFF; }
-
 // Kept entries of one row, written in j order: each kept entry's rank is the
 // number of kept entries with a smaller j (j is unique within a row).
 __device__ __forceinline__ void row_write_sorted(const uint32_t *kj, const uint32_t *kv, uint32_t nk, uint32_t lane,
@@ -579,17 +557,6 @@ __device__ __forceinline__ void row_write_sorted(const uint32_t *kj, const uint3
         for (uint32_t y = 0; y < nk; y++) rank += kj[y] < jx;
         sp_j[base + rank] = jx;
         sp_v[base + rank] = (uint8_t)kv[x];
-    }
-}
-
-__device__ __forceinline__ void row_write_sorted8(const uint32_t *kj, const uint8_t *kv, uint32_t nk, uint32_t lane,
-                                                  uint32_t nlanes, uint32_t *sp_j, uint8_t *sp_v, uint64_t base) {
-    for (uint32_t x = lane; x < nk; x += nlanes) {
-        const uint32_t jx = kj[x];
-        uint32_t rank = 0;
-        for (uint32_t y = 0; y < nk; y++) rank += kj[y] < jx;
-        sp_j[base + rank] = jx;
-        sp_v[base + rank] = kv[x];
     }
 }
 
@@ -1404,14 +1371,19 @@ __global__ void __launch_bounds__(512) k_long_vote(VoteArgs A, const PT *__restr
 
 // Dense groups, count pass for the row layout: detections per row, one
 // atomic per (row, tile).
+// Tiles of groups whose cluster masks overflowed (gover[tile_grp[ti]] != 0)
+// only; the others are voted by k_dense_rowcount_mask.
 __global__ void __launch_bounds__(256) k_dense_rowcount(const DenseTile *__restrict__ tiles, uint64_t ntiles,
                                                         const uint32_t *__restrict__ GT, const uint32_t *__restrict__ ids,
                                                         uint64_t nm, uint32_t nb, uint32_t v, uint32_t excl,
-                                                        uint32_t *__restrict__ dense_cnt, uchar4 *__restrict__ tv) {
+                                                        uint32_t *__restrict__ dense_cnt, uchar4 *__restrict__ tv,
+                                                        const uint32_t *__restrict__ tile_grp,
+                                                        const uint32_t *__restrict__ gover) {
     extern __shared__ uint32_t sd[];
     uint32_t *sA = sd, *sB = sd + (size_t)nb * kDT;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     for (uint64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        if (!gover[tile_grp[ti]]) continue;  // block-uniform
         const DenseTile T = tiles[ti];
         const uint32_t a0 = T.g0 + T.ta * kDT, b0 = T.g0 + T.tb * kDT;
         const uint32_t na = min((uint32_t)kDT, T.n - T.ta * kDT), nbb = min((uint32_t)kDT, T.n - T.tb * kDT);
@@ -1446,6 +1418,168 @@ __global__ void __launch_bounds__(256) k_dense_rowcount(const DenseTile *__restr
             for (int w = 0; w < 4; w++) {
                 const uint32_t gb = T.tb * kDT + tx * 4 + w;
                 if (ga < T.n && gb < T.n && ga < gb && acc[u][w] >= v && ids[T.g0 + gb] - i > excl) ++c;
+            }
+#pragma unroll
+            for (int d = 8; d; d >>= 1) c += __shfl_down_sync(~0u, c, d, 16);
+            if (tx == 0 && c) atomicAdd(dense_cnt + i, c);
+        }
+    }
+}
+
+// ---- dense votes from cluster masks
+//
+// Inside one dense group, the members sharing a key in table t form a
+// cluster; votes(i, j) is the number of tables in which i and j fall in the
+// same cluster.  Clusters of at least kClT members get one bit column each
+// (at most kClW * 32 per group): the tables where i and j share such a
+// cluster number popc(mask_i & mask_j).  The pairs of the smaller clusters
+// are added one by one into the tile votes.  Both parts are exact, so their
+// sum is the vote; a group with too many large clusters is voted by direct
+// key comparison (k_dense_rowcount) instead.
+constexpr uint32_t kClT = 64;
+constexpr uint32_t kClW = 32;
+
+struct DenseGroup {
+    uint32_t g0, n, t0, nt;  // first member, members, first tile, tiles per side
+};
+
+// comp[t * nm + k] = t : 8 | key : 32 | k : 24 (member k of table t)
+__global__ void k_clu_comp(const uint32_t *__restrict__ GT, uint64_t nm, uint32_t nb,
+                           unsigned long long *__restrict__ comp) {
+    const uint64_t n = (uint64_t)nb * nm;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (uint64_t)gridDim.x * blockDim.x)
+        comp[e] = (unsigned long long)(e / nm) << 56 | (unsigned long long)GT[e] << 24 | (e % nm);
+}
+
+// flag[e] = 1 where a cluster starts in the sorted list: a new (table, key),
+// or a new group within the same (table, key).
+__global__ void k_clu_mark(const unsigned long long *__restrict__ comp, uint64_t n, const uint32_t *__restrict__ mg,
+                           uint32_t *__restrict__ flag) {
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned long long x = comp[e];
+        uint32_t f = 1;
+        if (e) {
+            const unsigned long long y = comp[e - 1];
+            f = (x >> 24) != (y >> 24) || mg[x & 0xFFFFFF] != mg[y & 0xFFFFFF];
+        }
+        flag[e] = f;
+    }
+}
+
+__global__ void k_clu_starts(const uint32_t *__restrict__ flag, const uint64_t *__restrict__ cid, uint64_t n,
+                             const uint64_t *__restrict__ ncl, uint64_t *__restrict__ cst) {
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (uint64_t)gridDim.x * blockDim.x) {
+        if (flag[e]) cst[cid[e]] = e;
+        if (e == 0) cst[*ncl] = n;
+    }
+}
+
+// One warp per cluster: a column for a large one, its pairs for a small one.
+// MB is word-major: MB[w * nm + k].  tv32 holds the tile votes as bytes
+// (each below 256: at most b tables).
+__global__ void __launch_bounds__(256) k_clu_apply(const unsigned long long *__restrict__ comp,
+                                                   const uint64_t *__restrict__ cst, const uint64_t *__restrict__ ncl,
+                                                   const uint32_t *__restrict__ mg, const DenseGroup *__restrict__ G,
+                                                   uint64_t nm, uint32_t *__restrict__ gcol,
+                                                   uint32_t *__restrict__ gover, uint32_t *__restrict__ MB,
+                                                   uint32_t *__restrict__ tv32) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t nc = *ncl;
+    for (uint64_t c = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; c < nc;
+         c += (uint64_t)gridDim.x * blockDim.x / 32) {
+        const uint64_t e0 = cst[c], e1 = cst[c + 1];
+        const uint32_t sz = (uint32_t)(e1 - e0);
+        if (sz < 2) continue;  // warp-uniform
+        const uint32_t g = mg[comp[e0] & 0xFFFFFF];
+        if (sz >= kClT) {
+            uint32_t col = 0;
+            if (lane == 0) col = atomicAdd(gcol + g, 1u);
+            col = __shfl_sync(~0u, col, 0);
+            if (col >= kClW * 32) {
+                if (lane == 0) atomicOr(gover + g, 1u);
+                continue;
+            }
+            for (uint64_t x = e0 + lane; x < e1; x += 32)
+                atomicOr(MB + (uint64_t)(col / 32) * nm + (comp[x] & 0xFFFFFF), 1u << (col & 31));
+        } else {
+            const DenseGroup D = G[g];
+            const uint32_t np = sz * (sz - 1) / 2;
+            for (uint32_t q = lane; q < np; q += 32) {
+                uint32_t a = 0, rem = q;  // pair q = (a, b), a < b, in row-major order of the triangle
+                while (rem >= sz - 1 - a) {
+                    rem -= sz - 1 - a;
+                    a++;
+                }
+                const uint32_t bb = a + 1 + rem;
+                const uint32_t la = (uint32_t)(comp[e0 + a] & 0xFFFFFF) - D.g0;
+                const uint32_t lb = (uint32_t)(comp[e0 + bb] & 0xFFFFFF) - D.g0;
+                const uint32_t ta = la / kDT, tb = lb / kDT;
+                const uint64_t tn = D.t0 + (uint64_t)ta * D.nt - (uint64_t)ta * (ta - 1) / 2 + (tb - ta);
+                const uint64_t byte = tn * (kDT * kDT) + (la % kDT) * kDT + (lb % kDT);
+                atomicAdd(tv32 + (byte >> 2), 1u << (8 * (byte & 3)));
+            }
+        }
+    }
+}
+
+// Dense groups voted from the cluster masks: the small clusters' counts are
+// already in the tile; the large ones are added as popc(mask_a & mask_b).
+// Then, as k_dense_rowcount, the per-row detection counts.
+__global__ void __launch_bounds__(256) k_dense_rowcount_mask(const DenseTile *__restrict__ tiles, uint64_t ntiles,
+                                                             const uint32_t *__restrict__ tile_grp,
+                                                             const uint32_t *__restrict__ gcol,
+                                                             const uint32_t *__restrict__ gover,
+                                                             const uint32_t *__restrict__ MB, uint64_t nm,
+                                                             const uint32_t *__restrict__ ids, uint32_t v,
+                                                             uint32_t excl, uint32_t *__restrict__ dense_cnt,
+                                                             uchar4 *__restrict__ tv) {
+    __shared__ __align__(16) uint32_t sA[kClW][kDT], sB[kClW][kDT];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    for (uint64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const uint32_t g = tile_grp[ti];
+        if (gover[g]) continue;  // block-uniform
+        const uint32_t nw = (min(gcol[g], kClW * 32) + 31) / 32;
+        const DenseTile T = tiles[ti];
+        const uint32_t a0 = T.g0 + T.ta * kDT, b0 = T.g0 + T.tb * kDT;
+        const uint32_t na = min((uint32_t)kDT, T.n - T.ta * kDT), nbb = min((uint32_t)kDT, T.n - T.tb * kDT);
+        __syncthreads();
+        for (uint32_t x = threadIdx.x; x < nw * kDT; x += blockDim.x) {
+            const uint32_t w = x / kDT, c = x % kDT;
+            sA[w][c] = c < na ? MB[(uint64_t)w * nm + a0 + c] : 0u;
+            sB[w][c] = c < nbb ? MB[(uint64_t)w * nm + b0 + c] : 0u;
+        }
+        __syncthreads();
+        uint32_t acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uchar4 q = tv[ti * (kDT * kDT / 4) + (ty * 4 + u) * (kDT / 4) + tx];
+            acc[u][0] = q.x;
+            acc[u][1] = q.y;
+            acc[u][2] = q.z;
+            acc[u][3] = q.w;
+        }
+        for (uint32_t w = 0; w < nw; w++) {
+            const uint4 av = *reinterpret_cast<const uint4 *>(&sA[w][ty * 4]);
+            const uint4 bv = *reinterpret_cast<const uint4 *>(&sB[w][tx * 4]);
+            const uint32_t A4[4] = {av.x, av.y, av.z, av.w}, B4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+#pragma unroll
+                for (int q = 0; q < 4; q++) acc[u][q] += __popc(A4[u] & B4[q]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            tv[ti * (kDT * kDT / 4) + (ty * 4 + u) * (kDT / 4) + tx] =
+                make_uchar4((uint8_t)acc[u][0], (uint8_t)acc[u][1], (uint8_t)acc[u][2], (uint8_t)acc[u][3]);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t ga = T.ta * kDT + ty * 4 + u;
+            uint32_t c = 0;
+            const uint32_t i = ga < T.n ? ids[T.g0 + ga] : 0;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const uint32_t gb = T.tb * kDT + tx * 4 + q;
+                if (ga < T.n && gb < T.n && ga < gb && acc[u][q] >= v && ids[T.g0 + gb] - i > excl) ++c;
             }
 #pragma unroll
             for (int d = 8; d; d >>= 1) c += __shfl_down_sync(~0u, c, d, 16);
@@ -2247,6 +2381,8 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
         if ((st = alloc(&GT, (size_t)nm * nb)) || (st = alloc(&ids, nm))) return fail(st);
         k_gather_keys<<<std::max(1u, std::min<unsigned>(ceil_div(nm, 128), c->num_sms * 8)), 128, 0, s>>>(
             reinterpret_cast<unsigned long long *>(sorted), nm, d_sig, N, nb, GT, ids), FAST_LAUNCHED(c);
+        std::vector<DenseGroup> hgrp;
+        std::vector<uint32_t> htg, hmg(nm);  // group of each tile, of each member
         uint64_t g0 = 0;
         while (g0 < nm) {
             uint64_t g1 = g0 + 1;
@@ -2256,9 +2392,14 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
             dense_pairs += (uint64_t)n * (n - 1) / 2;
             const uint32_t gt0 = (uint32_t)tiles.size();  // the group's first tile
             const uint32_t nt = (n + kDT - 1) / kDT;
+            hgrp.push_back({(uint32_t)g0, n, gt0, nt});
+            for (uint64_t k = g0; k < g1; k++) hmg[k] = (uint32_t)hgrp.size() - 1;
             for (uint32_t a = 0; a < nt; a++) {
                 strips.push_back({(uint32_t)g0, n, a, gt0});
-                for (uint32_t b = a; b < nt; b++) tiles.push_back({(uint32_t)g0, n, a, b});
+                for (uint32_t b = a; b < nt; b++) {
+                    tiles.push_back({(uint32_t)g0, n, a, b});
+                    htg.push_back((uint32_t)hgrp.size() - 1);
+                }
             }
             g0 = g1;
         }
@@ -2270,10 +2411,50 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
         cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(DenseTile), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_strips, strips.data(), strips.size() * sizeof(DenseStrip), cudaMemcpyHostToDevice, s);
         if ((st = alloc(&tvotes, tiles.size() * (kDT * kDT / 4)))) return fail(st);
+        cudaMemsetAsync(tvotes, 0, tiles.size() * (size_t)(kDT * kDT), s);
+        // cluster masks and the small clusters' pair votes
+        uint32_t *d_tg = nullptr, *d_mg = nullptr, *gcol = nullptr, *gover = nullptr, *MB = nullptr;
+        DenseGroup *d_grp = nullptr;
+        if ((st = alloc(&d_tg, tiles.size())) || (st = alloc(&d_mg, nm)) || (st = alloc(&d_grp, ngroups)) ||
+            (st = alloc(&gcol, ngroups)) || (st = alloc(&gover, ngroups)))
+            return fail(st);
+        cudaMemcpyAsync(d_tg, htg.data(), htg.size() * 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_mg, hmg.data(), nm * 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_grp, hgrp.data(), ngroups * sizeof(DenseGroup), cudaMemcpyHostToDevice, s);
+        cudaMemsetAsync(gcol, 0, ngroups * 4, s);
+        const uint64_t ne = (uint64_t)nb * nm;
+        if (nm < (1u << 24) && nb <= 256) {
+            cudaMemsetAsync(gover, 0, ngroups * 4, s);
+            unsigned long long *ca = nullptr, *cb = nullptr;
+            uint32_t *flag = nullptr;
+            uint64_t *cid = nullptr, *cst = nullptr;
+            if ((st = alloc(&MB, (size_t)kClW * nm)) || (st = alloc(&ca, ne)) || (st = alloc(&cb, ne)) ||
+                (st = alloc(&flag, ne)) || (st = alloc(&cid, ne + 1)) || (st = alloc(&cst, ne + 1)))
+                return fail(st);
+            cudaMemsetAsync(MB, 0, (size_t)kClW * nm * 4, s);
+            const unsigned eg = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(ne, 256), c->num_sms * 8));
+            k_clu_comp<<<eg, 256, 0, s>>>(GT, nm, nb, ca), FAST_LAUNCHED(c);
+            uint64_t *srt = nullptr;  // by (table, key), members ascending within (stable)
+            if ((st = sort_u64(c, ne, reinterpret_cast<uint64_t *>(ca), reinterpret_cast<uint64_t *>(cb), 24, 64,
+                               &srt, s)))
+                return fail(st);
+            const unsigned long long *sc = reinterpret_cast<const unsigned long long *>(srt);
+            k_clu_mark<<<eg, 256, 0, s>>>(sc, ne, d_mg, flag), FAST_LAUNCHED(c);
+            if ((st = scan_excl(c, flag, cid, ne, 1, cid + ne, s))) return fail(st);
+            k_clu_starts<<<eg, 256, 0, s>>>(flag, cid, ne, cid + ne, cst), FAST_LAUNCHED(c);
+            k_clu_apply<<<c->num_sms * 8, 256, 0, s>>>(sc, cst, cid + ne, d_mg, d_grp, nm, gcol, gover, MB,
+                                                       reinterpret_cast<uint32_t *>(tvotes)), FAST_LAUNCHED(c);
+        } else {
+            cudaMemsetAsync(gover, 0x01, ngroups * 4, s);  // every group by direct comparison
+        }
         cudaFuncSetAttribute(k_dense_rowcount, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
         const unsigned dg = (unsigned)std::min<uint64_t>(tiles.size(), (uint64_t)c->num_sms * 4);
         k_dense_rowcount<<<dg, 256, dsm, s>>>(d_tiles, tiles.size(), GT, ids, nm, nb, p.v, p.excl, dense_cnt,
-                                              tvotes), FAST_LAUNCHED(c);
+                                              tvotes, d_tg, gover), FAST_LAUNCHED(c);
+        if (MB)
+            k_dense_rowcount_mask<<<(unsigned)std::min<uint64_t>(tiles.size(), (uint64_t)c->num_sms * 8), 256, 0, s>>>(
+                d_tiles, tiles.size(), d_tg, gcol, gover, MB, nm, ids, p.v, p.excl, dense_cnt, tvotes),
+                FAST_LAUNCHED(c);
     }
     stage_mark(c, 5, s);
 
