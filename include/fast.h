@@ -270,6 +270,14 @@ fast_status fast_get_stats(const fast_ctx *ctx, fast_stats *out);
  *   "vote_map"   1 = sum sparse votes in one global open-addressing map of
  *                packed (i, j) -> votes and order the list by a radix sort;
  *                0 = count them row by row (default)
+ *   "single_pass" 1 = write the row groups' pairs in one pass over the tables
+ *                into fixed-size group regions (with an overflow list), then
+ *                compact them, when one row partition is used and the regions
+ *                fit the budget (default); 0 = count the pairs in a first
+ *                pass and write them at exact offsets in a second
+ *   "group_slots" region slots per row group of the single pass, 0 (= about
+ *                twice the expected pairs per group) or in [1, 65536]; pairs
+ *                past them go through the overflow list
  */
 fast_status fast_set_option(fast_ctx *ctx, const char *name, double value);
 

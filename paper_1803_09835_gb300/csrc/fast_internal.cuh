@@ -164,6 +164,8 @@ struct fast_ctx {
     uint32_t group_pairs = 0;   // expected sparse pairs per row group of the vote (0 = 1024)
     float map_load = 0.5f;      // vote-map load factor target
     bool vote_map = false;      // sum sparse votes in one global hash map instead of per row
+    bool single_pass = true;    // write the sparse pairs in one pass (fixed group regions) when they fit
+    uint32_t group_slots = 0;   // region slots per row group of the single pass (0 = about twice the expected)
     // instrumentation
     fast_stats stats{};
     cudaEvent_t ev[16] = {};
@@ -284,7 +286,7 @@ fast_status history_groups(fast_ctx *c, const fast_tables *tb, const uint32_t *d
 uint32_t large_min_for(const fast_ctx *c, uint64_t N);  // the dense-group threshold (option or automatic)
 struct Scal {  // device scalar slots (ctx->d_scal)
     enum { NBIG, NLARGE, NMEDIUM, NHEAVY, NDROP, NMEMB, CUR_DENSE, CUR_SPARSE, CHANGED, NLONG, NMERGE, NMERGE_TOT,
-           NCAND, NMID, SMALLPAIRS, NSMALLEMIT, NSLOW, PART0 };
+           NCAND, NMID, SMALLPAIRS, NSMALLEMIT, NSLOW, NOVF, PART0 };
 };
 void history_groups_free(HistGroups *g);
 

@@ -608,14 +608,14 @@ __device__ __forceinline__ PairWin pair_tile(const EnumArgs &a, const uint32_t *
     w.key = key;
     w.heads = __ballot_sync(~0u, head);
     w.lab = kLabDrop;
-    if (FS || FO) {  // only flagged entries (dropped or in a dense group) need the random lookups
+    if (FS || a.fbits) {  // only flagged entries (dropped or in a dense group) need the random lookups
         uint32_t raw = 0;
         if (FS) {
             raw = valid ? __ldcs(FS + x) : 0u;
-        } else if (valid) {  // counting pass: flag the id from the bitmap and keep the flagged copy
+        } else if (valid) {  // flag the id from the bitmap (the counting pass keeps the flagged copy)
             const uint32_t id = __ldcs(S + x);
             raw = id | (__ldg(a.fbits + (id >> 5)) >> (id & 31)) << 31;
-            if (own) FO[x] = raw;
+            if (own && FO) FO[x] = raw;
         }
         w.id = raw & 0x7FFFFFFFu;
         if (valid) w.lab = !(raw >> 31) ? kNone : a.drop[w.id] ? kLabDrop : __ldg(a.label + w.id);
@@ -649,6 +649,23 @@ struct GroupRange {
     __device__ __forceinline__ bool has(uint64_t g) const { return g >= g_lo && g < g_hi; }
 };
 
+// Single-pass emission (MODE 2): every row group owns `cap` slots of `region`;
+// entries past them go to an overflow list of (group, entry), placed after
+// the region's entries when the groups are compacted to exact offsets.
+struct RegionSink {
+    uint32_t *region;
+    uint32_t cap;
+    unsigned long long *ovf, ovf_cap, *novf;
+    __device__ __forceinline__ void put(uint64_t g, uint64_t slot, uint32_t e) const {
+        if (slot < cap) {
+            region[g * cap + slot] = e;
+        } else {
+            const unsigned long long q = atomicAdd(novf, 1ull);
+            if (q < ovf_cap) ovf[q] = (unsigned long long)g << 32 | e;
+        }
+    }
+};
+
 struct PairSmem {  // one warp's tile window and its pair bookkeeping
     uint32_t id[64], lab[64], pre[32], cnt[32];
     uint64_t base[32];
@@ -658,7 +675,8 @@ template <int MODE, typename PT>
 __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, uint32_t nbits, uint32_t tiles_per_warp,
                                                    uint32_t *__restrict__ gcnt, const uint64_t *__restrict__ goff,
                                                    uint32_t *__restrict__ gcur, PT *__restrict__ ent,
-                                                   unsigned long long *__restrict__ n_emit, GroupRange gr) {
+                                                   unsigned long long *__restrict__ n_emit, GroupRange gr,
+                                                   RegionSink rs = RegionSink{}) {
     const uint32_t t = blockIdx.y, lane = threadIdx.x & 31;
     const uint64_t N = a.N, ntiles = (N + 31) / 32;
     const uint32_t *K = a.skey + (uint64_t)t * N;
@@ -720,11 +738,11 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
             }
             __syncwarp();
             const uint32_t cnt = W.cnt[lane], g = c.id >> gshift;
+            if (MODE != 1) emitted += cnt;
             if (MODE == 0) {
-                emitted += cnt;
                 if (cnt) atomicAdd(gcnt + g, cnt);
             } else if (__any_sync(~0u, cnt != 0)) {
-                W.base[lane] = cnt ? goff[g] - gr.ebase + atomicAdd(gcur + g, cnt) : 0;
+                W.base[lane] = !cnt ? 0 : MODE == 2 ? atomicAdd(gcur + g, cnt) : goff[g] - gr.ebase + atomicAdd(gcur + g, cnt);
                 W.cnt[lane] = 0;
                 __syncwarp();
                 for (uint32_t k = lane; k < P; k += 32) {
@@ -734,8 +752,11 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
                         if (W.pre[L + step] <= k) L += step;
                     const uint32_t y = L + 1 + (k - W.pre[L]);
                     const uint32_t i = W.id[L], li = W.lab[L], j = W.id[y], lj = W.lab[y];
-                    if (lj != kLabDrop && j - i > a.excl && (li == kNone || li != lj) && gr.has(i >> gshift))
-                        ent[W.base[L] + atomicAdd(&W.cnt[L], 1u)] = pack_entry<PT>(i & lmask, j, nbits);
+                    if (lj != kLabDrop && j - i > a.excl && (li == kNone || li != lj) && gr.has(i >> gshift)) {
+                        const uint64_t slot = W.base[L] + atomicAdd(&W.cnt[L], 1u);
+                        if (MODE == 2) rs.put(i >> gshift, slot, (uint32_t)pack_entry<PT>(i & lmask, j, nbits));
+                        else ent[slot] = pack_entry<PT>(i & lmask, j, nbits);
+                    }
                 }
             }
             __syncwarp();
@@ -743,7 +764,7 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
         hp = c.heads;
         c = n;
     }
-    if (MODE == 0 && n_emit) {
+    if (MODE != 1 && n_emit) {
         for (int o = 16; o; o >>= 1) emitted += __shfl_down_sync(~0u, emitted, o);
         if (lane == 0 && emitted) atomicAdd(n_emit, emitted);
     }
@@ -763,7 +784,8 @@ __global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, const uint4 *__r
                                                     const unsigned long long *__restrict__ nmedium, uint32_t gshift,
                                                     uint32_t nbits, uint32_t *__restrict__ gcnt,
                                                     const uint64_t *__restrict__ goff, uint32_t *__restrict__ gcur,
-                                                    PT *__restrict__ ent, GroupRange gr) {
+                                                    PT *__restrict__ ent, GroupRange gr,
+                                                    RegionSink rs = RegionSink{}) {
     __shared__ uint32_t s_id[kMedCap], s_lab[kMedCap];
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t s_next, s_mixed;
@@ -786,10 +808,13 @@ __global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, const uint4 *__r
                 if (MODE == 0) {
                     atomicAdd(gcnt + g, c);
                 } else {
-                    uint64_t o = goff[g] - gr.ebase + atomicAdd(gcur + g, c);
+                    uint64_t o = MODE == 2 ? atomicAdd(gcur + g, c) : goff[g] - gr.ebase + atomicAdd(gcur + g, c);
                     for (uint32_t y = x + 1; y < e.z; y++) {
                         const uint32_t j = s[y];
-                        if (!a.drop[j] && pair_live(a, i, j)) ent[o++] = pack_entry<PT>(i & lmask, j, nbits);
+                        if (!a.drop[j] && pair_live(a, i, j)) {
+                            if (MODE == 2) rs.put(g, o++, (uint32_t)pack_entry<PT>(i & lmask, j, nbits));
+                            else ent[o++] = pack_entry<PT>(i & lmask, j, nbits);
+                        }
                     }
                 }
             }
@@ -841,14 +866,18 @@ __global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, const uint4 *__r
                     if (lane == 0) atomicAdd(gcnt + g, c);
                 } else {
                     uint64_t o = 0;
-                    if (lane == 0) o = goff[g] - gr.ebase + atomicAdd(gcur + g, c);
+                    if (lane == 0) o = MODE == 2 ? atomicAdd(gcur + g, c) : goff[g] - gr.ebase + atomicAdd(gcur + g, c);
                     o = __shfl_sync(~0u, o, 0);
                     for (uint32_t y0 = x + 1; y0 < nl; y0 += 32) {
                         const uint32_t y = y0 + lane;
                         const uint32_t j = y < nl ? s_id[y] : 0u;
                         const bool keep = y < nl && j - i > a.excl && (li == kNone || li != s_lab[y]);
                         const uint32_t m = __ballot_sync(~0u, keep);
-                        if (keep) ent[o + __popc(m & ((1u << lane) - 1))] = pack_entry<PT>(i & lmask, j, nbits);
+                        if (keep) {
+                            const uint64_t slot = o + __popc(m & ((1u << lane) - 1));
+                            if (MODE == 2) rs.put(g, slot, (uint32_t)pack_entry<PT>(i & lmask, j, nbits));
+                            else ent[slot] = pack_entry<PT>(i & lmask, j, nbits);
+                        }
                         o += __popc(m);
                     }
                 }
@@ -2124,11 +2153,40 @@ static fast_status search_map(fast_ctx *c, const fast_tables *tb, const uint32_t
 
 // Sparse pairs of small and medium buckets: count per group, scan, append,
 // vote per row.  PT is the packed entry type (local row, j).
+// Row groups of a single-pass emission moved to exact offsets: a warp per
+// group copies its region slots, then the overflow (sorted by group) follows.
+__global__ void k_region_compact(const uint32_t *__restrict__ region, uint32_t cap, const uint32_t *__restrict__ gcur,
+                                 const uint64_t *__restrict__ goff, uint64_t ng, uint32_t *__restrict__ ent) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; g < ng;
+         g += (uint64_t)gridDim.x * blockDim.x / 32) {
+        const uint32_t n = min(gcur[g], cap);
+        const uint32_t *src = region + g * cap;
+        uint32_t *dst = ent + goff[g];
+        for (uint32_t x = lane; x < n; x += 32) dst[x] = __ldcs(src + x);
+    }
+}
+
+__global__ void k_ovf_place(const unsigned long long *__restrict__ ovf, uint64_t n, uint32_t cap,
+                            const uint64_t *__restrict__ goff, uint32_t *__restrict__ ent) {
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned long long x = ovf[q];
+        const uint64_t g = x >> 32;
+        uint64_t lo = 0, hi = q;  // first position of group g (the list is sorted by group)
+        while (lo < hi) {
+            const uint64_t m = (lo + hi) / 2;
+            if ((ovf[m] >> 32) < g) lo = m + 1;
+            else hi = m;
+        }
+        ent[goff[g] + cap + (q - lo)] = (uint32_t)x;
+    }
+}
+
 template <typename PT, typename Alloc>
 static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *medium, uint64_t nmedium,
                                  uint32_t gshift, uint32_t nbits, uint32_t *sp_cnt, uint64_t *sp_start,
                                  uint32_t **sp_j_out, uint8_t **sp_v_out, uint2 *long_rows, uint64_t &S_out,
-                                 Alloc &alloc, cudaStream_t s) {
+                                 Alloc &alloc, cudaStream_t s, uint64_t S_ub) {
     const fast_params &p = c->p;
     const uint64_t N = ea.N;
     unsigned long long *scal = reinterpret_cast<unsigned long long *>(c->d_scal);
@@ -2148,16 +2206,75 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     const unsigned mg = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(nmedium, c->num_sms * 8));
     cudaMemsetAsync(scal + Scal::NSMALLEMIT, 0, 8, s);
     const GroupRange all{0, ng, 0};
-    k_pairs_grp<0, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, tpw, gcnt, nullptr, nullptr, nullptr,
-                                          scal + Scal::NSMALLEMIT, all), FAST_LAUNCHED(c);
-    if (nmedium)
-        k_medium_grp<0, PT><<<mg, 256, 0, s>>>(ea, medium, scal + Scal::NMEDIUM, gshift, nbits, gcnt, nullptr, nullptr,
-                                               nullptr, all), FAST_LAUNCHED(c);
-    if ((st = scan_excl(c, gcnt, goff, ng, 1, goff + ng, s))) return st;
     uint64_t S = 0;
-    cudaMemcpyAsync(&S, goff + ng, 8, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(c->h_scal + Scal::NSMALLEMIT, scal + Scal::NSMALLEMIT, 8, cudaMemcpyDeviceToHost, s);
-    if ((st = sync_check(c, s, "pair count"))) return st;
+    // Single pass (one row partition, 32-bit entries, room for regions of
+    // about twice the expected group size): pairs are written once into
+    // fixed group regions and compacted; otherwise counted, then written.
+    bool single = false;
+    if (sizeof(PT) == 4 && p.query_part <= 1 && c->single_pass) {
+        uint32_t cap = 256;
+        while ((uint64_t)cap < 2 * (S_ub / ng + 1) && cap < (1u << 16)) cap <<= 1;
+        if (c->group_slots) cap = c->group_slots;
+        const uint64_t ovf_cap = c->group_slots ? S_ub + (1 << 20) : std::max<uint64_t>(1 << 20, S_ub / 8);
+        const uint64_t need = ng * cap * 4 + ovf_cap * 16 + S_ub * 4;
+        const uint64_t room = c->budget ? (c->budget > c->live ? (c->budget - c->live) / 2 : 0) : ~0ull;
+        uint32_t *region = nullptr;
+        unsigned long long *ovf = nullptr;
+        if (need <= room && !(st = alloc(&region, ng * cap)) && !(st = alloc(&ovf, ovf_cap))) {
+            EnumArgs e1 = ea;  // ids flagged from the bitmap, no flagged copy
+            e1.fsid = nullptr;
+            e1.fsid_out = nullptr;
+            const RegionSink rs{region, cap, ovf, ovf_cap, scal + Scal::NOVF};
+            cudaMemsetAsync(scal + Scal::NOVF, 0, 8, s);
+            stage_mark(c, 10, s);
+            k_pairs_grp<2, PT><<<eg, 256, 0, s>>>(e1, gshift, nbits, tpw, nullptr, nullptr, gcur, nullptr,
+                                                  scal + Scal::NSMALLEMIT, all, rs), FAST_LAUNCHED(c);
+            stage_mark(c, 12, s);
+            if (nmedium)
+                k_medium_grp<2, PT><<<mg, 256, 0, s>>>(e1, medium, scal + Scal::NMEDIUM, gshift, nbits, nullptr,
+                                                       nullptr, gcur, nullptr, all, rs), FAST_LAUNCHED(c);
+            if ((st = scan_excl(c, gcur, goff, ng, 1, goff + ng, s))) return st;
+            cudaMemcpyAsync(&S, goff + ng, 8, cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(c->h_scal + Scal::NSMALLEMIT, scal + Scal::NSMALLEMIT, 8, cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(c->h_scal + Scal::NOVF, scal + Scal::NOVF, 8, cudaMemcpyDeviceToHost, s);
+            if ((st = sync_check(c, s, "pair pass"))) return st;
+            const uint64_t novf = c->h_scal[Scal::NOVF];
+            if (novf <= ovf_cap) {
+                single = true;
+                if ((st = alloc(&ent, S))) return st;
+                k_region_compact<<<c->num_sms * 16, 256, 0, s>>>(region, cap, gcur, goff, ng,
+                                                                 reinterpret_cast<uint32_t *>(ent)), FAST_LAUNCHED(c);
+                if (novf) {
+                    unsigned long long *ovf2 = nullptr;
+                    uint64_t *srt = nullptr;
+                    if ((st = alloc(&ovf2, novf))) return st;
+                    if ((st = sort_u64(c, novf, reinterpret_cast<uint64_t *>(ovf), reinterpret_cast<uint64_t *>(ovf2),
+                                       32, 32 + bits_for(ng), &srt, s)))
+                        return st;
+                    k_ovf_place<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(novf, 256),
+                                                                                       c->num_sms * 8)),
+                                  256, 0, s>>>(reinterpret_cast<const unsigned long long *>(srt), novf, cap, goff,
+                                               reinterpret_cast<uint32_t *>(ent)), FAST_LAUNCHED(c);
+                }
+                stage_mark(c, 11, s);
+            } else {  // overflow list too short: count, then write
+                cudaMemsetAsync(gcur, 0, ng * 4, s);
+                cudaMemsetAsync(scal + Scal::NSMALLEMIT, 0, 8, s);
+            }
+        }
+        st = FAST_OK;
+    }
+    if (!single) {
+        k_pairs_grp<0, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, tpw, gcnt, nullptr, nullptr, nullptr,
+                                              scal + Scal::NSMALLEMIT, all), FAST_LAUNCHED(c);
+        if (nmedium)
+            k_medium_grp<0, PT><<<mg, 256, 0, s>>>(ea, medium, scal + Scal::NMEDIUM, gshift, nbits, gcnt, nullptr,
+                                                   nullptr, nullptr, all), FAST_LAUNCHED(c);
+        if ((st = scan_excl(c, gcnt, goff, ng, 1, goff + ng, s))) return st;
+        cudaMemcpyAsync(&S, goff + ng, 8, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(c->h_scal + Scal::NSMALLEMIT, scal + Scal::NSMALLEMIT, 8, cudaMemcpyDeviceToHost, s);
+        if ((st = sync_check(c, s, "pair count"))) return st;
+    }
     S_out = S;
     c->stats.n_pairs_small = c->h_scal[Scal::NSMALLEMIT];
 
@@ -2165,7 +2282,7 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     // pair counts, each written and voted in turn, so the pair buffer holds
     // one range.  As many as query_part asks for, or as the HBM budget needs.
     uint32_t nparts = std::max<uint32_t>(1, p.query_part);
-    if (c->budget) {
+    if (c->budget && !single) {
         const uint64_t room = c->budget > c->live ? (c->budget - c->live) / 2 : 0;
         const uint64_t need = S * sizeof(PT);
         if (room && need > room) nparts = std::max<uint64_t>(nparts, (need + room - 1) / room);
@@ -2188,7 +2305,7 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
         for (size_t q = 0; q + 1 < cut.size(); q++) part_max = std::max(part_max, hg[cut[q + 1]] - hg[cut[q]]);
     }
     c->stats.query_parts = (uint32_t)(cut.size() - 1);
-    if ((st = alloc(&ent, part_max))) return st;
+    if (!single && (st = alloc(&ent, part_max))) return st;
 
     // hash capacity: twice the power of two above the target (group sizes vary), at least 4096
     uint32_t vcap = 64;
@@ -2232,15 +2349,17 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
             va.g_hi = gr.g_hi;
             va.ebase = gr.ebase;
             // write the range's pairs (gcur restarts per range: every group is in exactly one)
-            if (cut.size() > 2 || attempt > 0) cudaMemsetAsync(gcur + gr.g_lo, 0, (gr.g_hi - gr.g_lo) * 4, s);
-            stage_mark(c, 10, s);
-            k_pairs_grp<1, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, tpw, nullptr, goff, gcur, ent, nullptr, gr),
-                FAST_LAUNCHED(c);
-            stage_mark(c, 12, s);
-            if (nmedium)
-                k_medium_grp<1, PT><<<mg, 256, 0, s>>>(ea, medium, scal + Scal::NMEDIUM, gshift, nbits, nullptr, goff,
-                                                       gcur, ent, gr), FAST_LAUNCHED(c);
-            stage_mark(c, 11, s);
+            if (!single) {
+                if (cut.size() > 2 || attempt > 0) cudaMemsetAsync(gcur + gr.g_lo, 0, (gr.g_hi - gr.g_lo) * 4, s);
+                stage_mark(c, 10, s);
+                k_pairs_grp<1, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, tpw, nullptr, goff, gcur, ent, nullptr, gr),
+                    FAST_LAUNCHED(c);
+                stage_mark(c, 12, s);
+                if (nmedium)
+                    k_medium_grp<1, PT><<<mg, 256, 0, s>>>(ea, medium, scal + Scal::NMEDIUM, gshift, nbits, nullptr,
+                                                           goff, gcur, ent, gr), FAST_LAUNCHED(c);
+                stage_mark(c, 11, s);
+            }
             // vote the range
             cudaMemsetAsync(scal + Scal::NLONG, 0, 8, s);
             cudaMemsetAsync(scal + Scal::NSLOW, 0, 8, s);
@@ -2486,9 +2605,10 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
         // 32-bit entries while entry + 1 cannot wrap to the empty key
         const fast_status r = gshift + nbits < 32
                                   ? sparse_groups<uint32_t>(c, ea, medium, nmedium, gshift, nbits, sp_cnt, sp_start,
-                                                            &sp_j, &sp_v, long_rows, S, alloc, s)
+                                                            &sp_j, &sp_v, long_rows, S, alloc, s, S_ub)
                                   : sparse_groups<unsigned long long>(c, ea, medium, nmedium, gshift, nbits, sp_cnt,
-                                                                      sp_start, &sp_j, &sp_v, long_rows, S, alloc, s);
+                                                                      sp_start, &sp_j, &sp_v, long_rows, S, alloc, s,
+                                                                      S_ub);
         if (r) return fail(r);
     }
     stage_mark(c, 6, s);

@@ -151,7 +151,8 @@ def test_row_partitions_identical_and_forced_by_budget():
     wb = replace(synth.scaled("c1", 20_000), n_templates=0, periods=(), kind=0, r=1, b=10, v=3, excl=0, occ_num=0)
     idxb = torch.from_numpy(synth.generate(wb, ld=_pad(wb.K))).cuda()
     pb = wb.params()
-    s = _searcher(pb, large_min=10**9)  # no dense groups: every pair goes through the pair buffer
+    # no dense groups: every pair goes through the pair buffer, counted then written
+    s = _searcher(pb, large_min=10**9, single_pass=0)
     refb = s.detect(idxb).numpy()
     st = s.stats()
     peak, need = st["peak_bytes"], st["n_emissions"] * 4
@@ -159,7 +160,7 @@ def test_row_partitions_identical_and_forced_by_budget():
     s.close()
     split = 0
     for frac in (0.3, 0.45, 0.6):
-        sb = Searcher(pb, hbm_budget_bytes=int(peak - frac * need), large_min=10**9)
+        sb = Searcher(pb, hbm_budget_bytes=int(peak - frac * need), large_min=10**9, single_pass=0)
         try:
             got = sb.detect(idxb).numpy()
         except FastError:
@@ -169,6 +170,27 @@ def test_row_partitions_identical_and_forced_by_budget():
         split += sb.stats()["query_parts"] >= 2
         sb.close()
     assert split >= 1
+
+
+@pytest.mark.parametrize("name,n,over", [("c1", 60_000, dict()), ("c0", 8192, dict(v=1, excl=0))])
+def test_single_pass_and_overflow_identical(name, n, over):
+    # pairs written once into fixed group regions (default), counted then
+    # written (single_pass=0), and regions of 2 slots per group so that
+    # almost every pair goes through the overflow list: one list
+    w = synth.scaled(name, n, **over)
+    idx = torch.from_numpy(synth.generate(w, ld=_pad(w.K))).cuda()
+    p = w.params()
+    lists = []
+    for opts in (dict(), dict(single_pass=0), dict(group_slots=2), dict(group_slots=1, large_min=10**9)):
+        s = _searcher(p, **opts)
+        lists.append(s.detect(idx).numpy())
+        s.close()
+    assert len(lists[0][0]) > 0
+    for got in lists[1:3]:
+        _assert_lists(got, lists[0])
+    _, _, want = _oracle_run(p, idx.cpu().numpy(), w.K)
+    _assert_lists(lists[0], want)
+    _assert_lists(lists[3], want)
 
 
 def test_dense_and_sparse_paths_agree():
