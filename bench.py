@@ -237,8 +237,8 @@ def kernel_rooflines(w, per, st, peaks, n_sms):
     HBM roofline fraction they reach.  Algorithmic bytes (per unit):
       k_sig_walk      read K u16 indices + write b keys  = 2K + 4b  per fingerprint
       radix sort      read key + write (key, id)         = 12       per table entry (all passes together)
-      k_pairs_grp<1>  read (key, flagged id) 8 per table entry + write 4 per small-bucket pair
-      k_group_vote    read 4 per pair emission + write 5 per kept sparse pair (not counted: small)
+      k_pairs_grp<2>  read (key, id) 8 per table entry + write 4 per small-bucket pair (one pass)
+      k_warp_vote     read 4 per pair emission + write 5 per kept sparse pair (not counted: small)
       output          write (i, j, votes)                = 9        per detection"""
     N, b, K = w.N, w.b, w.K
     hbm = float(peaks.get("hbm_gbs", 6800.0))
@@ -260,10 +260,56 @@ def kernel_rooflines(w, per, st, peaks, n_sms):
                   "time_at_peak_ms": 1000 * N * K * F * 4 / alu_peak})
     passes = max(1, st["sort_passes"])
     put("radix sort", per["sort"], N * b * 12, False, None, passes=passes)
-    put("k_pairs_grp<1>", per["k_pairs"], N * b * 8 + st["n_pairs_small"] * 4, True,
-        _traffic("k_pairs_grp<1>", st["n_pairs_small"]))
-    put("k_group_vote", per["k_vote"], st["n_emissions"] * 4, True, _traffic("k_group_vote", st["n_emissions"]))
+    put("k_pairs_grp<2>", per["k_pairs"], N * b * 8 + st["n_pairs_small"] * 4, True,
+        _traffic("k_pairs_grp<2>", N))
+    put("k_warp_vote", per["k_vote"], st["n_emissions"] * 4, True, _traffic("k_warp_vote", N))
     put("output", per["output"], st["n_detections"] * 9, False)
+    return out
+
+
+TRAFFIC_KERNELS = {  # kernel-name prefix in the ncu list -> (roofline name, source file)
+    "k_sig_walk": ("k_sig_walk", "paper_1803_09835_gb300/csrc/k_sig.cu"),
+    "k_pairs_grp<2": ("k_pairs_grp<2>", "paper_1803_09835_gb300/csrc/k_search.cu"),
+    "k_warp_vote": ("k_warp_vote", "paper_1803_09835_gb300/csrc/k_search.cu"),
+}
+
+
+def record_traffic(csv_path: str, n_windows: int, command: str) -> dict:
+    """profiles/dram_traffic.json from one ncu --csv capture of
+    dram__bytes_read.sum and dram__bytes_write.sum: per kernel of
+    TRAFFIC_KERNELS, the first launch's bytes per window of the workload,
+    with the hash of the kernel's source file at capture time."""
+    import csv
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
+    rows = list(csv.reader(open(csv_path)))
+    hdr = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
+    h = rows[hdr]
+    ki, mi, ui, vi, ii = (h.index(x) for x in ("Kernel Name", "Metric Name", "Metric Unit", "Metric Value", "ID"))
+    seen = {}
+    for r in rows[hdr + 1:]:
+        if len(r) <= vi:
+            continue
+        name = r[ki].replace("void ", "").replace("(anonymous namespace)::", "").replace("unnamed>::", "")
+        name = name.split("(")[0].split("::")[-1]
+        key = next((k for k in TRAFFIC_KERNELS if name.startswith(k)), None)
+        if key is None or (key in seen and seen[key]["id"] != r[ii]):
+            continue
+        rec = seen.setdefault(key, {"id": r[ii], "read": 0.0, "write": 0.0})
+        v = float(r[vi].replace(",", "")) * scale.get(r[ui], 1)
+        if r[mi] == "dram__bytes_read.sum":
+            rec["read"] = v
+        elif r[mi] == "dram__bytes_write.sum":
+            rec["write"] = v
+    out = {}
+    for key, rec in seen.items():
+        name, src = TRAFFIC_KERNELS[key]
+        out[name] = {"source": src, "source_sha256_16": _kernel_source_hash(src),
+                     "bytes_per_unit": (rec["read"] + rec["write"]) / n_windows, "unit": "fingerprint",
+                     "captured_on": f"{n_windows:,} windows, first launch", "dram_read_bytes": rec["read"],
+                     "dram_write_bytes": rec["write"], "command": command}
+    with open(os.path.join(ROOT, "profiles", "dram_traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
     return out
 
 
@@ -596,7 +642,14 @@ def main():
     ap.add_argument("--batch", action="store_true", help="12-station workload (c2) searched in station batches")
     ap.add_argument("--query-part", type=int, default=4, help="query partitions of the pair buffer for --batch")
     ap.add_argument("--groups", default="", help="--batch station groups by months, e.g. '12,6+1'")
+    ap.add_argument("--record-traffic", default="", metavar="CSV",
+                    help="write profiles/dram_traffic.json from an ncu dram-bytes capture of this workload")
+    ap.add_argument("--record-command", default="", help="the ncu command line to note beside --record-traffic")
     args = ap.parse_args()
+    if args.record_traffic:
+        w = station_workload(args.workload, 0, args.n)
+        print(json.dumps(record_traffic(args.record_traffic, w.N, args.record_command), indent=1))
+        return 0
     if args.serving:
         return serving_arm(args)
     if args.batch:

@@ -121,6 +121,7 @@ typedef struct {
     float ms_k_pairs, ms_k_vote;
     uint64_t n_pairs_small;   /* of n_emissions: pairs of buckets with at most 32 entries */
     uint64_t peak_bytes;      /* most device memory held at once during the call    */
+    uint64_t n_overflow;      /* single-pass pairs past their group's region slots   */
 } fast_stats;
 
 /*

@@ -901,7 +901,38 @@ struct VoteArgs {
     uint2 *long_rows;  // (row, candidate bound) for rows voted one CTA each
     unsigned long long *n_long;
     uint64_t long_cap;
+    // single-pass layout (rcnt != nullptr): group g's first rcap entries at
+    // g * rcap, the rest in the overflow list (sorted by group) from ostart[g]
+    const uint32_t *rcnt;
+    uint32_t rcap;
+    const unsigned long long *ovf;
+    const uint64_t *ostart;
 };
+
+// Where group g's entries are: base e0 and count n.
+__device__ __forceinline__ void group_span(const VoteArgs &A, uint64_t g, uint64_t &e0, uint64_t &n) {
+    if (A.rcnt) {
+        e0 = g * A.rcap;
+        n = A.rcnt[g];
+    } else {
+        e0 = A.goff[g] - A.ebase;
+        n = A.goff[g + 1] - A.goff[g];
+    }
+}
+
+// Entries of group g below `lim` lie at e0 + x; entries from lim to n are in
+// the overflow list (single pass only).  Loads are predicated, not branched,
+// so a batch of them stays in flight together.
+__device__ __forceinline__ uint64_t region_lim(const VoteArgs &A, uint64_t n) {
+    return A.rcnt ? min(n, (uint64_t)A.rcap) : n;
+}
+
+template <typename PT>
+__device__ __forceinline__ PT entry_at(const VoteArgs &A, const PT *__restrict__ ent, uint64_t g, uint64_t e0,
+                                       uint64_t lim, uint64_t x, bool stream = false) {
+    if (x < lim) return stream ? __ldcs(ent + e0 + x) : ent[e0 + x];
+    return (PT)(uint32_t)A.ovf[A.ostart[g] + (x - lim)];
+}
 
 // Hash insert for the row votes (key j+1, 0 = empty), 32-bit counts.
 __device__ __forceinline__ bool vadd(uint32_t *K, uint32_t *C, uint32_t slots, uint32_t j) {
@@ -969,7 +1000,7 @@ __device__ __forceinline__ uint32_t fhash(unsigned long long key, uint32_t lg) {
         }                                                                             \
     } else {                                                                          \
         for (uint64_t x_ = threadIdx.x; x_ < n; x_ += blockDim.x) {                   \
-            const PT raw = ent[e0 + x_];                                              \
+            const PT raw = entry_at(A, ent, g, e0, region_lim(A, n), x_);             \
             if ((uint32_t)(raw >> A.nbits) - r0 >= r1 - r0) continue;                 \
             BODY                                                                      \
         }                                                                             \
@@ -1120,15 +1151,12 @@ __global__ void __launch_bounds__(256) k_group_vote(VoteArgs A, const PT *__rest
     auto fetch = [&](uint64_t gg, PT (&buf)[kVRegs], uint64_t &s0, uint64_t &cnt) {
         s0 = 0;
         cnt = 0;
-        if (gg < A.ngroups) {
-            s0 = A.goff[gg] - A.ebase;
-            cnt = A.goff[gg + 1] - A.goff[gg];
-        }
+        if (gg < A.ngroups) group_span(A, gg, s0, cnt);
         const bool regs = cnt >= A.v && cnt <= A.vcap && cnt <= (uint64_t)kVRegs * blockDim.x;
 #pragma unroll
         for (int u = 0; u < kVRegs; u++) {
             const uint64_t x = threadIdx.x + (uint64_t)u * blockDim.x;
-            buf[u] = regs && x < cnt ? __ldcs(ent + s0 + x) : (PT)0;
+            buf[u] = regs && x < cnt ? entry_at(A, ent, gg, s0, region_lim(A, cnt), x, true) : (PT)0;
         }
     };
     const uint64_t count = list ? *nlist : A.ngroups;
@@ -1172,8 +1200,10 @@ __global__ void __launch_bounds__(kVW * 32) k_warp_vote(VoteArgs A, const PT *__
     const PT jmask = ((PT)1 << A.nbits) - 1;
     const uint32_t lt = (1u << lane) - 1;
     for (uint64_t g = A.g_lo + (uint64_t)blockIdx.x * kVW + warp; g < A.g_hi; g += (uint64_t)gridDim.x * kVW) {
-        const uint64_t e0 = A.goff[g] - A.ebase, n = A.goff[g + 1] - A.goff[g];
+        uint64_t e0, n;
+        group_span(A, g, e0, n);
         if (n < A.v) continue;  // warp-uniform
+        const uint64_t lim = region_lim(A, n);
         const uint64_t row0 = g << A.gshift;
         if (n > A.vcap) {  // every row of the group is voted one CTA each
             for (uint32_t r = lane; r < (1u << A.gshift); r += 32) {
@@ -1192,7 +1222,7 @@ __global__ void __launch_bounds__(kVW * 32) k_warp_vote(VoteArgs A, const PT *__
             for (uint32_t x0 = lane; x0 < n; x0 += 8 * 32) {
                 PT b8[8];
 #pragma unroll
-                for (int u = 0; u < 8; u++) b8[u] = x0 + 32 * u < n ? ent[e0 + x0 + 32 * u] : (PT)0;
+                for (int u = 0; u < 8; u++) b8[u] = x0 + 32 * u < lim ? ent[e0 + x0 + 32 * u] : x0 + 32 * u < n ? entry_at(A, ent, g, e0, lim, x0 + 32 * u) : (PT)0;
 #pragma unroll
                 for (int u = 0; u < 8; u++) {
                     const uint32_t part = x0 + 32 * u < n ? (uint32_t)(b8[u] >> A.nbits) * P / rows : 8u;
@@ -1227,7 +1257,7 @@ __global__ void __launch_bounds__(kVW * 32) k_warp_vote(VoteArgs A, const PT *__
         for (uint32_t x0 = lane; x0 < n; x0 += 8 * 32) {
             PT b8[8];
 #pragma unroll
-            for (int u = 0; u < 8; u++) b8[u] = x0 + 32 * u < n ? ent[e0 + x0 + 32 * u] : (PT)0;
+            for (int u = 0; u < 8; u++) b8[u] = x0 + 32 * u < lim ? ent[e0 + x0 + 32 * u] : x0 + 32 * u < n ? entry_at(A, ent, g, e0, lim, x0 + 32 * u) : (PT)0;
 #pragma unroll
             for (int u = 0; u < 8; u++)
                 if (x0 + 32 * u < n && (uint32_t)(b8[u] >> A.nbits) - r0 < r1 - r0) {
@@ -1240,7 +1270,7 @@ __global__ void __launch_bounds__(kVW * 32) k_warp_vote(VoteArgs A, const PT *__
         for (uint32_t x0 = lane; x0 < n; x0 += 8 * 32) {
             PT b8[8];
 #pragma unroll
-            for (int u = 0; u < 8; u++) b8[u] = x0 + 32 * u < n ? ent[e0 + x0 + 32 * u] : (PT)0;
+            for (int u = 0; u < 8; u++) b8[u] = x0 + 32 * u < lim ? ent[e0 + x0 + 32 * u] : x0 + 32 * u < n ? entry_at(A, ent, g, e0, lim, x0 + 32 * u) : (PT)0;
 #pragma unroll
             for (int u = 0; u < 8; u++)
                 if (x0 + 32 * u < n && (uint32_t)(b8[u] >> A.nbits) - r0 < r1 - r0) {
@@ -1267,7 +1297,8 @@ __global__ void __launch_bounds__(kVW * 32) k_warp_vote(VoteArgs A, const PT *__
             PT b8[8];
 #pragma unroll
             for (int u = 0; u < 8; u++)
-                b8[u] = x0 + 32 * u < n ? (p + 1 == P ? __ldcs(ent + e0 + x0 + 32 * u) : ent[e0 + x0 + 32 * u]) : (PT)0;
+                b8[u] = x0 + 32 * u < lim ? (p + 1 == P ? __ldcs(ent + e0 + x0 + 32 * u) : ent[e0 + x0 + 32 * u])
+                        : x0 + 32 * u < n ? entry_at(A, ent, g, e0, lim, x0 + 32 * u) : (PT)0;
 #pragma unroll
             for (int u = 0; u < 8; u++) {
                 if (x0 + 32 * u >= n || (uint32_t)(b8[u] >> A.nbits) - r0 >= r1 - r0) continue;
@@ -1359,8 +1390,10 @@ __global__ void __launch_bounds__(512) k_long_vote(VoteArgs A, const PT *__restr
         __syncthreads();
         const uint64_t g = i >> A.gshift;
         const uint32_t local = i & ((1u << A.gshift) - 1);
-        for (uint64_t e = A.goff[g] - A.ebase + threadIdx.x; e < A.goff[g + 1] - A.ebase; e += blockDim.x) {
-            const PT en = ent[e];
+        uint64_t e0, n;
+        group_span(A, g, e0, n);
+        for (uint64_t x = threadIdx.x; x < n; x += blockDim.x) {
+            const PT en = entry_at(A, ent, g, e0, region_lim(A, n), x);
             if ((uint32_t)(en >> A.nbits) == local) vadd(K, C, slots, (uint32_t)(en & jmask));
         }
         __syncthreads();
@@ -2153,32 +2186,12 @@ static fast_status search_map(fast_ctx *c, const fast_tables *tb, const uint32_t
 
 // Sparse pairs of small and medium buckets: count per group, scan, append,
 // vote per row.  PT is the packed entry type (local row, j).
-// Row groups of a single-pass emission moved to exact offsets: a warp per
-// group copies its region slots, then the overflow (sorted by group) follows.
-__global__ void k_region_compact(const uint32_t *__restrict__ region, uint32_t cap, const uint32_t *__restrict__ gcur,
-                                 const uint64_t *__restrict__ goff, uint64_t ng, uint32_t *__restrict__ ent) {
-    const uint32_t lane = threadIdx.x & 31;
-    for (uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; g < ng;
-         g += (uint64_t)gridDim.x * blockDim.x / 32) {
-        const uint32_t n = min(gcur[g], cap);
-        const uint32_t *src = region + g * cap;
-        uint32_t *dst = ent + goff[g];
-        for (uint32_t x = lane; x < n; x += 32) dst[x] = __ldcs(src + x);
-    }
-}
-
-__global__ void k_ovf_place(const unsigned long long *__restrict__ ovf, uint64_t n, uint32_t cap,
-                            const uint64_t *__restrict__ goff, uint32_t *__restrict__ ent) {
+// First position of each group in the overflow list of a single-pass
+// emission (sorted by group).
+__global__ void k_ovf_starts(const unsigned long long *__restrict__ ovf, uint64_t n, uint64_t *__restrict__ ostart) {
     for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (uint64_t)gridDim.x * blockDim.x) {
-        const unsigned long long x = ovf[q];
-        const uint64_t g = x >> 32;
-        uint64_t lo = 0, hi = q;  // first position of group g (the list is sorted by group)
-        while (lo < hi) {
-            const uint64_t m = (lo + hi) / 2;
-            if ((ovf[m] >> 32) < g) lo = m + 1;
-            else hi = m;
-        }
-        ent[goff[g] + cap + (q - lo)] = (uint32_t)x;
+        const uint64_t g = ovf[q] >> 32;
+        if (q == 0 || (ovf[q - 1] >> 32) != g) ostart[g] = q;
     }
 }
 
@@ -2211,12 +2224,19 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     // about twice the expected group size): pairs are written once into
     // fixed group regions and compacted; otherwise counted, then written.
     bool single = false;
+    c->stats.n_overflow = 0;
+    uint32_t rcap = 0;
+    const unsigned long long *ovf_sorted = nullptr;
+    uint64_t *ostart = nullptr;
     if (sizeof(PT) == 4 && p.query_part <= 1 && c->single_pass) {
+        // about twice the expected group size, plus one 128-byte line so that
+        // region starts do not all fall on the same DRAM channels
         uint32_t cap = 256;
         while ((uint64_t)cap < 2 * (S_ub / ng + 1) && cap < (1u << 16)) cap <<= 1;
+        cap += 32;
         if (c->group_slots) cap = c->group_slots;
         const uint64_t ovf_cap = c->group_slots ? S_ub + (1 << 20) : std::max<uint64_t>(1 << 20, S_ub / 8);
-        const uint64_t need = ng * cap * 4 + ovf_cap * 16 + S_ub * 4;
+        const uint64_t need = ng * cap * 4 + ovf_cap * 16;
         const uint64_t room = c->budget ? (c->budget > c->live ? (c->budget - c->live) / 2 : 0) : ~0ull;
         uint32_t *region = nullptr;
         unsigned long long *ovf = nullptr;
@@ -2239,22 +2259,22 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
             cudaMemcpyAsync(c->h_scal + Scal::NOVF, scal + Scal::NOVF, 8, cudaMemcpyDeviceToHost, s);
             if ((st = sync_check(c, s, "pair pass"))) return st;
             const uint64_t novf = c->h_scal[Scal::NOVF];
-            if (novf <= ovf_cap) {
+            c->stats.n_overflow = novf;
+            if (novf <= ovf_cap) {  // the vote reads the regions and the sorted overflow list in place
                 single = true;
-                if ((st = alloc(&ent, S))) return st;
-                k_region_compact<<<c->num_sms * 16, 256, 0, s>>>(region, cap, gcur, goff, ng,
-                                                                 reinterpret_cast<uint32_t *>(ent)), FAST_LAUNCHED(c);
+                ent = reinterpret_cast<PT *>(region);
+                rcap = cap;
                 if (novf) {
                     unsigned long long *ovf2 = nullptr;
                     uint64_t *srt = nullptr;
-                    if ((st = alloc(&ovf2, novf))) return st;
+                    if ((st = alloc(&ovf2, novf)) || (st = alloc(&ostart, ng))) return st;
                     if ((st = sort_u64(c, novf, reinterpret_cast<uint64_t *>(ovf), reinterpret_cast<uint64_t *>(ovf2),
                                        32, 32 + bits_for(ng), &srt, s)))
                         return st;
-                    k_ovf_place<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(novf, 256),
-                                                                                       c->num_sms * 8)),
-                                  256, 0, s>>>(reinterpret_cast<const unsigned long long *>(srt), novf, cap, goff,
-                                               reinterpret_cast<uint32_t *>(ent)), FAST_LAUNCHED(c);
+                    ovf_sorted = reinterpret_cast<const unsigned long long *>(srt);
+                    k_ovf_starts<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(novf, 256),
+                                                                                        c->num_sms * 8)),
+                                   256, 0, s>>>(ovf_sorted, novf, ostart), FAST_LAUNCHED(c);
                 }
                 stage_mark(c, 11, s);
             } else {  // overflow list too short: count, then write
@@ -2325,7 +2345,8 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     cudaFuncSetAttribute(k_long_vote<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
     uint64_t sp_cap = std::max<uint64_t>(N, 1 << 20);
     VoteArgs va{goff, ng, N, 0, ng, 0, gshift, nbits, p.v, vcap, sp_cnt, sp_start, nullptr, nullptr, 0,
-                scal + Scal::CUR_SPARSE, long_rows, scal + Scal::NLONG, N};
+                scal + Scal::CUR_SPARSE, long_rows, scal + Scal::NLONG, N,
+                single ? gcur : nullptr, rcap, ovf_sorted, ostart};
     std::vector<uint64_t> hgb(cut.size());  // goff at the cuts
     if (cut.size() > 2) {
         for (size_t q = 0; q < cut.size(); q++) cudaMemcpyAsync(&hgb[q], goff + cut[q], 8, cudaMemcpyDeviceToHost, s);
