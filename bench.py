@@ -428,7 +428,8 @@ def gpu_arm(args, rank, world, local_rank):
             "stage_ms": per,
             "counters": {k: last[k] for k in ("n_dropped", "n_emissions", "n_dense_pairs", "n_groups",
                                               "n_detections", "map_slots", "query_parts", "sort_passes",
-                                              "n_long_rows", "n_huge_rows", "max_row")}}
+                                              "n_long_rows", "n_huge_rows", "max_row", "n_pairs_small",
+                                              "n_overflow", "peak_bytes")}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, thr, Ms = oracle_sample(w, args.cpu_sample)
         line["cpu_baseline"] = {"value": args.cpu_sample / dt, "unit": UNIT, "cores": thr, "kind": "oracle",
