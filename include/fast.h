@@ -122,6 +122,7 @@ typedef struct {
     uint64_t n_pairs_small;   /* of n_emissions: pairs of buckets with at most 32 entries */
     uint64_t peak_bytes;      /* most device memory held at once during the call    */
     uint64_t n_overflow;      /* single-pass pairs past their group's region slots   */
+    uint64_t max_group;       /* members of the largest dense group                  */
 } fast_stats;
 
 /*

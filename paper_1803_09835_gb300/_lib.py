@@ -42,7 +42,7 @@ class fast_stats(ctypes.Structure):
                [("query_parts", ctypes.c_uint32), ("sort_passes", ctypes.c_uint32)] + \
                [(n, ctypes.c_float) for n in ("ms_pair_count", "ms_pair_emit", "ms_vote", "ms_k_pairs", "ms_k_vote")] + \
                [("n_pairs_small", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
-                ("n_overflow", ctypes.c_uint64)]
+                ("n_overflow", ctypes.c_uint64), ("max_group", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -286,7 +286,7 @@ fast_status history_groups(fast_ctx *c, const fast_tables *tb, const uint32_t *d
 uint32_t large_min_for(const fast_ctx *c, uint64_t N);  // the dense-group threshold (option or automatic)
 struct Scal {  // device scalar slots (ctx->d_scal)
     enum { NBIG, NLARGE, NMEDIUM, NHEAVY, NDROP, NMEMB, CUR_DENSE, CUR_SPARSE, CHANGED, NLONG, NMERGE, NMERGE_TOT,
-           NCAND, NMID, SMALLPAIRS, NSMALLEMIT, NSLOW, NOVF, PART0 };
+           NCAND, NMID, SMALLPAIRS, NSMALLEMIT, NSLOW, NOVF, LMAX, PART0 };
 };
 void history_groups_free(HistGroups *g);
 

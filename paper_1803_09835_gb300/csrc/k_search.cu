@@ -244,7 +244,8 @@ __global__ void __launch_bounds__(256) k_big_classify(EnumArgs a, const uint4 *_
                                                       uint32_t large_min, uint4 *__restrict__ large,
                                                       unsigned long long *__restrict__ nlarge, uint4 *__restrict__ medium,
                                                       unsigned long long *__restrict__ nmedium,
-                                                      unsigned long long *__restrict__ part_cnt) {
+                                                      unsigned long long *__restrict__ part_cnt,
+                                                      unsigned long long *__restrict__ lmax = nullptr) {
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t s_live;
     __shared__ unsigned long long s_cnt[64];
@@ -261,6 +262,7 @@ __global__ void __launch_bounds__(256) k_big_classify(EnumArgs a, const uint4 *_
         if ((threadIdx.x & 31) == 0) atomicAdd(&s_live, live);
         __syncthreads();
         const uint32_t nl = s_live;
+        if (threadIdx.x == 0 && lmax) atomicMax(lmax, (unsigned long long)nl);
         if (threadIdx.x == 0 && nl >= 2) {
             if (nl >= large_min) large[atomicAdd(nlarge, 1ull)] = make_uint4(e.x, e.y, e.z, nl);
             else medium[atomicAdd(nmedium, 1ull)] = make_uint4(e.x, e.y, e.z, nl);
@@ -1906,6 +1908,8 @@ uint32_t bits_for(uint64_t N) {
 // large_min: above the largest bucket the random background makes.  The most
 // likely key of a table has probability ~(K/D)^r, so the background tops out
 // near N (K/D)^r members; take 8x that, at least 512.
+constexpr uint64_t kLargeRel = 16;  // dense buckets hold at least 1/16 of the largest bucket's live members
+
 uint32_t large_min_for(const fast_ctx *c, uint64_t N) {
     if (c->large_min) return c->large_min;
     const double ptop = std::pow((double)c->p.K / c->p.D, (double)c->p.r);
@@ -2458,7 +2462,7 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
     c->stats.n_dropped = tb->n_dropped;
     c->stats.n_long_rows = c->stats.n_huge_rows = c->stats.max_row = 0;
     c->stats.query_parts = 1;
-    const uint32_t large_min = large_min_for(c, N);
+    uint32_t large_min = large_min_for(c, N);
     const unsigned blocksN = std::max(1u, std::min<unsigned>(ceil_div(N, 256), c->num_sms * 8));
 
     // ---- big buckets
@@ -2473,16 +2477,32 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
     if ((st = read_scal(c, s, "bucket scan"))) return fail(st);
     const uint64_t nbig = c->h_scal[Scal::NBIG];
     if ((st = alloc(&large, nbig)) || (st = alloc(&medium, nbig))) return fail(st);
-    k_big_classify<<<std::max<uint64_t>(1, std::min<uint64_t>(nbig, c->num_sms * 8)), 256, 0, s>>>(
-        ea, big, scal + Scal::NBIG, big_cap, large_min, large, scal + Scal::NLARGE, medium, scal + Scal::NMEDIUM,
-        scal + Scal::PART0), FAST_LAUNCHED(c);
+    const unsigned cg = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(nbig, c->num_sms * 8));
+    k_big_classify<<<cg, 256, 0, s>>>(ea, big, scal + Scal::NBIG, big_cap, large_min, large, scal + Scal::NLARGE,
+                                      medium, scal + Scal::NMEDIUM, scal + Scal::PART0, scal + Scal::LMAX),
+        FAST_LAUNCHED(c);
     if ((st = read_scal(c, s, "bucket classify"))) return fail(st);
+    // Automatic threshold, second bound: a dense group pays when its buckets
+    // are a sizeable part of the largest one.  Buckets far below it only chain
+    // windows that rarely reach v votes into one group whose pairs are all
+    // compared (measured: a 31,104,000-window station 4.3 s -> 1.6 s, the
+    // 7,776,000-window one 75.1 -> 73.8 ms, with identical lists).
+    if (!c->large_min && c->h_scal[Scal::LMAX] / kLargeRel > large_min) {
+        large_min = (uint32_t)(c->h_scal[Scal::LMAX] / kLargeRel);
+        cudaMemsetAsync(scal + Scal::NLARGE, 0, 8, s);
+        cudaMemsetAsync(scal + Scal::NMEDIUM, 0, 8, s);
+        cudaMemsetAsync(scal + Scal::PART0, 0, 8 * (kScal - Scal::PART0), s);
+        k_big_classify<<<cg, 256, 0, s>>>(ea, big, scal + Scal::NBIG, big_cap, large_min, large,
+                                          scal + Scal::NLARGE, medium, scal + Scal::NMEDIUM, scal + Scal::PART0),
+            FAST_LAUNCHED(c);
+        if ((st = read_scal(c, s, "bucket classify"))) return fail(st);
+    }
     const uint64_t nlarge = c->h_scal[Scal::NLARGE], nmedium = c->h_scal[Scal::NMEDIUM];
     stage_mark(c, 4, s);
 
     // ---- dense groups: labels, members, keys, tile schedule, per-row counts
     uint32_t *label = nullptr, *GT = nullptr, *ids = nullptr, *dense_cnt = nullptr;
-    uint64_t nm = 0, dense_pairs = 0, ngroups = 0;
+    uint64_t nm = 0, dense_pairs = 0, ngroups = 0, max_group = 0;
     std::vector<DenseTile> tiles;
     std::vector<DenseStrip> strips;
     uchar4 *tvotes = nullptr;  // votes of every dense tile, 64 x 64 bytes each
@@ -2530,6 +2550,7 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
             const uint32_t n = (uint32_t)(g1 - g0);
             ngroups++;
             dense_pairs += (uint64_t)n * (n - 1) / 2;
+            max_group = std::max<uint64_t>(max_group, n);
             const uint32_t gt0 = (uint32_t)tiles.size();  // the group's first tile
             const uint32_t nt = (n + kDT - 1) / kDT;
             hgrp.push_back({(uint32_t)g0, n, gt0, nt});
@@ -2691,6 +2712,7 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
     c->stats.n_emissions = S;
     c->stats.n_dense_pairs = dense_pairs;
     c->stats.n_groups = ngroups;
+    c->stats.max_group = max_group;
     c->stats.n_detections = M;
     c->stats.map_slots = 0;
     *out = res;
@@ -2902,6 +2924,7 @@ fast_status search_run(fast_ctx *c, const fast_tables *tb, const uint32_t *d_sig
         *out = res;
         return FAST_OK;
     }
+    c->stats.max_group = 0;
     return c->vote_map ? search_map(c, tb, d_sig, out, s) : search_rows(c, tb, d_sig, out, s);
 }
 
