@@ -23,6 +23,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -274,7 +275,7 @@ TRAFFIC_KERNELS = {  # kernel-name prefix in the ncu list -> (roofline name, sou
 }
 
 
-def record_traffic(csv_path: str, n_windows: int, command: str) -> dict:
+def record_traffic(csv_path: str, n_windows: int, command: str, out_path: str | None = None) -> dict:
     """profiles/dram_traffic.json from one ncu --csv capture of
     dram__bytes_read.sum and dram__bytes_write.sum: per kernel of
     TRAFFIC_KERNELS, the first launch's bytes per window of the workload,
@@ -289,7 +290,8 @@ def record_traffic(csv_path: str, n_windows: int, command: str) -> dict:
     for r in rows[hdr + 1:]:
         if len(r) <= vi:
             continue
-        name = r[ki].replace("void ", "").replace("(anonymous namespace)::", "").replace("unnamed>::", "")
+        name = r[ki].replace("void ", "").replace("(anonymous namespace)::", "").replace("<unnamed>::", "")
+        name = re.sub(r"\((?:int|bool|unsigned int|long|unsigned long)\)", "", name.replace("unnamed>::", ""))
         name = name.split("(")[0].split("::")[-1]
         key = next((k for k in TRAFFIC_KERNELS if name.startswith(k)), None)
         if key is None or (key in seen and seen[key]["id"] != r[ii]):
@@ -307,7 +309,7 @@ def record_traffic(csv_path: str, n_windows: int, command: str) -> dict:
                      "bytes_per_unit": (rec["read"] + rec["write"]) / n_windows, "unit": "fingerprint",
                      "captured_on": f"{n_windows:,} windows, first launch", "dram_read_bytes": rec["read"],
                      "dram_write_bytes": rec["write"], "command": command}
-    with open(os.path.join(ROOT, "profiles", "dram_traffic.json"), "w") as f:
+    with open(out_path or os.path.join(ROOT, "profiles", "dram_traffic.json"), "w") as f:
         json.dump(out, f, indent=1)
         f.write("\n")
     return out
