@@ -2286,7 +2286,10 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
                 cudaMemsetAsync(scal + Scal::NSMALLEMIT, 0, 8, s);
             }
         }
-        st = FAST_OK;
+        if (st) {  // the regions did not fit the device: count, then write (not an error of the call)
+            st = FAST_OK;
+            c->err.clear();
+        }
     }
     if (!single) {
         k_pairs_grp<0, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, tpw, gcnt, nullptr, nullptr, nullptr,
