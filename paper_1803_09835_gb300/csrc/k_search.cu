@@ -7,12 +7,14 @@
 // GB300 design.  Every bucket pair is one "emission"; emissions from all b
 // tables must be summed per pair.  Buckets come in two very different kinds:
 //   * sparse: the background, sizes ~2..50, almost every pair seen once.
-//     Default (row-partitioned) path: a counting pass sizes, per row group
-//     (2^gshift consecutive ids i), the region its pairs take; a writing pass
-//     appends every pair (i, j) there as a packed (row-in-group, j) word; a
-//     warp per group then counts the votes of its pairs in shared memory (a
-//     counting filter first, an exact hash for the few that pass) and keeps
-//     those with votes >= v in (i, j) order.  The rows are assembled into the
+//     Default (row-partitioned) path: one pass over the tables appends every
+//     pair (i, j), as a packed (row-in-group, j) word, to the region of its
+//     row group (2^gshift consecutive ids i; a fixed number of slots per group,
+//     the rare excess in an overflow list); a warp per group then counts the
+//     votes of its pairs in shared memory (a counting filter first, an exact
+//     hash for the few that pass) and keeps those with votes >= v in (i, j)
+//     order.  When the regions do not fit, a counting pass sizes the groups
+//     exactly and a writing pass fills them.  The rows are assembled into the
 //     canonical list with one scan, no global sort.  Alternative path
 //     (`vote_map`): one device open-addressing map of packed (i, j) -> votes
 //     (a 64-bit slot: i:28 | j:28 | votes:8) per query partition, then a radix
@@ -20,12 +22,15 @@
 //   * dense: a repeating source (e.g. periodic noise) puts thousands of
 //     near-copies in one bucket in most tables, so the same pairs recur in
 //     every table -- ~10^10 emissions for ~10^8 distinct pairs.  Buckets with
-//     at least `large_min` live members are merged into groups (connected
-//     components of shared large buckets); for every pair inside a group the
-//     votes are computed directly by comparing the two fingerprints' b keys,
-//     tile by tile in shared memory, once per pair instead of once per table.
-//     The sparse path skips pairs inside a group, so each pair is counted by
-//     exactly one of the two paths, and both count exactly the definition.
+//     at least `large_min` live members (and at least 1/16 of the largest
+//     bucket's) are merged into groups (connected components of shared large
+//     buckets); for every pair inside a group the votes are computed once per
+//     pair instead of once per table: from bit masks of the group's large
+//     same-key clusters (popcount) plus the pairs of its small clusters, or,
+//     for a group with too many large clusters, by comparing the two
+//     fingerprints' b keys tile by tile in shared memory.  The sparse path
+//     skips pairs inside a group, so each pair is counted by exactly one of
+//     the two paths, and both count exactly the definition.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
