@@ -2592,28 +2592,36 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
         cudaMemcpyAsync(d_grp, hgrp.data(), ngroups * sizeof(DenseGroup), cudaMemcpyHostToDevice, s);
         cudaMemsetAsync(gcol, 0, ngroups * 4, s);
         const uint64_t ne = (uint64_t)nb * nm;
-        if (nm < (1u << 24) && nb <= 256) {
-            cudaMemsetAsync(gover, 0, ngroups * 4, s);
+        // the cluster masks need 36 bytes of scratch per member and table;
+        // without them (or past 2^24 members) every group is voted by direct
+        // key comparison
+        auto clusters = [&]() -> fast_status {
             unsigned long long *ca = nullptr, *cb = nullptr;
             uint32_t *flag = nullptr;
             uint64_t *cid = nullptr, *cst = nullptr;
-            if ((st = alloc(&MB, (size_t)kClW * nm)) || (st = alloc(&ca, ne)) || (st = alloc(&cb, ne)) ||
-                (st = alloc(&flag, ne)) || (st = alloc(&cid, ne + 1)) || (st = alloc(&cst, ne + 1)))
-                return fail(st);
+            fast_status r;
+            if ((r = alloc(&MB, (size_t)kClW * nm)) || (r = alloc(&ca, ne)) || (r = alloc(&cb, ne)) ||
+                (r = alloc(&flag, ne)) || (r = alloc(&cid, ne + 1)) || (r = alloc(&cst, ne + 1)))
+                return r;
+            cudaMemsetAsync(gover, 0, ngroups * 4, s);
             cudaMemsetAsync(MB, 0, (size_t)kClW * nm * 4, s);
             const unsigned eg = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(ne, 256), c->num_sms * 8));
             k_clu_comp<<<eg, 256, 0, s>>>(GT, nm, nb, ca), FAST_LAUNCHED(c);
             uint64_t *srt = nullptr;  // by (table, key), members ascending within (stable)
-            if ((st = sort_u64(c, ne, reinterpret_cast<uint64_t *>(ca), reinterpret_cast<uint64_t *>(cb), 24, 64,
-                               &srt, s)))
-                return fail(st);
+            if ((r = sort_u64(c, ne, reinterpret_cast<uint64_t *>(ca), reinterpret_cast<uint64_t *>(cb), 24, 64,
+                              &srt, s)))
+                return r;
             const unsigned long long *sc = reinterpret_cast<const unsigned long long *>(srt);
             k_clu_mark<<<eg, 256, 0, s>>>(sc, ne, d_mg, flag), FAST_LAUNCHED(c);
-            if ((st = scan_excl(c, flag, cid, ne, 1, cid + ne, s))) return fail(st);
+            if ((r = scan_excl(c, flag, cid, ne, 1, cid + ne, s))) return r;
             k_clu_starts<<<eg, 256, 0, s>>>(flag, cid, ne, cid + ne, cst), FAST_LAUNCHED(c);
             k_clu_apply<<<c->num_sms * 8, 256, 0, s>>>(sc, cst, cid + ne, d_mg, d_grp, nm, gcol, gover, MB,
                                                        reinterpret_cast<uint32_t *>(tvotes)), FAST_LAUNCHED(c);
-        } else {
+            return FAST_OK;
+        };
+        if (nm >= (1u << 24) || nb > 256 || clusters()) {
+            c->err.clear();
+            MB = nullptr;
             cudaMemsetAsync(gover, 0x01, ngroups * 4, s);  // every group by direct comparison
         }
         cudaFuncSetAttribute(k_dense_rowcount, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
