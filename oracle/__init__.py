@@ -64,6 +64,7 @@ def _L():
         "orc_search_row": (u64, [P, vp, vp, u64, u64, pp(vp), pp(vp)]),
         "orc_pair_votes": (u32, [P, vp, u64, u64, u64]),
         "orc_stream_query": (u64, [P, vp, u64, u64, u64, vp, pp(vp), pp(vp), pp(vp)]),
+        "orc_channel_merge": (u64, [u32, vp, vp, vp, vp, u32, vp, vp, vp, u64]),
         "orc_free": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -202,3 +203,24 @@ def stream_query(params: dict, keys_all: np.ndarray, n0: int, j0: int, hist_drop
     n = _L().orc_stream_query(ctypes.byref(_p(params)), _ptr(keys_all), N, n0, j0, _ptr(hist_drop),
                               ctypes.byref(pi), ctypes.byref(pj), ctypes.byref(pv))
     return _take(n, pi, pj, pv)
+
+
+def channel_merge(lists, thr: int):
+    """Channel level (§7.1, by the sort-merge-reduce of §7.2): the channels'
+    (i, j, votes) lists summed per pair and thresholded at thr.  Returns
+    (i, j, summed votes) as uint32 / uint32 / uint16 arrays in (dt, idx1) order,
+    dt = j - i, idx1 = i."""
+    lists = [tuple(np.ascontiguousarray(a, dtype=t) for a, t in zip(l, (np.uint32, np.uint32, np.uint8)))
+             for l in lists]
+    nch = len(lists)
+    M = np.array([len(l[0]) for l in lists] or [0], dtype=np.uint64)
+    ptrs = [(ctypes.c_void_p * max(1, nch))(*[l[k].ctypes.data if len(l[k]) else None for l in lists])
+            for k in range(3)]
+    total = int(M.sum()) if nch else 0
+    oi = np.empty(max(1, total), np.uint32)
+    oj = np.empty(max(1, total), np.uint32)
+    os_ = np.empty(max(1, total), np.uint16)
+    n = _L().orc_channel_merge(nch, _ptr(M), ctypes.cast(ptrs[0], ctypes.c_void_p),
+                               ctypes.cast(ptrs[1], ctypes.c_void_p), ctypes.cast(ptrs[2], ctypes.c_void_p),
+                               thr, _ptr(oi), _ptr(oj), _ptr(os_), total)
+    return oi[:n].copy(), oj[:n].copy(), os_[:n].copy()

@@ -21,6 +21,10 @@
  *   6. votes(i,j) = number of tables in which i and j share a bucket, kept when
  *      votes >= v and j - i > E                  (§6.1 "Search"; §6.3 detection
  *                                                equation; §7.2 output triplets)
+ *   7. (streaming replay of one request, section 7 below)
+ *   8. channel level: the channels' lists summed by sort-merge-reduce and
+ *      thresholded again                         (§7.1 "Channel Level"; §7.2,
+ *                                                the sort-merge-reduce procedure)
  *
  * The paper leaves the hash family, hash_combine and the exact filter rule
  * open; the readings fixed here are:
@@ -476,4 +480,80 @@ uint64_t orc_stream_query(const orc_params *p, const uint32_t *keys, uint64_t Nt
     *out_j = L.j;
     *out_votes = L.votes;
     return L.n;
+}
+
+/* ------------------------------------------------------------------ */
+/* 8. channel level (§7.1 "Channel Level", §7.2 sort-merge-reduce)    */
+/* ------------------------------------------------------------------ */
+
+/*
+ * The channels of one station see the same ground motion at the same times,
+ * so their similarity matrices are summed and the sum is thresholded again.
+ * The paper's procedure, in its order:
+ *   sort    every channel's entries (dt = j - i, idx1 = i, sim) by dt, then idx1;
+ *   merge   the sorted channel lists into one list in the same order (ties
+ *           keep the channel order);
+ *   reduce  consecutive entries with equal (dt, idx1) into one whose sim is
+ *           their sum, discarding sums below thr.
+ * Output: (i, j, summed sim) in (dt, idx1) order.  The sum of nch votes of at
+ * most 255 each needs 16 bits.  Returns the number of entries; writes at most
+ * cap of them.
+ */
+typedef struct {
+    uint32_t dt, idx1, sim;
+} orc_trip;
+
+static int orc_cmp_trip(const void *x, const void *y)
+{
+    const orc_trip *a = x, *b = y;
+    if (a->dt != b->dt) return a->dt < b->dt ? -1 : 1;
+    if (a->idx1 != b->idx1) return a->idx1 < b->idx1 ? -1 : 1;
+    return 0;
+}
+
+uint64_t orc_channel_merge(uint32_t nch, const uint64_t *M, const uint32_t *const *I, const uint32_t *const *J,
+                           const uint8_t *const *V, uint32_t thr, uint32_t *out_i, uint32_t *out_j,
+                           uint16_t *out_sim, uint64_t cap)
+{
+    /* sorting phase */
+    orc_trip **ch = malloc(sizeof(orc_trip *) * (nch ? nch : 1));
+    uint64_t *pos = calloc(nch ? nch : 1, sizeof(uint64_t));
+    uint64_t total = 0;
+    for (uint32_t c = 0; c < nch; c++) {
+        ch[c] = malloc(sizeof(orc_trip) * (M[c] ? M[c] : 1));
+        for (uint64_t k = 0; k < M[c]; k++) ch[c][k] = (orc_trip){J[c][k] - I[c][k], I[c][k], V[c][k]};
+        qsort(ch[c], M[c], sizeof(orc_trip), orc_cmp_trip);
+        total += M[c];
+    }
+    /* merging phase: repeatedly take the smallest head (the lowest channel on ties) */
+    orc_trip *merged = malloc(sizeof(orc_trip) * (total ? total : 1));
+    for (uint64_t k = 0; k < total; k++) {
+        int best = -1;
+        for (uint32_t c = 0; c < nch; c++) {
+            if (pos[c] == M[c]) continue;
+            if (best < 0 || orc_cmp_trip(&ch[c][pos[c]], &ch[best][pos[best]]) < 0) best = (int)c;
+        }
+        merged[k] = ch[best][pos[best]++];
+    }
+    /* reduce phase */
+    uint64_t n = 0;
+    for (uint64_t k = 0; k < total;) {
+        uint64_t e = k;
+        uint32_t sum = 0;
+        while (e < total && merged[e].dt == merged[k].dt && merged[e].idx1 == merged[k].idx1) sum += merged[e++].sim;
+        if (sum >= thr) {
+            if (n < cap) {
+                out_i[n] = merged[k].idx1;
+                out_j[n] = merged[k].idx1 + merged[k].dt;
+                out_sim[n] = (uint16_t)sum;
+            }
+            n++;
+        }
+        k = e;
+    }
+    for (uint32_t c = 0; c < nch; c++) free(ch[c]);
+    free(ch);
+    free(pos);
+    free(merged);
+    return n;
 }
