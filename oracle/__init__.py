@@ -65,6 +65,7 @@ def _L():
         "orc_pair_votes": (u32, [P, vp, u64, u64, u64]),
         "orc_stream_query": (u64, [P, vp, u64, u64, u64, vp, pp(vp), pp(vp), pp(vp)]),
         "orc_channel_merge": (u64, [u32, vp, vp, vp, vp, u32, vp, vp, vp, u64]),
+        "orc_station_clusters": (u64, [vp, vp, vp, u64, u32, u32, u32, vp, u64]),
         "orc_free": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -224,3 +225,20 @@ def channel_merge(lists, thr: int):
                                ctypes.cast(ptrs[1], ctypes.c_void_p), ctypes.cast(ptrs[2], ctypes.c_void_p),
                                thr, _ptr(oi), _ptr(oj), _ptr(os_), total)
     return oi[:n].copy(), oj[:n].copy(), os_[:n].copy()
+
+
+def station_clusters(i, j, sim, gap: int, width: int, min_n: int):
+    """Station level (§7.1, §7.2): thin diagonal clusters of a (dt, idx1)-ordered
+    list (i, j, sim) -- runs along each diagonal with gaps below `gap`, merged
+    across adjacent diagonals up to `width` diagonals, pruned below `min_n`
+    entries.  Returns an int64 array [clusters, 6]: dt_min, dt_max, idx1_min,
+    idx1_max, entries, summed sim, in (dt_min, idx1_min) order."""
+    if gap < 1 or width < 1:
+        raise ValueError("gap and width must be >= 1")
+    i = np.ascontiguousarray(i, dtype=np.uint32)
+    j = np.ascontiguousarray(j, dtype=np.uint32)
+    sim = np.ascontiguousarray(sim, dtype=np.uint16)
+    n = len(i)
+    out = np.empty((max(1, n), 6), np.uint64)
+    nc = _L().orc_station_clusters(_ptr(i), _ptr(j), _ptr(sim), n, gap, width, min_n, _ptr(out), max(1, n))
+    return out[:nc].astype(np.int64)

@@ -25,6 +25,8 @@
  *   8. channel level: the channels' lists summed by sort-merge-reduce and
  *      thresholded again                         (§7.1 "Channel Level"; §7.2,
  *                                                the sort-merge-reduce procedure)
+ *   9. station level: thin diagonal clusters with summary statistics
+ *                                                (§7.1 "Station Level"; §7.2)
  *
  * The paper leaves the hash family, hash_combine and the exact filter rule
  * open; the readings fixed here are:
@@ -556,4 +558,125 @@ uint64_t orc_channel_merge(uint32_t nch, const uint64_t *M, const uint32_t *cons
     free(pos);
     free(merged);
     return n;
+}
+
+/* ------------------------------------------------------------------ */
+/* 9. station level (§7.1 "Station Level", §7.2 "Station")             */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Thin diagonal clusters of one station's (combined) similarity matrix, in the
+ * paper's steps:
+ *   runs    along every diagonal dt, the maximal sequences of entries whose
+ *           consecutive idx1 differ by less than `gap` (the largest gap inside
+ *           a sequence is smaller than the gap parameter);
+ *   merge   runs on adjacent diagonals (dt and dt + 1) are merged when their
+ *           idx1 ranges come within `gap` of each other, as long as the merged
+ *           cluster spans at most `width` diagonals (the paper's "relatively
+ *           narrow width");
+ *   summary per cluster: bounding box (dt_min, dt_max, idx1_min, idx1_max),
+ *           number of entries and summed similarity;
+ *   prune   clusters of fewer than `min_n` entries (min_n = 2 drops isolated
+ *           matches).
+ * Readings (the paper leaves them open): the merge is greedy in (dt, idx1)
+ * order of the runs -- each run, taken in that order, joins the first cluster
+ * of the previous diagonal that it comes within `gap` of and that the width
+ * limit lets it join; clusters are reported in (dt_min, idx1_min) order;
+ * gap >= 1.
+ * Input: n entries (i, j, sim) in (dt, idx1) order, dt = j - i, idx1 = i.
+ * Output: 6 uint64 per cluster (dt_min, dt_max, idx1_min, idx1_max, count, sim);
+ * returns the number of clusters, writes at most cap.
+ */
+typedef struct {
+    uint64_t dt, s, e, n, sim; /* one run: diagonal, idx1 range, entries, summed sim */
+    int64_t parent;            /* union-find over runs */
+    uint64_t dt_min, dt_max, s_min, e_max; /* the cluster's box (valid at roots) */
+} orc_run;
+
+static int64_t orc_root(orc_run *r, int64_t x)
+{
+    while (r[x].parent != x) {
+        r[x].parent = r[r[x].parent].parent;
+        x = r[x].parent;
+    }
+    return x;
+}
+
+static int orc_cmp_box(const void *x, const void *y)
+{
+    const uint64_t *a = x, *b = y;
+    if (a[0] != b[0]) return a[0] < b[0] ? -1 : 1;
+    if (a[2] != b[2]) return a[2] < b[2] ? -1 : 1;
+    return 0;
+}
+
+uint64_t orc_station_clusters(const uint32_t *I, const uint32_t *J, const uint16_t *S, uint64_t n, uint32_t gap,
+                              uint32_t width, uint32_t min_n, uint64_t *out, uint64_t cap)
+{
+    /* runs along each diagonal */
+    orc_run *r = malloc(sizeof(orc_run) * (n ? n : 1));
+    uint64_t nr = 0;
+    for (uint64_t k = 0; k < n;) {
+        const uint64_t dt = J[k] - I[k];
+        orc_run run = {dt, I[k], I[k], 0, 0, 0, 0, 0, 0, 0};
+        uint64_t e = k;
+        while (e < n && J[e] - I[e] == dt && (e == k || I[e] - I[e - 1] < gap)) {
+            run.e = I[e];
+            run.n++;
+            run.sim += S[e];
+            e++;
+        }
+        run.parent = (int64_t)nr;
+        run.dt_min = run.dt_max = dt;
+        run.s_min = run.s;
+        run.e_max = run.e;
+        r[nr++] = run;
+        k = e;
+    }
+    /* merge across adjacent diagonals, runs in (dt, idx1) order */
+    uint64_t prev0 = 0; /* first run of diagonal dt - 1 */
+    for (uint64_t x = 0; x < nr; x++) {
+        if (x > 0 && r[x].dt != r[x - 1].dt) {
+            /* the runs of the previous diagonal start where that diagonal started */
+            uint64_t y = x - 1;
+            while (y > 0 && r[y - 1].dt == r[x - 1].dt) y--;
+            prev0 = y;
+        }
+        if (x == 0 || r[prev0].dt + 1 != r[x].dt) continue;
+        for (uint64_t y = prev0; y < nr && r[y].dt == r[x].dt - 1; y++) {
+            const int near = r[y].s <= r[x].e + gap - 1 && r[x].s <= r[y].e + gap - 1;
+            if (!near) continue;
+            const int64_t a = orc_root(r, (int64_t)y), b = orc_root(r, (int64_t)x);
+            if (a == b) continue;
+            const uint64_t lo = r[a].dt_min < r[b].dt_min ? r[a].dt_min : r[b].dt_min;
+            const uint64_t hi = r[a].dt_max > r[b].dt_max ? r[a].dt_max : r[b].dt_max;
+            if (hi - lo + 1 > width) continue;
+            r[b].parent = a; /* x's cluster joins the earlier one */
+            r[a].dt_min = lo;
+            r[a].dt_max = hi;
+            if (r[b].s_min < r[a].s_min) r[a].s_min = r[b].s_min;
+            if (r[b].e_max > r[a].e_max) r[a].e_max = r[b].e_max;
+            r[a].n += r[b].n;
+            r[a].sim += r[b].sim;
+            break; /* the first cluster it comes near */
+        }
+    }
+    /* summaries of the roots, pruned, in (dt_min, idx1_min) order */
+    uint64_t *box = malloc(sizeof(uint64_t) * 6 * (nr ? nr : 1));
+    uint64_t nc = 0;
+    for (uint64_t x = 0; x < nr; x++) {
+        if (r[x].parent != (int64_t)x || r[x].n < min_n) continue;
+        uint64_t *b = box + 6 * nc++;
+        b[0] = r[x].dt_min;
+        b[1] = r[x].dt_max;
+        b[2] = r[x].s_min;
+        b[3] = r[x].e_max;
+        b[4] = r[x].n;
+        b[5] = r[x].sim;
+    }
+    qsort(box, nc, sizeof(uint64_t) * 6, orc_cmp_box);
+    for (uint64_t c = 0; c < nc && c < cap; c++) memcpy(out + 6 * c, box + 6 * c, sizeof(uint64_t) * 6);
+    free(box);
+    free(r);
+    return nc;
 }
