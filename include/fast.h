@@ -74,11 +74,16 @@ typedef enum {
  *             occ_den * size > occ_num * N; a fingerprint in heavy buckets in
  *             more than b/2 tables is dropped.  occ_num = 0 turns it off.
  *   table_group
- *             tables sorted and held at once (0 = all b); votes are merged
- *             across groups (§6.4 "Partition": identical results).
+ *             tables sorted at once by the table build (0 = all b; at most
+ *             b): the tables are radix-sorted table_group at a time straight
+ *             into the table set, so the sort's scratch holds table_group * N
+ *             (key, id) pairs instead of b * N.  The table set itself keeps
+ *             all b tables, and the search counts votes over all of them, so
+ *             the result does not depend on the value (§6.4 "Partition":
+ *             identical results).
  *   query_part
- *             query partitions of the vote map (0 = automatic); identical
- *             results for any value (§6.4).
+ *             query partitions of the pair buffer (0 = automatic: as many as
+ *             the memory left needs); identical results for any value (§6.4).
  */
 typedef struct {
     uint32_t D, K, b, r;
@@ -358,8 +363,22 @@ fast_status fast_stream_latency(fast_server *srv, uint64_t req_id, double *secon
 /* Forgets a finished request and frees its results. */
 fast_status fast_stream_release(fast_server *srv, uint64_t req_id);
 
-/* fast_set_option on every station's context; before any history is loaded. */
+/*
+ * fast_set_option on every station's context; before any history is loaded.
+ * One server setting is also taken here, at any time:
+ *   "admit_timeout_ms"  the longest a request waits for admission (its
+ *                       working set to fit the HBM budget next to the running
+ *                       requests), in [0, 86400000] ms, default 300000; a
+ *                       request still waiting then fails with FAST_ETIMEOUT.
+ */
 fast_status fast_server_set_option(fast_server *srv, const char *name, double value);
+
+/*
+ * Test hook: reserves `bytes` of the admission budget as if a request that
+ * never finishes were running (0 gives it back).  Requests that no longer fit
+ * wait for admission, and fail with FAST_ETIMEOUT once admit_timeout_ms ends.
+ */
+fast_status fast_server_hold_budget(fast_server *srv, uint64_t bytes);
 
 /*
  * Test hook: the request with id req_id fails on the host (FAST_EINTERNAL)
@@ -376,9 +395,9 @@ fast_status fast_server_inject_failure(fast_server *srv, uint64_t req_id);
  * reserved the GPU's memory for its own pools, so any further driver
  * allocation fails or would break its budget), and latency-bound callers for
  * which cudaMalloc's implicit device-wide synchronisation is unacceptable.
- * This entry point gives them the table-construction step of §6.1: it sorts
- * d_keys[0..n) by key, stably, and writes d_skey[k] / d_sid[k] = the k-th
- * (key, original index) pair -- exactly one table of fast_build_tables.
+ * This entry point sorts d_keys[0..n) by key, stably, and writes d_skey[k] /
+ * d_sid[k] = the k-th (key, original index) pair: the same listing as one
+ * table of fast_build_tables.
  *
  * The caller passes the input and both outputs (n uint32 each, device
  * memory, not overlapping).  The scratch (one ping-pong pair of keys and ids
@@ -394,7 +413,9 @@ fast_status fast_server_inject_failure(fast_server *srv, uint64_t req_id);
  *     them.  Every scratch word a call reads is written earlier in the same
  *     call, so nothing left by a previous call leaks into the result.
  * Returns FAST_OK once the work is enqueued on `stream`, FAST_EINVAL for bad
- * arguments, FAST_ECUDA if a CUDA call fails.
+ * arguments, FAST_ECUDA if a CUDA call fails -- also, before anything is
+ * launched, when an error of earlier work is pending on the calling thread
+ * (that error is left in place for the caller to read).
  */
 fast_status fast_table_sort_static(const uint32_t *d_keys, uint64_t n, uint32_t *d_skey, uint32_t *d_sid,
                                    void *stream);

@@ -239,6 +239,13 @@ def station_clusters(i, j, sim, gap: int, width: int, min_n: int):
     j = np.ascontiguousarray(j, dtype=np.uint32)
     sim = np.ascontiguousarray(sim, dtype=np.uint16)
     n = len(i)
+    # the runs are read off consecutive entries: the list must be in (dt, idx1)
+    # order (the search's own (i, j) order would split every run)
+    dt = j.astype(np.int64) - i.astype(np.int64)
+    if n > 1:
+        ddt, di = np.diff(dt), np.diff(i.astype(np.int64))
+        if (ddt < 0).any() or ((ddt == 0) & (di <= 0)).any():
+            raise ValueError("station_clusters needs its entries in strictly increasing (dt, idx1) order")
     out = np.empty((max(1, n), 6), np.uint64)
     nc = _L().orc_station_clusters(_ptr(i), _ptr(j), _ptr(sim), n, gap, width, min_n, _ptr(out), max(1, n))
     return out[:nc].astype(np.int64)

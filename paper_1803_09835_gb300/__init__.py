@@ -206,6 +206,12 @@ class Server:
     def inject_failure(self, req_id: int):
         fast_server_inject_failure(self.srv, req_id)
 
+    def hold_budget(self, nbytes: int):
+        _lib.fast_server_hold_budget(self.srv, nbytes)
+
+    def set_option(self, name: str, value: float):
+        _lib.fast_server_set_option(self.srv, name, value)
+
     def close(self):
         if getattr(self, "srv", None):
             fast_server_destroy(self.srv)

@@ -102,6 +102,7 @@ def load():
         "fast_stream_latency": (st, [vp, u64, pp(ctypes.c_double)]),
         "fast_stream_release": (st, [vp, u64]),
         "fast_server_inject_failure": (st, [vp, u64]),
+        "fast_server_hold_budget": (st, [vp, u64]),
         "fast_server_set_option": (st, [vp, ctypes.c_char_p, ctypes.c_double]),
         "fast_plan_create": (st, [vp, vp, vp, u32, u32, vp, pp(vp)]),
         "fast_plan_run": (st, [vp, vp, vp]),
@@ -337,6 +338,10 @@ def fast_stream_release(srv, req_id: int):
 
 def fast_server_inject_failure(srv, req_id: int):
     _scheck(srv, load().fast_server_inject_failure(srv, req_id))
+
+
+def fast_server_hold_budget(srv, nbytes: int):
+    _scheck(srv, load().fast_server_hold_budget(srv, nbytes))
 
 
 def fast_server_set_option(srv, name: str, value: float):

@@ -107,6 +107,7 @@ static fast_status validate(const fast_params *p, std::string &why) {
     if (p->v < 1 || p->v > p->b) return why = "v must be in [1, b]", FAST_EINVAL;
     if (p->occ_num > 0 && p->occ_den == 0) return why = "occ_den must be > 0 when the filter is on", FAST_EINVAL;
     if (p->query_part > 64) return why = "query_part must be <= 64", FAST_EINVAL;
+    if (p->table_group > p->b) return why = "table_group must be <= b (0 = all b tables)", FAST_EINVAL;
     return FAST_OK;
 }
 
@@ -237,34 +238,48 @@ fast_status build_tables(fast_ctx *c, const uint32_t *d_sig, uint64_t N, const u
     if (h_soff) tb->soff.assign(h_soff, h_soff + nst + 1);
     else tb->soff = {0, N};
     const size_t n = (size_t)nb * N;
+    // table groups (§6.4 "Partition"): the tables are sorted `grp` at a time
+    // into their final place, so the sort's scratch pair holds grp * N
+    // entries instead of b * N; every group's sorted tables are kept
+    const uint32_t grp = c->p.table_group && c->p.table_group < nb ? c->p.table_group : nb;
+    const size_t ns = (size_t)grp * N;
     uint32_t *ka = nullptr, *va = nullptr;
     fast_status st;
     if ((st = dalloc_t(c, &tb->d_soff, nst + 1, s)) || (st = dalloc_t(c, &tb->d_skey, n, s)) ||
         (st = dalloc_t(c, &tb->d_sid, n, s)) || (st = dalloc_t(c, &tb->d_drop, N ? N : 1, s)) ||
-        (st = dalloc_t(c, &ka, n, s)) || (st = dalloc_t(c, &va, n, s))) {
-        dfree(c, ka, n * 4, s);
-        dfree(c, va, n * 4, s);
+        (st = dalloc_t(c, &ka, ns, s)) || (st = dalloc_t(c, &va, ns, s))) {
+        dfree(c, ka, ns * 4, s);
+        dfree(c, va, ns * 4, s);
         fast_tables_free(tb);
         return st;
     }
     if (!c->capturing)  // a captured build gets its offsets uploaded once by the plan
         cudaMemcpyAsync(tb->d_soff, tb->soff.data(), (nst + 1) * 8, cudaMemcpyHostToDevice, s);
-    uint32_t *ko = nullptr, *vo = nullptr;
-    st = sort_u32(c, nb, N, d_sig, nullptr, ka, va, tb->d_skey, tb->d_sid, 0, 32, &ko, &vo, s, &c->stats.sort_passes);
-    if (!st && N && ko != tb->d_skey) {  // odd number of passes: result sits in the scratch pair
-        cudaMemcpyAsync(tb->d_skey, ko, n * 4, cudaMemcpyDeviceToDevice, s);
-        cudaMemcpyAsync(tb->d_sid, vo, n * 4, cudaMemcpyDeviceToDevice, s);
-    }
-    if (!st && N && nst > 1) {  // stable station pass into the scratch pair, which becomes the table
-        st = sort_station_pass(c, nb, N, tb->d_skey, tb->d_sid, ka, va, Stations{tb->d_soff, nst}, s);
-        if (!st) {
-            std::swap(tb->d_skey, ka);
-            std::swap(tb->d_sid, va);
-            c->stats.sort_passes++;
+    c->stats.sort_passes = 0;
+    for (uint32_t t0 = 0; t0 < nb && !st && N; t0 += grp) {
+        const uint32_t gn = std::min(grp, nb - t0);
+        const size_t off = (size_t)t0 * N, m = (size_t)gn * N;
+        uint32_t *dk = tb->d_skey + off, *dv = tb->d_sid + off;
+        uint32_t *ko = nullptr, *vo = nullptr;
+        st = sort_u32(c, gn, N, d_sig + off, nullptr, ka, va, dk, dv, 0, 32, &ko, &vo, s, &c->stats.sort_passes);
+        if (!st && ko != dk) {  // odd number of passes: result sits in the scratch pair
+            cudaMemcpyAsync(dk, ko, m * 4, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(dv, vo, m * 4, cudaMemcpyDeviceToDevice, s);
+        }
+        if (!st && nst > 1) {  // stable station pass into the scratch pair
+            st = sort_station_pass(c, gn, N, dk, dv, ka, va, Stations{tb->d_soff, nst}, s);
+            if (!st && grp == nb) {  // one group: the scratch pair becomes the table
+                std::swap(tb->d_skey, ka);
+                std::swap(tb->d_sid, va);
+            } else if (!st) {
+                cudaMemcpyAsync(dk, ka, m * 4, cudaMemcpyDeviceToDevice, s);
+                cudaMemcpyAsync(dv, va, m * 4, cudaMemcpyDeviceToDevice, s);
+            }
         }
     }
-    dfree(c, ka, n * 4, s);
-    dfree(c, va, n * 4, s);
+    if (nst > 1 && N) c->stats.sort_passes++;
+    dfree(c, ka, ns * 4, s);
+    dfree(c, va, ns * 4, s);
     stage_mark(c, 2, s);
     if (!st) st = filter_launch(c, tb, s);
     stage_mark(c, 9, s);

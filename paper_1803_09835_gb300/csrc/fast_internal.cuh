@@ -284,6 +284,7 @@ struct HistGroups {
 };
 fast_status history_groups(fast_ctx *c, const fast_tables *tb, const uint32_t *d_sig, HistGroups *g, cudaStream_t s);
 uint32_t large_min_for(const fast_ctx *c, uint64_t N);  // the dense-group threshold (option or automatic)
+uint64_t room_bytes(const fast_ctx *c);                 // device memory a call may still take
 struct Scal {  // device scalar slots (ctx->d_scal)
     enum { NBIG, NLARGE, NMEDIUM, NHEAVY, NDROP, NMEMB, CUR_DENSE, CUR_SPARSE, CHANGED, NLONG, NMERGE, NMERGE_TOT,
            NCAND, NMID, SMALLPAIRS, NSMALLEMIT, NSLOW, NOVF, LMAX, PART0 };

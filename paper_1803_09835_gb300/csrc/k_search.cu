@@ -1921,6 +1921,23 @@ uint32_t large_min_for(const fast_ctx *c, uint64_t N) {
     return (uint32_t)std::max(512.0, std::min(1e9, 8.0 * N * ptop));
 }
 
+// Device memory the call may still take: what the HBM budget leaves, or,
+// without a budget, the device's free memory plus what the context's pool
+// holds unused, less a 1 GiB margin.
+uint64_t room_bytes(const fast_ctx *c) {
+    if (c->budget) return c->budget > c->live ? c->budget - c->live : 0;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    uint64_t reserved = 0, used = 0;
+    cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+    cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrUsedMemCurrent, &used);
+    const uint64_t avail = fr + (reserved > used ? reserved - used : 0);
+    return avail > (1ull << 30) ? avail - (1ull << 30) : 0;
+}
+
 // Tiles of 32 table entries per warp for the warp-window passes: enough warps
 // for ~16 resident per SM slot over all tables, at most 64 tiles each.
 static uint32_t tiles_per_warp(const fast_ctx *c, uint64_t N, uint32_t nb) {
@@ -2246,7 +2263,7 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
         if (c->group_slots) cap = c->group_slots;
         const uint64_t ovf_cap = c->group_slots ? S_ub + (1 << 20) : std::max<uint64_t>(1 << 20, S_ub / 8);
         const uint64_t need = ng * cap * 4 + ovf_cap * 16;
-        const uint64_t room = c->budget ? (c->budget > c->live ? (c->budget - c->live) / 2 : 0) : ~0ull;
+        const uint64_t room = room_bytes(c) / 2;
         uint32_t *region = nullptr;
         unsigned long long *ovf = nullptr;
         if (need <= room && !(st = alloc(&region, ng * cap)) && !(st = alloc(&ovf, ovf_cap))) {
@@ -2314,8 +2331,8 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     // pair counts, each written and voted in turn, so the pair buffer holds
     // one range.  As many as query_part asks for, or as the HBM budget needs.
     uint32_t nparts = std::max<uint32_t>(1, p.query_part);
-    if (c->budget && !single) {
-        const uint64_t room = c->budget > c->live ? (c->budget - c->live) / 2 : 0;
+    if (!single) {
+        const uint64_t room = room_bytes(c) / 2;
         const uint64_t need = S * sizeof(PT);
         if (room && need > room) nparts = std::max<uint64_t>(nparts, (need + room - 1) / room);
     }
@@ -2619,7 +2636,11 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
                                                        reinterpret_cast<uint32_t *>(tvotes)), FAST_LAUNCHED(c);
             return FAST_OK;
         };
-        if (nm >= (1u << 24) || nb > 256 || clusters()) {
+        // only a lack of memory (or a group too large for the masks) falls
+        // back to direct comparison; any other failure is the call's error
+        const fast_status cr = nm >= (1u << 24) || nb > 256 ? FAST_EBUDGET : clusters();
+        if (cr && cr != FAST_ENOMEM && cr != FAST_EBUDGET) return fail(cr);
+        if (cr) {
             c->err.clear();
             MB = nullptr;
             cudaMemsetAsync(gover, 0x01, ngroups * 4, s);  // every group by direct comparison
@@ -2640,7 +2661,14 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
     {  // flagged copy of the id lists (made by the counting pass): the pair passes look up drop / label only for flagged ids
         uint32_t *bits = nullptr, *fsid = nullptr;
         const uint64_t n = (uint64_t)nb * N;
-        if ((st = alloc(&bits, (N + 31) / 32)) || (st = alloc(&fsid, n))) return fail(st);
+        if ((st = alloc(&bits, (N + 31) / 32))) return fail(st);
+        // the copy saves the pair passes' bitmap lookups but costs b * N * 4
+        // bytes: it is made only when that is a small part of the memory left
+        // (the pair buffer needs the rest); without it the passes read the bitmap
+        if (n * 16 <= room_bytes(c) && alloc(&fsid, n)) {
+            fsid = nullptr;
+            c->err.clear();
+        }
         k_flag_bits<<<std::max(1u, std::min<unsigned>(ceil_div((N + 31) / 32, 256), c->num_sms * 8)), 256, 0, s>>>(
             tb->d_drop, label, N, bits), FAST_LAUNCHED(c);
         ea.fbits = bits;      // the counting pass fills fsid,

@@ -462,6 +462,10 @@ extern "C" fast_status fast_table_sort_static(const uint32_t *d_keys, uint64_t n
     uint32_t *tmp_v = tmp_k + kStaticMaxKeys;
     uint32_t *counts = reinterpret_cast<uint32_t *>(base + kStaticMaxKeys * 8);
     uint64_t *offs = reinterpret_cast<uint64_t *>(base + kStaticMaxKeys * 8 + kStaticCountsBytes);
+    // an error left pending by earlier work of the caller is reported (and
+    // left in place for the caller) before anything is launched, so that the
+    // check after the launches below sees only this call's own launch errors
+    if (cudaPeekAtLastError() != cudaSuccess) return FAST_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t nchunks = (uint32_t)((n + kChunk - 1) / kChunk);
     const dim3 grid(nchunks, 1);

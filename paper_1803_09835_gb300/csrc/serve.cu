@@ -17,6 +17,8 @@
 // Requests of one station run in admission order, so request q sees history,
 // every earlier batch of its station and itself; stations run concurrently,
 // each on its own stream, as HBM budget admits them.
+#include <string.h>
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -385,6 +387,8 @@ struct fast_server {
     uint64_t next_req = 1;
     std::atomic<bool> stop{false};
     std::atomic<uint64_t> fail_at{0};  // host-side fault injection: request id that fails
+    std::atomic<uint64_t> admit_ms{300000};  // longest admission wait of one request (ms)
+    uint64_t held = 0;                       // budget bytes held by the test hook (under adm_mu)
     int device = 0;
     std::string err;
 };
@@ -611,22 +615,30 @@ void worker_main(fast_server *S, fast_station *st) {
             res = FAST_EBUDGET;
             msg = "request can never fit the HBM budget";
         } else {
-            {   // admission: wait until the request's working set fits next to the running ones
+            bool admitted = false;
+            {   // admission: wait, at most admit_ms, until the request's working
+                // set fits next to the running ones
                 std::unique_lock<std::mutex> lk(S->adm_mu);
-                S->adm_cv.wait(lk, [&] {
+                const auto until = std::chrono::steady_clock::now() + std::chrono::milliseconds(S->admit_ms.load());
+                admitted = S->adm_cv.wait_until(lk, until, [&] {
                     return S->stop.load() || !S->budget || S->resident + S->in_flight.load() + need <= S->budget;
                 });
-                S->in_flight += need;
+                if (admitted) S->in_flight += need;
             }
-            if (S->stop.load()) {
+            if (!admitted) {
                 res = FAST_ETIMEOUT;
-                msg = "server stopped";
+                msg = "admission wait ran out: the HBM budget did not free up in time";
             } else {
-                res = process(S, st, work);
-                if (res) msg = st->ctx->err;
+                if (S->stop.load()) {
+                    res = FAST_ETIMEOUT;
+                    msg = "server stopped";
+                } else {
+                    res = process(S, st, work);
+                    if (res) msg = st->ctx->err;
+                }
+                S->in_flight -= need;
+                S->adm_cv.notify_all();
             }
-            S->in_flight -= need;
-            S->adm_cv.notify_all();
         }
         if (grp.size() > 1 && !res) {  // each request takes the pairs whose j lies in its windows
             for (fast_request *q : grp) {
@@ -875,6 +887,14 @@ fast_status fast_stream_release(fast_server *S, uint64_t req_id) {
 
 fast_status fast_server_set_option(fast_server *S, const char *name, double value) {
     if (!S || !name) return FAST_EINVAL;
+    if (!strcmp(name, "admit_timeout_ms")) {  // a server setting, allowed at any time
+        if (!(value >= 0 && value <= 86400e3)) {
+            S->err = "admit_timeout_ms must be in [0, 86400000]";
+            return FAST_EINVAL;
+        }
+        S->admit_ms = (uint64_t)value;
+        return FAST_OK;
+    }
     for (auto *sn : S->st) {
         std::lock_guard<std::mutex> lk(sn->mu);
         if (sn->loaded) {
@@ -889,6 +909,18 @@ fast_status fast_server_set_option(fast_server *S, const char *name, double valu
             return st;
         }
     }
+    return FAST_OK;
+}
+
+fast_status fast_server_hold_budget(fast_server *S, uint64_t bytes) {
+    if (!S) return FAST_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(S->adm_mu);
+        S->in_flight -= S->held;
+        S->in_flight += bytes;
+        S->held = bytes;
+    }
+    S->adm_cv.notify_all();
     return FAST_OK;
 }
 

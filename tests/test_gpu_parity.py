@@ -105,6 +105,12 @@ DETECT_CASES = [
     ("c1", 30_000, dict(occ_num=0), dict(large_min=10**9)),   # no dense groups: long rows per fingerprint
     ("c4", 50_000, dict(), dict()),                           # C4 shape: 30/60/90/3600 s sources, 200-repeat templates
     ("c4", 50_000, dict(query_part=5), dict(large_min=32)),   # C4 shape, five row partitions, dense groups
+    # table groups (§6.4): tables sorted g at a time, votes over all of them
+    ("c4", 50_000, dict(table_group=1), dict()),
+    ("c4", 50_000, dict(table_group=3, query_part=5), dict()),
+    ("c4", 50_000, dict(table_group=10), dict(large_min=32)),
+    ("c4", 50_000, dict(table_group=10, query_part=5), dict()),
+    ("c1", 20_000, dict(table_group=7), dict(single_pass=0)),  # 100 = 14 x 7 + 2: a short last group
 ]
 
 
@@ -112,9 +118,10 @@ DETECT_CASES = [
 def test_detections_bit_exact(name, n, over, opts):
     over = dict(over)
     qp = over.pop("query_part", 0)
+    tg = over.pop("table_group", 0)
     w = synth.scaled(name, n, **over)
     idx = synth.generate(w, ld=_pad(w.K))
-    p = dict(w.params(), query_part=qp)
+    p = dict(w.params(), query_part=qp, table_group=tg)
     s = _searcher(p, **opts)
     res = s.detect(torch.from_numpy(idx).cuda())
     got = res.numpy()
@@ -290,7 +297,7 @@ def test_bad_index_is_reported_and_context_survives():
 
 
 @pytest.mark.parametrize("bad", [dict(b=0), dict(b=256), dict(v=17), dict(r=0), dict(K=3000), dict(kind=2),
-                                 dict(occ_num=1, occ_den=0), dict(D=70000)])
+                                 dict(occ_num=1, occ_den=0), dict(D=70000), dict(table_group=17)])
 def test_invalid_parameters(bad):
     from paper_1803_09835_gb300 import FastError
     with pytest.raises(FastError):

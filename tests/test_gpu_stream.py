@@ -147,3 +147,37 @@ def test_dense_groups_in_requests_stay_exact():
         for s in range(2):
             for q in range(len(SIZES)):
                 assert _same(got[s][q][1:], want[s][q]), f"large_min {lm} station {s} request {q}"
+
+
+def test_admission_wait_is_bounded_and_short_polls_pend():
+    # A request whose working set can never be admitted (the whole budget is
+    # held by the test hook, as if by a request that never ends) stays
+    # pending, then fails with FAST_ETIMEOUT when the admission wait runs out;
+    # all of it on the host, nothing on the GPU waits.  Released, the budget
+    # admits the next request again.
+    import time
+
+    from paper_1803_09835_gb300 import FastError, _lib
+    w, idx = _station(9)
+    p = w.params()
+    budget = 64 << 20
+    srv = _server(p, 1, hbm_budget_bytes=budget)
+    srv.load_history(0, idx[:N0])
+    sl = _slices(idx)
+    srv.set_option("admit_timeout_ms", 400)
+    srv.hold_budget(budget)
+    t0 = time.perf_counter()
+    r0 = srv.submit(0, sl[0])
+    assert srv.poll(r0, 0.0) is None            # FAST_EPENDING at once
+    assert srv.poll(r0, 0.001) is None          # and after a 1 ms wait
+    with pytest.raises(FastError) as e:
+        srv.wait(r0, timeout_s=60.0)
+    assert e.value.status == _lib.FAST_ETIMEOUT
+    assert 0.35 < time.perf_counter() - t0 < 30.0
+    srv.hold_budget(0)
+    first, i, j, v = srv.wait(srv.submit(0, sl[1]), timeout_s=60.0)
+    assert first == N0 + SIZES[0]               # ids continue the station timeline
+    assert np.all(j >= first) and np.all(i < j)
+    with pytest.raises(FastError):
+        srv.set_option("admit_timeout_ms", -1)
+    srv.close()

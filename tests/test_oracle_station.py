@@ -110,6 +110,23 @@ def test_width_limit_splits_a_wide_staircase():
     assert two.tolist() == [[100, 102, 1000, 1002, 3, 3], [103, 105, 1003, 1005, 3, 3]]
 
 
+def test_rejects_lists_not_in_diagonal_order():
+    # the search's canonical (i, j) order is not (dt, idx1) order: such a list
+    # (and one with a repeated entry) is refused instead of silently giving
+    # split runs
+    i = np.array([5, 5, 6], np.uint32)
+    j = np.array([20, 30, 21], np.uint32)
+    s = np.ones(3, np.uint16)
+    with pytest.raises(ValueError):
+        oracle.station_clusters(i, j, s, gap=3, width=2, min_n=1)
+    with pytest.raises(ValueError):
+        oracle.station_clusters(np.array([5, 5], np.uint32), np.array([20, 20], np.uint32),
+                                np.ones(2, np.uint16), gap=3, width=2, min_n=1)
+    o = np.lexsort((i, j - i))
+    assert oracle.station_clusters(i[o], j[o], s[o], gap=3, width=2, min_n=1).tolist() == [[15, 15, 5, 6, 2, 2],
+                                                                                          [25, 25, 5, 5, 1, 1]]
+
+
 def test_empty_and_bad_arguments():
     e = np.zeros(0, np.uint32)
     assert oracle.station_clusters(e, e, np.zeros(0, np.uint16), gap=3, width=2, min_n=1).shape == (0, 6)

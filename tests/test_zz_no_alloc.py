@@ -4,13 +4,16 @@ fast_table_sort_static serves callers that cannot let the library allocate
 device memory (hosts that reserve the GPU's memory for their own pools, or
 cannot afford cudaMalloc's implicit synchronisation).  It must give exactly
 the listing one table of fast_build_tables gives, call after call, although
-every call reuses the same fixed scratch array.
+every call reuses the same fixed scratch array.  Both calls are also
+compared with the oracle's canonical table listing.
 """
 import ctypes
 
 import numpy as np
 import pytest
 import torch
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -59,6 +62,9 @@ def test_static_scratch_sort_matches_table_build(lib):
         assert st == 0
         want_k, want_s = _reference_table(kd, n)
         assert np.array_equal(skey, want_k) and np.array_equal(sid, want_s)
+        # and against the oracle's canonical table listing (key, then id)
+        ok, oid = oracle.table(keys)
+        assert np.array_equal(skey, ok) and np.array_equal(sid, oid)
 
 
 def test_static_scratch_sort_rejects_oversize(lib):
