@@ -156,6 +156,20 @@ fast_status fast_sig(fast_ctx *ctx, const uint16_t *d_idx, uint64_t N, uint32_t 
                      void *stream);
 
 /*
+ * Signatures of a station too large to hold its fingerprints in device
+ * memory at once (§6.1 "Hash signature generation", Algorithm 1; §6.4
+ * "Partition"), fed in chunks: d_idx holds n rows (ld >= K uint16 each) that
+ * are windows col0 .. col0 + n - 1 of a station of N windows; their keys go
+ * to d_sig[t*N + col0 + k] of the caller's [b][N] key array (caller-allocated,
+ * device).  col0 + n <= N.  Enqueues the work on `stream` and returns without
+ * synchronising, so the caller may refill another chunk buffer meanwhile; an
+ * index >= D is reported as FAST_EINVAL by the next call on the context that
+ * synchronises (fast_build_tables on these keys does).
+ */
+fast_status fast_sig_rows(fast_ctx *ctx, const uint16_t *d_idx, uint64_t n, uint32_t ld, uint32_t *d_sig, uint64_t N,
+                          uint64_t col0, void *stream);
+
+/*
  * Hash-table construction (§6.1 "Hash table construction") and the
  * occurrence filter (§6.5).  Reads d_sig (b*N, table-major, as written by
  * fast_sig) and builds, per table, the (key, id) pairs stably sorted by key
@@ -253,6 +267,25 @@ void fast_plan_destroy(fast_plan *plan);
  */
 fast_status fast_detect_host(fast_ctx *ctx, const uint16_t *h_idx, uint64_t N, uint32_t ld, uint64_t *M,
                              uint32_t *h_i, uint32_t *h_j, uint8_t *h_votes, uint64_t cap, void *stream);
+
+/*
+ * The whole path over a station whose fingerprints are produced in chunks by
+ * the caller (§6.4 "Partition": a long station's data need not be held at
+ * once): fill(user, row0, n, ld, h_rows) must write windows row0 .. row0+n-1
+ * (n rows of ld uint16, ld >= K) into the pinned host buffer h_rows and
+ * return 0 (non-zero aborts the call with FAST_EINVAL).  The library calls
+ * it for consecutive chunks of chunk_rows windows (the last may be shorter),
+ * on the calling thread, while the previous chunk is copied and signed on
+ * the device: only two chunks of input are ever held, on the host and on the
+ * device.  Then builds the tables (table_group at a time) and searches, as
+ * fast_detect does; *out as fast_detect gives.  N < 2^28.  The staging
+ * buffers (2 * chunk_rows * ld * 2 bytes of pinned host memory) are kept by
+ * the context for later calls.  Synchronises `stream`.
+ */
+typedef int (*fast_fill_rows)(void *user, uint64_t row0, uint64_t n, uint32_t ld, uint16_t *h_rows);
+
+fast_status fast_detect_chunked(fast_ctx *ctx, uint64_t N, uint32_t ld, uint64_t chunk_rows, fast_fill_rows fill,
+                                void *user, fast_result **out, void *stream);
 
 /*
  * Device views of a result: *M detections as three arrays (structure of
@@ -385,6 +418,69 @@ fast_status fast_server_hold_budget(fast_server *srv, uint64_t bytes);
  * instead of running; every other request is unaffected.
  */
 fast_status fast_server_inject_failure(fast_server *srv, uint64_t req_id);
+
+/* ------------------------------------------------------------------ */
+/* Alignment: the steps that take the search's output (§7)             */
+/* ------------------------------------------------------------------ */
+typedef struct fast_merged fast_merged;
+typedef struct fast_clusters fast_clusters;
+
+/*
+ * Channel level (§7.1 "Channel Level"; §7.2, the sort-merge-reduce
+ * procedure): the similarity lists of nch channels of one station are summed
+ * per pair and the pairs whose summed votes reach thr are kept ("a slightly
+ * higher similarity threshold on the combined similarity matrix").
+ *   N          windows of the station: every id of every list is < N;
+ *              2 <= N <= 2^28.
+ *   nch        channels, 1..256; channel c has h_M[c] entries d_i[c][k],
+ *              d_j[c][k], d_votes[c][k] (device arrays; h_M, d_i, d_j,
+ *              d_votes are host arrays of nch entries), each with i < j and
+ *              each pair at most once per channel (a fast_search result
+ *              qualifies, in any order).
+ * *out receives the kept pairs (i, j, sim), sim the summed votes (16 bits),
+ * in the paper's merged order: dt = j - i ascending, then idx1 = i
+ * ascending.  An entry with j <= i or j >= N makes the call fail with
+ * FAST_EINVAL.  Synchronises `stream`.  The inputs are not modified.
+ */
+fast_status fast_channel_merge(fast_ctx *ctx, uint64_t N, uint32_t nch, const uint64_t *h_M,
+                               const uint32_t *const *d_i, const uint32_t *const *d_j,
+                               const uint8_t *const *d_votes, uint32_t thr, fast_merged **out, void *stream);
+
+/* Device views of a merged list: *M entries as three arrays.  Any out-pointer may be NULL. */
+fast_status fast_merged_view(const fast_merged *res, uint64_t *M, const uint32_t **d_i, const uint32_t **d_j,
+                             const uint16_t **d_sim);
+
+void fast_merged_free(fast_merged *res);
+
+/*
+ * Station level (§7.1 "Station Level"; §7.2 "Station"): thin diagonal
+ * clusters of a station's combined similarity list, each reduced to summary
+ * statistics, small ones pruned.
+ *   Input: n entries (d_i, d_j, d_sim; device arrays) in strictly increasing
+ *   (dt = j - i, idx1 = i) order, as fast_channel_merge returns them;
+ *   n < 2^32 - 1.  Otherwise the call fails with FAST_EINVAL.
+ *   runs     along every diagonal dt, the maximal sequences of entries whose
+ *            consecutive idx1 differ by less than `gap` (gap >= 1);
+ *   merge    each run, in (dt, idx1) order, joins the first cluster on
+ *            diagonal dt - 1 it comes within `gap` of (idx1 ranges
+ *            [s, e] and [s', e'] are near when s <= e' + gap - 1 and
+ *            s' <= e + gap - 1) if the joined cluster then spans at most
+ *            `width` diagonals (width >= 1), else it starts its own;
+ *   summary  per cluster: dt_min, dt_max, idx1_min, idx1_max (idx1 of the
+ *            first and last entry of its runs), entries, summed sim;
+ *   prune    clusters of fewer than min_n entries are dropped.
+ * *out receives 6 uint64 per cluster in that order, clusters in
+ * (dt_min, idx1_min) order (ties in the order of their first runs).
+ * Synchronises `stream`.
+ */
+fast_status fast_station_clusters(fast_ctx *ctx, const uint32_t *d_i, const uint32_t *d_j, const uint16_t *d_sim,
+                                  uint64_t n, uint32_t gap, uint32_t width, uint32_t min_n, fast_clusters **out,
+                                  void *stream);
+
+/* Device view of the clusters: *n rows of 6 uint64. */
+fast_status fast_clusters_view(const fast_clusters *res, uint64_t *n, const uint64_t **d_box);
+
+void fast_clusters_free(fast_clusters *res);
 
 /*
  * One table's stable (key, id) sort without any device allocation.

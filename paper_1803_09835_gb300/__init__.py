@@ -21,7 +21,7 @@ from ._lib import (FAST_MINHASH, FAST_MINMAX, FastError, fast_build_tables, fast
                    fast_set_option, fast_sig, fast_stream_latency, fast_stream_poll, fast_stream_release,
                    fast_stream_submit, fast_tables_free, fast_tables_view)
 
-__all__ = ["Searcher", "Plan", "Result", "Tables", "FastError", "FAST_MINHASH", "FAST_MINMAX", "fast_create", "fast_destroy",
+__all__ = ["Searcher", "Plan", "Result", "Merged", "Clusters", "Tables", "FastError", "FAST_MINHASH", "FAST_MINMAX", "fast_create", "fast_destroy",
            "fast_sig", "fast_build_tables", "fast_tables_view", "fast_tables_free", "fast_search", "fast_detect",
            "fast_detect_host", "fast_result_view", "fast_result_free", "fast_get_stats", "fast_set_option", "Server",
            "fast_server_create", "fast_server_destroy", "fast_server_load_history", "fast_stream_submit",
@@ -43,6 +43,52 @@ class Result:
     def free(self):
         if self.handle:
             fast_result_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Merged:
+    """A channel-merged list (i, j, summed votes) in (dt, idx1) order, in device memory."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self.M, self.i, self.j, self.sim = _lib.fast_merged_view(handle, owner=self)
+
+    def numpy(self):
+        """(i, j, sim) as numpy uint32 / uint32 / uint16 arrays."""
+        return (self.i.cpu().numpy().view(np.uint32), self.j.cpu().numpy().view(np.uint32),
+                self.sim.cpu().numpy().view(np.uint16))
+
+    def free(self):
+        if self.handle:
+            _lib.fast_merged_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Clusters:
+    """Station-level clusters: rows (dt_min, dt_max, idx1_min, idx1_max, entries, sim)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self.n, self.box = _lib.fast_clusters_view(handle, owner=self)
+
+    def numpy(self):
+        return self.box.cpu().numpy().reshape(-1, 6)
+
+    def free(self):
+        if self.handle:
+            _lib.fast_clusters_free(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -107,6 +153,11 @@ class Searcher:
         fast_sig(self.ctx, idx, N, ld, out, stream)
         return out
 
+    def sig_rows(self, idx, sig, col0: int, stream=None):
+        """Keys of rows col0 .. col0 + n - 1 of a station into its [b, N] key array (chunked input)."""
+        n, ld = idx.shape
+        _lib.fast_sig_rows(self.ctx, idx, n, ld, sig, sig.shape[1], col0, stream)
+
     def build_tables(self, sig, stream=None) -> Tables:
         return Tables(fast_build_tables(self.ctx, sig, sig.shape[1], stream), sig)
 
@@ -116,6 +167,11 @@ class Searcher:
     def detect(self, idx, stream=None) -> Result:
         N, ld = idx.shape
         return Result(fast_detect(self.ctx, idx, N, ld, stream))
+
+    def detect_chunked(self, N: int, ld: int, fill, chunk_rows: int = 1 << 22, stream=None) -> Result:
+        """Whole path over a station produced chunk by chunk: fill(row0, n, rows)
+        writes windows row0 .. row0 + n - 1 into the [n, ld] uint16 array rows."""
+        return Result(_lib.fast_detect_chunked(self.ctx, N, ld, chunk_rows, fill, stream))
 
     def detect_batch(self, idx, station_N, stream=None):
         """Several stations in one pass: idx holds their rows one after another."""
@@ -139,6 +195,16 @@ class Searcher:
 
     def stats(self) -> dict:
         return fast_get_stats(self.ctx)
+
+    def channel_merge(self, results, N: int, thr: int, stream=None) -> Merged:
+        """Channel level: the channels' Results summed per pair, kept at >= thr."""
+        lists = [(r.M, r.i, r.j, r.votes) for r in results]
+        return Merged(_lib.fast_channel_merge(self.ctx, N, lists, thr, stream))
+
+    def station_clusters(self, merged, gap: int, width: int, min_n: int, stream=None) -> Clusters:
+        """Station level over a (dt, idx1)-ordered list (a Merged, or (i, j, sim) device tensors)."""
+        i, j, sim = (merged.i, merged.j, merged.sim) if isinstance(merged, Merged) else merged
+        return Clusters(_lib.fast_station_clusters(self.ctx, i, j, sim, i.shape[0], gap, width, min_n, stream))
 
 
 class Plan:

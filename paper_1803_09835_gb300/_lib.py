@@ -64,6 +64,10 @@ class fast_plan_info_t(ctypes.Structure):
 
 _lib = None
 
+# int fill(void *user, uint64_t row0, uint64_t n, uint32_t ld, uint16_t *h_rows)
+FILL_ROWS = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                             ctypes.c_void_p)
+
 
 def load():
     """Loads libfast.so (built by ``__graft_entry__.build()``); raises if absent."""
@@ -81,6 +85,8 @@ def load():
         "fast_destroy": (None, [vp]),
         "fast_last_error": (ctypes.c_char_p, [vp]),
         "fast_sig": (st, [vp, vp, u64, u32, vp, vp]),
+        "fast_sig_rows": (st, [vp, vp, u64, u32, vp, u64, u64, vp]),
+        "fast_detect_chunked": (st, [vp, u64, u32, u64, FILL_ROWS, vp, pp(vp), vp]),
         "fast_build_tables": (st, [vp, vp, u64, pp(vp), vp]),
         "fast_tables_view": (st, [vp, pp(u64), pp(u32), pp(vp), pp(vp), pp(vp)]),
         "fast_tables_free": (None, [vp]),
@@ -103,6 +109,12 @@ def load():
         "fast_stream_release": (st, [vp, u64]),
         "fast_server_inject_failure": (st, [vp, u64]),
         "fast_server_hold_budget": (st, [vp, u64]),
+        "fast_channel_merge": (st, [vp, u64, u32, vp, vp, vp, vp, u32, pp(vp), vp]),
+        "fast_merged_view": (st, [vp, pp(u64), pp(vp), pp(vp), pp(vp)]),
+        "fast_merged_free": (None, [vp]),
+        "fast_station_clusters": (st, [vp, vp, vp, vp, u64, u32, u32, u32, pp(vp), vp]),
+        "fast_clusters_view": (st, [vp, pp(u64), pp(vp)]),
+        "fast_clusters_free": (None, [vp]),
         "fast_server_set_option": (st, [vp, ctypes.c_char_p, ctypes.c_double]),
         "fast_plan_create": (st, [vp, vp, vp, u32, u32, vp, pp(vp)]),
         "fast_plan_run": (st, [vp, vp, vp]),
@@ -158,7 +170,7 @@ class _DevArray:
 def _view(ptr, n, typestr, owner):
     import torch
     if n == 0:
-        dt = {"<i4": torch.int32, "|u1": torch.uint8}[typestr]
+        dt = {"<i4": torch.int32, "|u1": torch.uint8, "<i2": torch.int16, "<i8": torch.int64}[typestr]
         return torch.empty(0, dtype=dt, device="cuda")
     return torch.as_tensor(_DevArray(ptr, n, typestr, owner), device="cuda")
 
@@ -208,6 +220,34 @@ def fast_tables_free(tb):
     load().fast_tables_free(tb)
 
 
+def fast_sig_rows(ctx, d_idx, n: int, ld: int, d_sig, N: int, col0: int, stream=None):
+    _check(ctx, load().fast_sig_rows(ctx, _dptr(d_idx), n, ld, _dptr(d_sig), N, col0, _stream(stream)))
+
+
+def fast_detect_chunked(ctx, N: int, ld: int, chunk_rows: int, fill, stream=None):
+    """fill(row0, n, rows) writes windows row0 .. row0 + n - 1 into the
+    [n, ld] uint16 numpy view `rows` of the library's pinned staging buffer."""
+    import numpy as np
+    err = []
+
+    def cb(_user, row0, n, ld_, ptr):
+        try:
+            rows = np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ctypes.c_uint16)), (n, ld_))
+            fill(row0, n, rows)
+            return 0
+        except Exception as e:  # reported as the call's failure
+            err.append(e)
+            return 1
+
+    fn = FILL_ROWS(cb)
+    out = ctypes.c_void_p()
+    st = load().fast_detect_chunked(ctx, N, ld, chunk_rows, fn, None, ctypes.byref(out), _stream(stream))
+    if err:
+        raise err[0]
+    _check(ctx, st)
+    return out
+
+
 def fast_search(ctx, tb, stream=None):
     out = ctypes.c_void_p()
     _check(ctx, load().fast_search(ctx, tb, ctypes.byref(out), _stream(stream)))
@@ -239,6 +279,53 @@ def fast_result_view(res, owner=None):
 
 def fast_result_free(res):
     load().fast_result_free(res)
+
+
+def fast_channel_merge(ctx, N: int, lists, thr: int, stream=None):
+    """lists: per channel (M, d_i, d_j, d_votes), device tensors (int32 views
+    of uint32 ids, uint8 votes)."""
+    nch = len(lists)
+    arr = ctypes.c_void_p * max(1, nch)
+    M = (ctypes.c_uint64 * max(1, nch))(*[int(m) for m, _, _, _ in lists])
+    cols = [[(l[k + 1].data_ptr() if int(l[0]) else None) for l in lists] for k in range(3)]  # i, j, votes
+    ptrs = [arr(*col) for col in cols]
+    out = ctypes.c_void_p()
+    _check(ctx, load().fast_channel_merge(ctx, N, nch, M, ctypes.cast(ptrs[0], ctypes.c_void_p),
+                                          ctypes.cast(ptrs[1], ctypes.c_void_p), ctypes.cast(ptrs[2], ctypes.c_void_p),
+                                          thr, ctypes.byref(out), _stream(stream)))
+    return out
+
+
+def fast_merged_view(res, owner=None):
+    """(M, i [M] int32 view, j [M] int32 view, sim [M] int16 view of uint16)."""
+    M = ctypes.c_uint64()
+    i, j, v = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(None, load().fast_merged_view(res, ctypes.byref(M), ctypes.byref(i), ctypes.byref(j), ctypes.byref(v)))
+    m = M.value
+    return m, _view(i.value, m, "<i4", owner), _view(j.value, m, "<i4", owner), _view(v.value, m, "<i2", owner)
+
+
+def fast_merged_free(res):
+    load().fast_merged_free(res)
+
+
+def fast_station_clusters(ctx, d_i, d_j, d_sim, n: int, gap: int, width: int, min_n: int, stream=None):
+    out = ctypes.c_void_p()
+    _check(ctx, load().fast_station_clusters(ctx, _dptr(d_i), _dptr(d_j), _dptr(d_sim), n, gap, width, min_n,
+                                             ctypes.byref(out), _stream(stream)))
+    return out
+
+
+def fast_clusters_view(res, owner=None):
+    """(n, boxes [n * 6] int64 view)."""
+    n = ctypes.c_uint64()
+    b = ctypes.c_void_p()
+    _check(None, load().fast_clusters_view(res, ctypes.byref(n), ctypes.byref(b)))
+    return n.value, _view(b.value, 6 * n.value, "<i8", owner)
+
+
+def fast_clusters_free(res):
+    load().fast_clusters_free(res)
 
 
 def fast_get_stats(ctx) -> dict:

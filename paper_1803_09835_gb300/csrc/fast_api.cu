@@ -72,6 +72,7 @@ fast_status sync_check(fast_ctx *c, cudaStream_t s, const char *where) {
     if (flags & ERR_WALK) return set_error(c, FAST_EINVAL, w + ": fingerprint with no valid index");
     if (flags & ERR_MAP_FULL) return set_error(c, FAST_EMAPFULL, w + ": vote map probe limit reached");
     if (flags & ERR_OVERFLOW) return set_error(c, FAST_EINTERNAL, w + ": device list capacity exceeded");
+    if (flags & ERR_INPUT) return set_error(c, FAST_EINVAL, w + ": input list out of order or out of range");
     return set_error(c, FAST_EINTERNAL, w + ": device error flag " + std::to_string(flags));
 }
 
@@ -198,6 +199,10 @@ void fast_destroy(fast_ctx *c) {
         if (ev) cudaEventDestroy(ev);
     for (auto &ev : c->cev)
         if (ev) cudaEventDestroy(ev);
+    for (auto &ev : c->chev)
+        if (ev) cudaEventDestroy(ev);
+    for (auto *h : c->h_stage)
+        if (h) cudaFreeHost(h);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     cudaGetLastError();
@@ -215,6 +220,19 @@ fast_status fast_sig(fast_ctx *c, const uint16_t *d_idx, uint64_t N, uint32_t ld
     fast_status st = sig_launch(c, d_idx, N, ld, d_sig, s);
     if (st) return st;
     return sync_check(c, s, "fast_sig");
+}
+
+fast_status fast_sig_rows(fast_ctx *c, const uint16_t *d_idx, uint64_t n, uint32_t ld, uint32_t *d_sig, uint64_t N,
+                          uint64_t col0, void *stream) {
+    if (!c) return FAST_EINVAL;
+    c->err.clear();
+    if ((n && (!d_idx || !d_sig)) || ld < c->p.K || col0 > N || n > N - col0)
+        return set_error(c, FAST_EINVAL, "fast_sig_rows: bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    fast_status st = sig_launch_rows(c, d_idx, n, ld, d_sig + col0, N, s);
+    if (st) return st;
+    cudaError_t e = cudaGetLastError();
+    return e ? cuda_fail(c, e, "fast_sig_rows") : FAST_OK;
 }
 
 }  // extern "C"
@@ -534,6 +552,82 @@ fast_status fast_detect_host(fast_ctx *c, const uint16_t *h_idx, uint64_t N, uin
     st = sync_check(c, s, "fast_detect_host copy-out");
     fast_result_free(res);
     return st;
+}
+
+fast_status fast_detect_chunked(fast_ctx *c, uint64_t N, uint32_t ld, uint64_t chunk_rows, fast_fill_rows fill,
+                                void *user, fast_result **out, void *stream) {
+    if (!c || !out) return FAST_EINVAL;
+    c->err.clear();
+    *out = nullptr;
+    if (!fill || ld < c->p.K || chunk_rows == 0) return set_error(c, FAST_EINVAL, "fast_detect_chunked: bad arguments");
+    if (N > (1ull << 28) - 1) return set_error(c, FAST_EINVAL, "N must be < 2^28");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (!c->copy_stream && (e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking)))
+        return cuda_fail(c, e, "copy stream");
+    for (auto &ev : c->chev)
+        if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming))) return cuda_fail(c, e, "chunk events");
+    chunk_rows = std::min<uint64_t>(chunk_rows, std::max<uint64_t>(N, 1));
+    const size_t cbytes = (size_t)chunk_rows * ld * 2;
+    if (c->h_stage_bytes < cbytes) {  // pinned staging, kept for later calls
+        for (auto *&h : c->h_stage) {
+            if (h) cudaFreeHost(h);
+            h = nullptr;
+        }
+        c->h_stage_bytes = 0;
+        for (auto *&h : c->h_stage)
+            if ((e = cudaMallocHost(&h, cbytes))) return cuda_fail(c, e, "pinned staging");
+        c->h_stage_bytes = cbytes;
+    }
+    g_marked = 0;
+    c->stats.n_launches = 0;
+    c->peak = c->live;
+    stage_mark(c, 0, s);
+    uint32_t *sig = nullptr;
+    uint16_t *d_chunk[2] = {};
+    const size_t nsig = (size_t)c->p.b * N;
+    fast_status st = dalloc_t(c, &sig, nsig ? nsig : 1, s);
+    if (!st) st = dalloc(c, (void **)&d_chunk[0], cbytes, s);
+    if (!st) st = dalloc(c, (void **)&d_chunk[1], cbytes, s);
+    if (!st) {
+        cudaEventRecord(c->chev[2], s);  // the buffers' allocations, ordered on s
+        cudaStreamWaitEvent(c->copy_stream, c->chev[2], 0);
+        cudaEventRecord(c->chev[3], s);
+    }
+    // chunk k: filled on the host into staging buffer k % 2 (once that
+    // buffer's previous copy is done), copied on the copy stream (once the
+    // signature kernel of chunk k - 2 has read the device buffer), signed on s
+    for (uint64_t r0 = 0, k = 0; r0 < N && !st; r0 += chunk_rows, k++) {
+        const int b = (int)(k & 1);
+        const uint64_t n = std::min<uint64_t>(chunk_rows, N - r0);
+        if (k >= 2 && (e = cudaEventSynchronize(c->chev[b]))) {
+            st = cuda_fail(c, e, "chunk copy");
+            break;
+        }
+        if (fill(user, r0, n, ld, c->h_stage[b]) != 0) {
+            st = set_error(c, FAST_EINVAL, "fast_detect_chunked: the fill callback failed at row " + std::to_string(r0));
+            break;
+        }
+        if (k >= 2) cudaStreamWaitEvent(c->copy_stream, c->chev[2 + b], 0);
+        cudaMemcpyAsync(d_chunk[b], c->h_stage[b], n * ld * 2, cudaMemcpyHostToDevice, c->copy_stream);
+        cudaEventRecord(c->chev[b], c->copy_stream);
+        cudaStreamWaitEvent(s, c->chev[b], 0);
+        st = sig_launch_rows(c, d_chunk[b], n, ld, sig + r0, N, s);
+        cudaEventRecord(c->chev[2 + b], s);
+    }
+    dfree(c, d_chunk[0], cbytes, s);
+    dfree(c, d_chunk[1], cbytes, s);
+    stage_mark(c, 1, s);
+    if (!st) st = detect_from_sig(c, sig, N, out, s);
+    dfree(c, sig, nsig * 4, s);
+    if (st) {
+        cudaStreamSynchronize(c->copy_stream);  // no copy may still read the staging buffers
+        return st;
+    }
+    stats_times(c, true);
+    c->stats.n_fingerprints = N;
+    c->stats.peak_bytes = c->peak;
+    return FAST_OK;
 }
 
 fast_status fast_result_view(const fast_result *r, uint64_t *M, const uint32_t **d_i, const uint32_t **d_j,

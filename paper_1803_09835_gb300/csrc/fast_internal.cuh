@@ -64,6 +64,7 @@ enum : uint32_t {
     ERR_OVERFLOW = 1u << 2,    // an output / list capacity was exceeded
     ERR_WALK = 1u << 3,        // signature walk ran off the end (bad input)
     ERR_INTERNAL = 1u << 4,
+    ERR_INPUT = 1u << 5,       // an input list breaks its stated order or range
 };
 
 __device__ __forceinline__ void set_err(uint32_t *err, uint32_t bit) { atomicOr(err, bit); }
@@ -172,6 +173,11 @@ struct fast_ctx {
     // host entry: input copied in chunks on a second stream while the signature kernel runs
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t cev[kCopyChunks + 1] = {};
+    // chunked host input (fast_detect_chunked): two pinned staging buffers,
+    // their copy-done and consumed events
+    uint16_t *h_stage[2] = {};
+    size_t h_stage_bytes = 0;
+    cudaEvent_t chev[4] = {};
     bool timing = true;
     std::string err;
 };

@@ -124,6 +124,9 @@ def _load():
     lib.synth_generate.restype = i32
     lib.synth_generate.argtypes = [u64, u32, u32, vp, u32, u64, u32, vp, dbl, u32, u32, u32, dbl,
                                    u64, u64, u32, i32, vp]
+    lib.synth_generate_rows.restype = i32
+    lib.synth_generate_rows.argtypes = [u64, u64, u64, u32, u32, vp, u32, u64, u32, vp, dbl, u32, u32, u32, dbl,
+                                        u64, u64, u32, i32, vp]
     return lib
 
 
@@ -139,26 +142,33 @@ def build() -> str:
 _lib = None
 
 
-def generate(w: Workload, ld: int | None = None, out=None, threads: int = 0, owner: bool = False):
+def generate(w: Workload, ld: int | None = None, out=None, threads: int = 0, owner: bool = False,
+             rows: tuple | None = None):
     """Draw the workload's fingerprints into a [N, ld] uint16 array.
 
     ``out`` may be any writable C-contiguous uint16 buffer exposing
     ``__array_interface__`` or a ``data_ptr()`` (e.g. a pinned torch tensor).
+    ``rows = (r0, r1)`` draws only windows r0 .. r1 - 1 (exactly those rows
+    of the whole station) into an [r1 - r0, ld] array.
     Returns ``out`` (or a new numpy array), plus the owner codes if asked.
     """
     global _lib
     if _lib is None:
         _lib = _load()
     ld = ld or w.K
+    r0, r1 = rows if rows is not None else (0, w.N)
+    if not 0 <= r0 <= r1 <= w.N:
+        raise ValueError("rows outside the station")
+    n = r1 - r0
     if out is None:
-        out = np.empty((w.N, ld), dtype=np.uint16)
+        out = np.empty((n, ld), dtype=np.uint16)
     ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.__array_interface__["data"][0]
-    own = np.empty(w.N, dtype=np.uint32) if owner else None
+    own = np.empty(n, dtype=np.uint32) if owner else None
     periods = (ctypes.c_uint64 * max(1, len(w.periods)))(*w.periods)
-    rc = _lib.synth_generate(w.N, w.D, w.K, ptr, ld, w.seed, len(w.periods), periods, w.per_redraw,
-                             w.n_templates, w.rep_lo, w.rep_hi, w.tpl_redraw, w.tpl_seed or w.seed,
-                             w.place_range, w.tpl_offset_max, threads,
-                             own.ctypes.data if owner else None)
+    rc = _lib.synth_generate_rows(w.N, r0, n, w.D, w.K, ptr, ld, w.seed, len(w.periods), periods, w.per_redraw,
+                                  w.n_templates, w.rep_lo, w.rep_hi, w.tpl_redraw, w.tpl_seed or w.seed,
+                                  w.place_range, w.tpl_offset_max, threads,
+                                  own.ctypes.data if owner else None)
     if rc < 0:
         raise ValueError("synth_generate: bad arguments")
     return (out, own) if owner else out

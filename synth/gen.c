@@ -127,10 +127,10 @@ static void syn_copy(syn_rng *g, const uint16_t *base, uint32_t D, uint32_t K, d
 }
 
 typedef struct {
-    uint64_t N, w0, w1, seed;
+    uint64_t N, w0, w1, row0, seed;
     uint32_t D, K, ld;
     uint16_t *out;
-    const uint32_t *owner;
+    const uint32_t *owner; /* indexed by w - row0 */
     const uint16_t *pbase, *tbase;
     double per_redraw, tpl_redraw;
 } syn_job;
@@ -141,8 +141,8 @@ static void *syn_worker(void *arg)
     uint64_t *bm = malloc(sizeof(uint64_t) * ((j->D + 63) / 64));
     uint32_t *perm = malloc(sizeof(uint32_t) * (j->K ? j->K : 1));
     for (uint64_t w = j->w0; w < j->w1; w++) {
-        uint16_t *row = j->out + w * (uint64_t)j->ld;
-        uint32_t own = j->owner[w];
+        uint16_t *row = j->out + (w - j->row0) * (uint64_t)j->ld;
+        uint32_t own = j->owner[w - j->row0];
         uint32_t kind = own & (3u << 30), id = own & ((1u << 30) - 1);
         if (kind == OWNER_RANDOM) {
             syn_rng g = {syn_stream(j->seed, DOM_ROW, w), 0};
@@ -162,9 +162,12 @@ static void *syn_worker(void *arg)
 }
 
 /*
- * Fills out[N][ld] (ld >= K) and, when owner_out != NULL, owner_out[N] with
- * each window's source: 0 random, (1<<30)|p periodic source p,
- * (2<<30)|tau template tau.
+ * Fills out[nrows][ld] (ld >= K) with windows row0 .. row0 + nrows - 1 of the
+ * station's N windows and, when owner_out != NULL, owner_out[nrows] with each
+ * window's source: 0 random, (1<<30)|p periodic source p, (2<<30)|tau
+ * template tau.  Every window depends only on (seed, its index), so any range
+ * of rows is drawn exactly as in the whole station (rows of a large station
+ * can be drawn chunk by chunk).
  *
  * Templates draw their base sets and repeat counts from `tpl_seed` (shared
  * by all stations of a network) and their repeat windows uniformly from
@@ -173,16 +176,18 @@ static void *syn_worker(void *arg)
  * Periodic sources and everything else draw from `seed`.
  * Returns the number of threads used, or -1 on bad arguments.
  */
-int synth_generate(uint64_t N, uint32_t D, uint32_t K, uint16_t *out, uint32_t ld, uint64_t seed,
-                   uint32_t n_periodic, const uint64_t *periods, double per_redraw,
-                   uint32_t n_templates, uint32_t rep_lo, uint32_t rep_hi, double tpl_redraw,
-                   uint64_t tpl_seed, uint64_t place_range, uint32_t tpl_offset_max,
-                   int nthreads, uint32_t *owner_out)
+int synth_generate_rows(uint64_t N, uint64_t row0, uint64_t nrows, uint32_t D, uint32_t K, uint16_t *out,
+                        uint32_t ld, uint64_t seed, uint32_t n_periodic, const uint64_t *periods,
+                        double per_redraw, uint32_t n_templates, uint32_t rep_lo, uint32_t rep_hi,
+                        double tpl_redraw, uint64_t tpl_seed, uint64_t place_range, uint32_t tpl_offset_max,
+                        int nthreads, uint32_t *owner_out)
 {
     if (D == 0 || D > 65536 || K == 0 || K > D || ld < K || rep_hi < rep_lo) return -1;
+    if (row0 > N || nrows > N - row0) return -1;
     if (place_range == 0) place_range = N;
-    uint32_t *owner = owner_out ? owner_out : malloc(sizeof(uint32_t) * (N ? N : 1));
-    memset(owner, 0, sizeof(uint32_t) * N);
+    const uint64_t row1 = row0 + nrows;
+    uint32_t *owner = owner_out ? owner_out : malloc(sizeof(uint32_t) * (nrows ? nrows : 1));
+    memset(owner, 0, sizeof(uint32_t) * nrows);
     uint64_t *bm = malloc(sizeof(uint64_t) * ((D + 63) / 64));
 
     uint16_t *pbase = malloc(sizeof(uint16_t) * (uint64_t)K * (n_periodic ? n_periodic : 1));
@@ -191,7 +196,9 @@ int synth_generate(uint64_t N, uint32_t D, uint32_t K, uint16_t *out, uint32_t l
         syn_subset(&g, D, K, bm, pbase + (uint64_t)p * K);
         syn_rng h = {syn_stream(seed, DOM_PPHASE, p), 0};
         uint64_t P = periods[p] ? periods[p] : 1;
-        for (uint64_t w = syn_below(&h, P); w < N; w += P) owner[w] = OWNER_PERIODIC | p;
+        uint64_t w = syn_below(&h, P);
+        if (w < row0) w += (row0 - w + P - 1) / P * P; /* first copy at or after row0 */
+        for (; w < row1; w += P) owner[w - row0] = OWNER_PERIODIC | p;
     }
 
     uint16_t *tbase = malloc(sizeof(uint16_t) * (uint64_t)K * (n_templates ? n_templates : 1));
@@ -204,7 +211,7 @@ int synth_generate(uint64_t N, uint32_t D, uint32_t K, uint16_t *out, uint32_t l
         uint64_t delta = syn_below(&off, (uint64_t)tpl_offset_max + 1);
         for (uint32_t k = 0; k < reps; k++) {
             uint64_t w = syn_below(&pl, place_range) + delta;
-            if (w < N) owner[w] = OWNER_TEMPLATE | t;
+            if (w < N && w >= row0 && w < row1) owner[w - row0] = OWNER_TEMPLATE | t;
         }
     }
     free(bm);
@@ -214,12 +221,12 @@ int synth_generate(uint64_t N, uint32_t D, uint32_t K, uint16_t *out, uint32_t l
         long n = sysconf(_SC_NPROCESSORS_ONLN);
         T = n > 0 ? (int)n : 1;
     }
-    if ((uint64_t)T > N / 4096 + 1) T = (int)(N / 4096 + 1);
+    if ((uint64_t)T > nrows / 4096 + 1) T = (int)(nrows / 4096 + 1);
     pthread_t *th = malloc(sizeof(pthread_t) * T);
     syn_job *jobs = malloc(sizeof(syn_job) * T);
     for (int k = 0; k < T; k++) {
-        jobs[k] = (syn_job){N,     N * k / T, N * (k + 1) / T, seed,      D,         K, ld,
-                            out,   owner,     pbase,           tbase,     per_redraw, tpl_redraw};
+        jobs[k] = (syn_job){N,   row0 + nrows * k / T, row0 + nrows * (k + 1) / T, row0, seed, D, K, ld,
+                            out, owner, pbase, tbase, per_redraw, tpl_redraw};
         pthread_create(&th[k], NULL, syn_worker, &jobs[k]);
     }
     for (int k = 0; k < T; k++) pthread_join(th[k], NULL);
@@ -229,4 +236,15 @@ int synth_generate(uint64_t N, uint32_t D, uint32_t K, uint16_t *out, uint32_t l
     free(tbase);
     if (!owner_out) free(owner);
     return T;
+}
+
+/* The whole station: rows 0 .. N - 1 (see synth_generate_rows). */
+int synth_generate(uint64_t N, uint32_t D, uint32_t K, uint16_t *out, uint32_t ld, uint64_t seed,
+                   uint32_t n_periodic, const uint64_t *periods, double per_redraw,
+                   uint32_t n_templates, uint32_t rep_lo, uint32_t rep_hi, double tpl_redraw,
+                   uint64_t tpl_seed, uint64_t place_range, uint32_t tpl_offset_max,
+                   int nthreads, uint32_t *owner_out)
+{
+    return synth_generate_rows(N, 0, N, D, K, out, ld, seed, n_periodic, periods, per_redraw, n_templates, rep_lo,
+                               rep_hi, tpl_redraw, tpl_seed, place_range, tpl_offset_max, nthreads, owner_out);
 }

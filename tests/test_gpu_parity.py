@@ -230,6 +230,55 @@ def test_host_entry_point_matches_device():
     s.close()
 
 
+def _filler(w, ld):
+    def fill(r0, n, rows):
+        synth.generate(w, ld=ld, out=rows, rows=(r0, r0 + n))
+    return fill
+
+
+@pytest.mark.parametrize("n,tg,qp,chunk", [(50_000, 10, 0, 7001), (300_000, 10, 5, 65_536), (40_000, 0, 0, 40_000)])
+def test_chunked_host_input_c4_shape(n, tg, qp, chunk):
+    # §6.4: a station too long to hold at once, fed in chunks, with its tables
+    # sorted 10 at a time and its pair buffer split into query partitions
+    w = synth.scaled("c4", n)
+    p = dict(w.params(), table_group=tg, query_part=qp)
+    s = _searcher(p)
+    r = s.detect_chunked(w.N, 400, _filler(w, 400), chunk_rows=chunk)
+    got = r.numpy()
+    r.free()
+    idx = synth.generate(w, ld=400)
+    _, _, want = _oracle_run(p, idx, w.K)
+    assert len(want[0]) > 0
+    _assert_lists(got, want)
+    s.close()
+
+
+def test_chunked_signatures_and_fill_failure():
+    from paper_1803_09835_gb300 import FastError
+    w = synth.scaled("c1", 20_000)
+    idx = synth.generate(w, ld=408)
+    p = w.params()
+    s = _searcher(p)
+    sig = torch.empty((p["b"], w.N), dtype=torch.int32, device="cuda")
+    for r0, r1 in ((0, 5003), (5003, 5003), (5003, 17_777), (17_777, 20_000)):
+        s.sig_rows(torch.from_numpy(idx[r0:r1]).cuda(), sig, r0)
+    assert np.array_equal(_u32(sig), oracle.keys(p, np.ascontiguousarray(idx[:, :w.K])))
+    with pytest.raises(FastError):
+        s.sig_rows(torch.from_numpy(idx[:10]).cuda(), sig, w.N - 5)  # past the end
+
+    def bad(r0, n, rows):
+        if r0 > 0:
+            raise RuntimeError("fingerprint source gone")
+        rows[:] = idx[r0:r0 + n]
+    with pytest.raises(RuntimeError):
+        s.detect_chunked(w.N, 408, bad, chunk_rows=6000)
+    good = s.detect_chunked(w.N, 408, lambda r0, n, rows: rows.__setitem__(slice(None), idx[r0:r0 + n]),
+                            chunk_rows=6000)
+    _, _, want = _oracle_run(p, idx, w.K)
+    _assert_lists(good.numpy(), want)
+    s.close()
+
+
 # ------------------------------------------------------------ edge cases
 
 def _params(**kw):
@@ -352,3 +401,71 @@ def test_c1_full_size_sampled_rows():
     # sampled entries: votes from the definition
     for x in rng.integers(0, len(gi), 3000):
         assert oracle.pair_votes(p, keys, int(gi[x]), int(gj[x])) == gv[x]
+
+
+@pytest.mark.slow
+def test_c4_full_size_chunked_table_groups():
+    """The 5-year, 157,680,000-window station: input generated and fed in
+    chunks, tables sorted 10 at a time (the configuration's 10 groups of 10),
+    the pair buffer in as many query partitions as the device needs.  The
+    oracle cannot hold this station's keys, so the list is checked by its
+    invariants, by exact votes of sampled entries (keys of the two windows
+    from the oracle), and by recall on sampled candidate pairs (copies of one
+    template or of the hourly / daily sources): a pair of live windows is in
+    the list exactly when the oracle counts >= v shared tables."""
+    w = synth.workload("c4")
+    p = dict(w.params(), table_group=10)
+    s = _searcher(p)
+    r = s.detect_chunked(w.N, 400, _filler(w, 400), chunk_rows=1 << 22)
+    gi, gj, gv = r.numpy()
+    st = s.stats()
+    r.free()
+    s.close()
+    torch.cuda.empty_cache()
+    assert len(gi) > 10**8 and st["n_dropped"] > 0
+    assert np.all(gi < gj) and np.all(gj.astype(np.int64) - gi > p["excl"])
+    assert np.all(gv >= p["v"]) and np.all(gv <= p["b"])
+    key = (gi.astype(np.uint64) << np.uint64(32)) | gj
+    assert np.all(key[1:] > key[:-1])
+    del key
+    rng = np.random.default_rng(4)
+
+    def keys_of(ids):
+        ids = np.asarray(ids, np.int64)
+        rows = np.concatenate([synth.generate(w, ld=400, rows=(int(x), int(x) + 1)) for x in ids])
+        return oracle.keys(p, rows)
+
+    # exact votes of sampled entries
+    xs = rng.integers(0, len(gi), 2000)
+    ki, kj = keys_of(gi[xs]), keys_of(gj[xs])
+    assert np.array_equal((ki == kj).sum(axis=0), gv[xs])
+    # recall on candidate pairs among windows of one template or source that
+    # the filter cannot touch (sources repeating more often than every 200 s
+    # are the only ones whose buckets can exceed 0.5 % of the station)
+    own = np.empty(w.N, np.uint32)
+    for r0 in range(0, w.N, 1 << 24):
+        r1 = min(w.N, r0 + (1 << 24))
+        own[r0:r1] = synth.generate(w, ld=400, rows=(r0, r1), owner=True)[1]
+    groups = {}
+    for code in (synth.OWNER_PERIODIC + 3, synth.OWNER_PERIODIC + 4):  # 3600 s and 86400 s sources
+        groups[code] = np.nonzero(own == code)[0]
+    tpl = own[own >= synth.OWNER_TEMPLATE]
+    for t in rng.choice(np.unique(tpl), 40, replace=False):
+        groups[int(t)] = np.nonzero(own == t)[0]
+    cand = []
+    for ids in groups.values():
+        if len(ids) < 2:
+            continue
+        for _ in range(25):
+            a, b = np.sort(rng.choice(ids, 2, replace=False))
+            if b - a > p["excl"]:
+                cand.append((a, b))
+    cand = np.array(cand, np.int64)
+    ka, kb = keys_of(cand[:, 0]), keys_of(cand[:, 1])
+    votes = (ka == kb).sum(axis=0)
+    key = gi.astype(np.int64) * (1 << 32) + gj
+    want = cand[:, 0] * (1 << 32) + cand[:, 1]
+    pos = np.minimum(np.searchsorted(key, want), len(key) - 1)
+    found = key[pos] == want
+    assert np.array_equal(found, votes >= p["v"]), (found.sum(), (votes >= p["v"]).sum())
+    assert found.sum() > 0

@@ -48,3 +48,17 @@ def test_request_schedule():
     t, st, size = synth.requests(5000, 2000.0)
     assert np.all(np.diff(t) >= 0) and abs(5000 / t[-1] - 2000) < 200
     assert size.min() >= 60 and size.max() <= 3600 and st.max() < 12
+
+
+def test_row_ranges_equal_the_whole_station():
+    # a large station is drawn chunk by chunk: any row range must be exactly
+    # those rows of the whole station (periodic phases, template placements)
+    w = synth.scaled("c4", 50_000)
+    full, own = synth.generate(w, ld=408, owner=True)
+    for r0, r1 in ((0, 50_000), (0, 1), (17, 4113), (29_999, 50_000), (12_345, 12_345)):
+        part, po = synth.generate(w, ld=408, owner=True, rows=(r0, r1))
+        assert part.shape == (r1 - r0, 408)
+        assert np.array_equal(part, full[r0:r1]) and np.array_equal(po, own[r0:r1])
+    import pytest
+    with pytest.raises(ValueError):
+        synth.generate(w, rows=(10, 50_001))
