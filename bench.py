@@ -1,20 +1,25 @@
 #!/usr/bin/env python
 """Throughput of the LSH fingerprint search on GB300: fingerprints/s, bit-exact.
 
-One step = the whole hot path on one station's fingerprints resident in HBM:
-Min-Max signatures -> per-table bucket keys -> radix-sorted hash tables ->
-occurrence filter -> pair enumeration + vote counting -> canonical (i, j,
-votes) list (fast_detect).  The workload is the paper-scale single station:
-3 months at 1 s lag (N = 7,776,000 windows), D = 8192, K = 400, Min-Max
-b = 100 x r = 4, v = 4, |i - j| <= 10 excluded, 0.5 % occurrence filter,
-synthetic (seeded) fingerprints with 2,000 repeating templates and three
-periodic noise sources.
+Headline workload (default): the batched multi-station search -- 12 stations
+of 1..12 months at 1 s lag (N_s = s x 2,592,000 windows, 202,176,000 in all),
+D = 8192, K = 400, Min-Max b = 100 x r = 4, v = 4, |i - j| <= 10 excluded,
+0.5 % occurrence filter per station, 8,000 templates shared across stations
+at station offsets of 0..30 windows, periodic noise every 60, 300 and 3600 s.
+One step = the whole hot path over all 12 stations, their fingerprints
+resident in HBM: Min-Max signatures -> bucket keys -> radix-sorted tables
+(10 tables at a time) -> occurrence filter -> pair enumeration + votes ->
+canonical (i, j, votes) lists, searched as batches of whole stations
+(fast_detect_batch; pairs never cross stations).  Beside it: the same
+stations one fast_detect per station ("plain"), the end-to-end figure from
+pinned host memory (fast_detect_host, results copied back), and the
+single-station 3-month workload (c1) as a diagnostic.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
-With N > 1 (torchrun, one rank per GPU) every rank searches its own station
-(an independent problem, no data-path collective): weak scaling; the value is
-the fingerprints of all ranks over the slowest rank's time.
+With N > 1 (torchrun, one rank per GPU) every rank searches its own network
+of stations (independent problems, no data-path collective): weak scaling;
+the value is the fingerprints of all ranks over the slowest rank's time.
 ``--impl reference`` times the CPU oracle (plain C, the definition written
 out) on a bounded sample of the same workload on this machine's cores.
 """
@@ -129,10 +134,21 @@ def _sample_workload(w, n):
 
 
 def reference_arm(args, rank, world):
+    """The oracle, as it stands, on a bounded sample of the workload (its
+    first --ref-sample windows; for the 12-station workload, of its
+    12-month station), each step one whole-path run on the host cores."""
     import synth
     if rank != 0:
         return 0
-    w = synth.workload(args.workload)
+    if args.workload == "c2":
+        w = c2_stations(0)[11]
+        what = "the 12-month station of the 12-station workload"
+        cfg = {"workload": "c2: 12 stations of 1..12 months (202,176,000 windows); the oracle runs a bounded "
+                           "sample of it", "sample_windows": args.ref_sample}
+    else:
+        w = synth.workload(args.workload)
+        what = f"the {w.name} workload"
+        cfg = workload_config(w, 1, {"sample_windows": args.ref_sample})
     n = args.ref_sample
     sw = _sample_workload(w, n)
     times, thr, M = [], 0, 0
@@ -142,12 +158,11 @@ def reference_arm(args, rank, world):
             times.append(dt)
     ms = 1000 * statistics.mean(times)
     value = n / (ms / 1000)
-    sample = (f"first {n:,} windows of the {w.name} workload (its own filter threshold), whole path "
+    sample = (f"first {n:,} windows of {what} (its own filter threshold), whole path "
               f"(keys on {thr} threads, filter, search single-threaded); {M:,} detections")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": workload_config(w, 1, {"sample_windows": n}),
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -212,8 +227,7 @@ def weak_value(n_per_rank, ms_max: float) -> float:
 # ------------------------------------------------------------------- GB300 leg
 
 STAGES = ("sig", "sort", "filter", "enum", "dense", "sparse", "output", "pair_count", "pair_emit", "vote",
-          "k_pairs", "k_vote")
-
+          "k_pairs", "k_vote", "k_medium", "k_vote_block", "k_count_small", "k_count_medium")
 
 def _kernel_source_hash(rel: str) -> str:
     import hashlib
@@ -233,39 +247,383 @@ def _traffic(kernel: str, units: float):
     return rec["bytes_per_unit"] * units
 
 
-def kernel_rooflines(w, per, st, peaks, n_sms):
-    """Per kernel: live ms per launch, algorithmic bytes per launch and the
-    HBM roofline fraction they reach.  Algorithmic bytes (per unit):
-      k_sig_walk      read K u16 indices + write b keys  = 2K + 4b  per fingerprint
-      radix sort      read key + write (key, id)         = 12       per table entry (all passes together)
-      k_pairs_grp<2>  read (key, id) 8 per table entry + write 4 per small-bucket pair (one pass)
-      k_warp_vote     read 4 per pair emission + write 5 per kept sparse pair (not counted: small)
-      output          write (i, j, votes)                = 9        per detection"""
-    N, b, K = w.N, w.b, w.K
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+class KernelBytes:
+    """Algorithmic bytes of the heavy kernels, summed over the searches of a
+    step (each search's counters).  Per unit:
+      k_sig_walk          read K u16 indices + write b keys = 2K + 4b per fingerprint
+      radix sort          read key + write (key, id)       = 12 per table entry (all passes together)
+      k_pairs_grp         read (key, id) 8 per table entry + write 4 per small-bucket pair
+      k_medium_grp        write 4 per medium-bucket pair (its bucket reads are not counted)
+      k_pairs_grp count   read (key, id) 8 per table entry
+      k_warp_vote         read 4 per pair emission
+      output              write (i, j, votes) = 9 per detection
+    Table reads repeated by query partitions are overhead, not algorithmic."""
+
+    def __init__(self, w):
+        self.w = w
+        self.b = {k: 0.0 for k in ("k_sig_walk", "radix sort", "k_pairs_grp", "k_medium_grp", "k_pairs_grp count",
+                                   "k_warp_vote", "output")}
+
+    def add(self, N, st):
+        w, b = self.w, self.b
+        b["k_sig_walk"] += N * (2 * w.K + 4 * w.b)
+        b["radix sort"] += N * w.b * 12
+        b["k_pairs_grp"] += N * w.b * 8 + st["n_pairs_small"] * 4
+        b["k_medium_grp"] += (st["n_emissions"] - st["n_pairs_small"]) * 4
+        b["k_pairs_grp count"] += N * w.b * 8 if st["ms_k_count_small"] > 0 else 0
+        b["k_warp_vote"] += st["n_emissions"] * 4
+        b["output"] += st["n_detections"] * 9
+
+
+KERNEL_MS = {"k_sig_walk": "sig", "radix sort": "sort", "k_pairs_grp": "k_pairs", "k_medium_grp": "k_medium",
+             "k_pairs_grp count": "k_count_small", "k_warp_vote": "k_vote", "output": "output"}
+SINGLE = {"k_sig_walk", "k_pairs_grp", "k_medium_grp", "k_pairs_grp count", "k_warp_vote"}
+
+
+def kernel_rooflines(kb, per, steps, peaks, units):
+    """Per heavy kernel: live ms per step (CUDA events on the launching
+    stream, summed over the step's launches), algorithmic bytes per step and
+    the HBM roofline fraction they reach; ``traffic`` is DRAM bytes from the
+    committed ncu record of that kernel (scaled to the step's units), or None."""
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     src = "measured" if "hbm_gbs" in peaks else "fallback"
     out = {}
-
-    def put(name, ms, nbytes, single, traffic=None, **extra):
+    for name, stage in KERNEL_MS.items():
+        ms = per[stage]
+        nbytes = kb.b[name] / steps
         ach = nbytes / (ms / 1000) / 1e9 if ms > 0 else 0.0
         out[name] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                     "traffic": traffic, "peak_source": src, "algorithmic_bytes": nbytes, "ms": ms,
-                     "single_kernel": single, **extra}
-
-    F = b * ((w.r + 1) // 2) if w.kind else b * w.r
-    clock = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    alu_peak = n_sms * 128 * clock  # int32 lanes x clock
-    put("k_sig_walk", per["sig"], N * (2 * K + 4 * b), True, _traffic("k_sig_walk", N),
-        alu_view={"definition": "direct evaluation: N*K*F hash evaluations x 4 int ops",
-                  "ops": N * K * F * 4, "peak_ops_per_s": alu_peak,
-                  "time_at_peak_ms": 1000 * N * K * F * 4 / alu_peak})
-    passes = max(1, st["sort_passes"])
-    put("radix sort", per["sort"], N * b * 12, False, None, passes=passes)
-    put("k_pairs_grp<2>", per["k_pairs"], N * b * 8 + st["n_pairs_small"] * 4, True,
-        _traffic("k_pairs_grp<2>", N))
-    put("k_warp_vote", per["k_vote"], st["n_emissions"] * 4, True, _traffic("k_warp_vote", N))
-    put("output", per["output"], st["n_detections"] * 9, False)
+                     "traffic": _traffic(name, units), "peak_source": f"{src} ({hbm:g} GB/s)",
+                     "algorithmic_bytes": nbytes, "ms": ms, "single_kernel": name in SINGLE}
     return out
+
+
+def dominant(kernels):
+    dom = max((k for k in kernels if kernels[k]["single_kernel"] and kernels[k]["ms"] > 0),
+              key=lambda k: kernels[k]["ms"])
+    roof = dict(kernels[dom])
+    roof["kernel"] = dom
+    roof.pop("single_kernel")
+    return roof
+
+
+COUNTERS = ("n_dropped", "n_emissions", "n_dense_pairs", "n_groups", "n_detections", "query_parts", "sort_passes",
+            "n_long_rows", "n_huge_rows", "max_row", "n_pairs_small", "n_overflow", "peak_bytes")
+
+
+class Meter:
+    """Stage times, launches and counters of the searches inside timed steps."""
+
+    def __init__(self, w):
+        self.on = False
+        self.acc = {k: 0.0 for k in STAGES}
+        self.launches = 0
+        self.kb = KernelBytes(w)
+        self.last = {}
+
+    def add(self, N, st):
+        if not self.on:
+            return
+        for k in STAGES:
+            self.acc[k] += st["ms_" + k]
+        self.launches += st["n_launches"]
+        self.kb.add(N, st)
+        self.last[N] = {k: st[k] for k in COUNTERS}
+
+
+def _sample_line(w, n, label):
+    dt, thr, Ms = oracle_sample(w, n)
+    return {"value": n / dt, "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": f"first {n:,} windows of {label} (its own filter threshold), whole path (keys on {thr} "
+                      f"threads, filter, search single-threaded), {dt:.1f} s, {Ms:,} detections; the oracle's "
+                      f"search cost per window grows with the station length, so the full workload runs slower "
+                      f"per window than this sample"}
+
+
+def station_arm(args, rank, world, local_rank, w, steps, warmup, e2e=True):
+    """One station per rank, fast_detect on its fingerprints resident in HBM;
+    returns the result line (also the diagnostic single-station figures)."""
+    import torch
+
+    import synth
+    from paper_1803_09835_gb300 import Searcher, fast_detect_host
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    ld = ((w.K + 7) // 8) * 8
+    h_idx = torch.empty((w.N, ld), dtype=torch.uint16, pin_memory=True)
+    synth.generate(w, ld=ld, out=h_idx)
+    d_idx = h_idx.cuda()
+    s = Searcher(w.params())
+    meter = Meter(w)
+
+    def step():
+        r = s.detect(d_idx)
+        m = r.M
+        r.free()
+        meter.add(w.N, s.stats())
+        return m
+
+    clocks = Clocks(local_rank)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def start():
+        clocks.start()
+        meter.on = True
+        ev0.record()
+
+    def stop():
+        ev1.record()
+        torch.cuda.synchronize()
+        meter.on = False
+        return ev0.elapsed_time(ev1)
+
+    ms, M = timed_steps(step, steps, warmup, dist, torch.cuda.synchronize, (start, stop))
+    clk = clocks.stop()
+    ms = max_over_ranks(ms, dist, "cuda")
+    n_total = w.N * world
+    line = {"metric": METRIC, "value": weak_value([w.N] * world, ms), "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": workload_config(w, world, {"detections_per_station": M}),
+            "gpu_launches": meter.launches, "clocks": clk}
+    if e2e:  # end to end through the host entry point: pinned input in, pinned result out
+        e2e_steps = max(1, min(steps, args.e2e_steps))
+        h_i = torch.empty(M, dtype=torch.int32, pin_memory=True)
+        h_j = torch.empty(M, dtype=torch.int32, pin_memory=True)
+        h_v = torch.empty(M, dtype=torch.uint8, pin_memory=True)
+        fast_detect_host(s.ctx, h_idx, w.N, ld, h_i, h_j, h_v, M)  # warm-up: the library's pool grows once
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            m2 = fast_detect_host(s.ctx, h_idx, w.N, ld, h_i, h_j, h_v, M)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(1000 * (time.perf_counter() - t0) / e2e_steps, dist, "cuda")
+        assert m2 == M
+        line["e2e"] = {"value": n_total / (e2e_ms / 1000), "unit": UNIT, "ms_per_step": e2e_ms,
+                       "h2d_bytes_per_step": w.N * ld * 2, "d2h_bytes_per_step": M * 9}
+    per = {k: meter.acc[k] / steps for k in STAGES}
+    kernels = kernel_rooflines(meter.kb, per, steps, _peaks(), w.N)
+    line["roofline"] = dominant(kernels)
+    line["kernels"] = {k: {kk: v[kk] for kk in ("ms", "bound", "achieved", "frac", "unit")} for k, v in kernels.items()}
+    line["stage_ms"] = per
+    line["counters"] = meter.last.get(w.N, {})
+    s.close()
+    return line
+
+
+def c2_stations(rank: int, n_month: int = 0):
+    """Rank `rank`'s network of 12 stations, station s (0-based) covering
+    s + 1 months (n_month windows per month for quick runs).  Rank 0 is the
+    workload itself; other ranks draw their own stations and templates."""
+    from dataclasses import replace
+
+    import synth
+    ws = []
+    for st in range(12):
+        w = synth.workload("c2", station=st) if not n_month else synth.scaled("c2", (st + 1) * n_month, station=st)
+        if rank:
+            w = replace(w, seed=w.seed + 1000 * rank, tpl_seed=w.tpl_seed + 1000 * rank)
+        ws.append(w)
+    return ws
+
+
+C2_GROUPS = ((12,), (11,), (10,), (9,), (8,), (7,), (6, 1), (5, 2), (4, 3))  # stations by months, ~<= 31M windows
+
+
+def c2_arm(args, rank, world, local_rank):
+    """The headline: the 12-station workload, every station's fingerprints
+    resident in HBM (161.7 GB), one step = all stations searched as batches
+    of whole stations (one fast_detect_batch per batch of C2_GROUPS)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1803_09835_gb300 import Searcher, fast_detect_host
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    ws = c2_stations(rank, args.n)
+    ld = 400
+    N_all = sum(w.N for w in ws)
+    t0 = time.perf_counter()
+    bufs = []  # one device buffer per batch: its stations' rows one after another
+    for grp in C2_GROUPS:
+        sub = [ws[m - 1] for m in grp]
+        d = torch.empty((sum(w.N for w in sub), ld), dtype=torch.int16, device="cuda")
+        off = 0
+        for w in sub:
+            d[off:off + w.N].copy_(torch.from_numpy(synth.generate(w, ld=ld).view(np.int16)))
+            off += w.N
+        bufs.append((grp, d, [w.N for w in sub]))
+    gen_s = time.perf_counter() - t0
+    p = dict(ws[0].params(), table_group=10)
+    s = Searcher(p)
+    meter = Meter(ws[0])
+    last_M = {}
+
+    def step():
+        tot = 0
+        for grp, d, lens in bufs:
+            res = s.detect_batch(d, lens)
+            meter.add(sum(lens), s.stats())
+            for m, r in zip(grp, res):
+                last_M[m] = r.M
+                tot += r.M
+                r.free()
+        return tot
+
+    clocks = Clocks(local_rank)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def start():
+        clocks.start()
+        meter.on = True
+        ev0.record()
+
+    def stop():
+        ev1.record()
+        torch.cuda.synchronize()
+        meter.on = False
+        return ev0.elapsed_time(ev1)
+
+    ms, M = timed_steps(step, args.steps, args.warmup, dist, torch.cuda.synchronize, (start, stop))
+    clk = clocks.stop()
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = weak_value([N_all] * world, ms)
+
+    # the plain search: the same stations, one fast_detect per station
+    plain_M, plain_ms = {}, 0.0
+    for grp, d, lens in bufs:
+        off = 0
+        for m, n in zip(grp, lens):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = s.detect(d[off:off + n])
+            e1.record()
+            torch.cuda.synchronize()
+            plain_ms += e0.elapsed_time(e1)
+            plain_M[m] = r.M
+            r.free()
+            off += n
+    plain_ms = max_over_ranks(plain_ms, dist, "cuda")
+
+    # a batch plan: the (4 + 3)-month batch's build captured as a CUDA graph,
+    # search options autotuned on the first run
+    plan_info = None
+    if not args.no_plan:
+        grp, d, lens = next(b for b in bufs if b[0] == (4, 3))
+        st_ = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        plan = s.plan(d, lens, st_)
+        for r in plan.run():
+            r.free()
+        torch.cuda.synchronize()
+        pt = time.perf_counter()
+        pres = plan.run()
+        torch.cuda.synchronize()
+        info = plan.info()
+        plan_info = {"batch_months": list(grp), "ms_wall": 1000 * (time.perf_counter() - pt),
+                     "build_graph_ms": info["build_ms"], "graph_kernels": info["graph_kernels"],
+                     "best": info["best"], "same_counts": [r.M for r in pres] == [last_M[m] for m in grp]}
+        for r in pres:
+            r.free()
+        plan.close()
+    del bufs, d
+    torch.cuda.empty_cache()
+
+    # end to end through the host entry point, station by station: pinned
+    # input in, every detection copied back to pinned host memory
+    e2e_ms = h2d = d2h = 0
+    if not args.no_e2e:
+        nmax = max(w.N for w in ws)
+        mmax = max(last_M.values())
+        h_idx = torch.empty((nmax, ld), dtype=torch.uint16, pin_memory=True)
+        h_i = torch.empty(mmax, dtype=torch.int32, pin_memory=True)
+        h_j = torch.empty(mmax, dtype=torch.int32, pin_memory=True)
+        h_v = torch.empty(mmax, dtype=torch.uint8, pin_memory=True)
+        for k, w in enumerate(ws):
+            synth.generate(w, ld=ld, out=h_idx[:w.N])  # drawing the input is not timed
+            if k == 0:
+                fast_detect_host(s.ctx, h_idx, w.N, ld, h_i, h_j, h_v, mmax)  # warm-up
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            m = fast_detect_host(s.ctx, h_idx, w.N, ld, h_i, h_j, h_v, mmax)
+            torch.cuda.synchronize()
+            e2e_ms += 1000 * (time.perf_counter() - t1)
+            assert m == last_M[k + 1]
+            h2d += w.N * ld * 2
+            d2h += m * 9
+        e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
+        del h_idx, h_i, h_j, h_v
+    s.close()
+    torch.cuda.empty_cache()
+
+    per = {k: meter.acc[k] / args.steps for k in STAGES}
+    kernels = kernel_rooflines(meter.kb, per, args.steps, _peaks(), N_all)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"c2: 12 stations of 1..12 months at 1 s lag (N_s = s x {ws[0].N:,}), "
+                                   f"{N_all:,} windows per network, D={ws[0].D}, K={ws[0].K}, Min-Max b={ws[0].b} "
+                                   f"x r={ws[0].r}, v={ws[0].v}, excl={ws[0].excl}, occurrence filter 0.5% per "
+                                   f"station, templates shared across stations (offsets 0..30), periodic sources "
+                                   f"{list(ws[0].periods)} s",
+                       "networks": world, "windows_per_step": N_all * world,
+                       "batches_months": [list(g) for g in C2_GROUPS], "table_group": 10,
+                       "query_part": "automatic (as many as the memory beside the resident inputs needs)",
+                       "l2": f"inputs larger than L2 ({N_all * ld * 2 / 1e9:.1f} GB resident), no flush",
+                       "input_generation_s": gen_s, "detections_per_step": M},
+            "e2e": {"value": (N_all * world / (e2e_ms / 1000)) if e2e_ms else None, "unit": UNIT,
+                    "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "how": "fast_detect_host per station from pinned host memory, every detection copied back "
+                           "(the input's drawing between stations not timed)"},
+            "gpu_launches": meter.launches, "roofline": dominant(kernels), "clocks": clk,
+            "plain": {"value": N_all * world / (plain_ms / 1000), "unit": UNIT, "ms_per_step": plain_ms,
+                      "how": "the same stations, one fast_detect per station, inputs resident",
+                      "same_counts_as_batched": plain_M == last_M},
+            "plan": plan_info,
+            "kernels": {k: {kk: v[kk] for kk in ("ms", "bound", "achieved", "frac", "unit", "algorithmic_bytes")}
+                        for k, v in kernels.items()},
+            "stage_ms": per,
+            "counters_by_batch": {str(n): c for n, c in meter.last.items()},
+            "detections_by_station_months": {str(m): last_M[m] for m in sorted(last_M)}}
+    return line
+
+
+def gpu_arm(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    if args.workload == "c2":
+        line = c2_arm(args, rank, world, local_rank)
+        if not args.no_c1:  # the single-station 3-month workload, as a diagnostic
+            import synth
+            w1 = station_workload("c1", rank, 0)
+            c1 = station_arm(args, rank, world, local_rank, w1, steps=5, warmup=3, e2e=False)
+            line["c1"] = {k: c1[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup", "roofline",
+                                              "kernels", "stage_ms", "counters")}
+        sample_w = _sample_workload(c2_stations(0)[11], args.cpu_sample)
+        label = "the 12-month station of the same workload"
+    else:
+        w = station_workload(args.workload, rank, args.n)
+        line = station_arm(args, rank, world, local_rank, w, args.steps, args.warmup)
+        sample_w = _sample_workload(w, args.cpu_sample)
+        label = "the same workload"
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _sample_line(sample_w, args.cpu_sample, label)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 TRAFFIC_KERNELS = {  # kernel-name prefix in the ncu list -> (roofline name, source file)
@@ -315,225 +673,63 @@ def record_traffic(csv_path: str, n_windows: int, command: str, out_path: str | 
     return out
 
 
-def path_sol(w, per, st, peaks, n_sms, ms_step):
-    """Speed-of-light time of the whole path by stage (each stage at the larger
-    of its HBM time and, for signatures, the direct-evaluation ALU time), over
-    the measured step time."""
-    N, b, K = w.N, w.b, w.K
-    hbm = float(peaks.get("hbm_gbs", 6800.0)) * 1e9
-    clock = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    F = b * ((w.r + 1) // 2) if w.kind else b * w.r
-    t = {
-        "sig": max(N * (2 * K + 4 * b) / hbm, N * K * F * 4 / (n_sms * 128 * clock)),
-        "sort_filter": N * b * 20 / hbm,  # read key 4, write (key, id) 8, read key 4 + id 4 again
-        "pairs_votes": st["n_emissions"] * 13 / hbm,
-        "output": st["n_detections"] * 9 / hbm,
-    }
-    tsol = 1000 * sum(t.values())
-    return {"t_sol_ms": tsol, "frac": tsol / ms_step, "by_stage_ms": {k: 1000 * v for k, v in t.items()}}
+# ------------------------------------------------------------- parameter sweep
 
+def sweep_arm(args):
+    """Bucket statistics and search cost against the number of values per
+    table r, on uniform and on imbalanced, correlated fingerprints (§6.3:
+    skewed bits make large buckets; more hash values per table shrink them).
+    One C1-shaped station of --n windows (default 1,000,000) per setting;
+    per table: the bucket pairs sum(s (s - 1) / 2) (the candidates the search
+    has to count), their share of all pairs (selectivity), the largest
+    bucket and the share of fingerprints in the largest 0.1 % of buckets."""
+    from dataclasses import replace
 
-def gpu_arm(args, rank, world, local_rank):
     import numpy as np
     import torch
 
     import synth
     from paper_1803_09835_gb300 import Searcher
-
-    torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-    w = station_workload(args.workload, rank, args.n)
-    ld = ((w.K + 7) // 8) * 8
-    h_idx = torch.empty((w.N, ld), dtype=torch.uint16, pin_memory=True)
-    synth.generate(w, ld=ld, out=h_idx)
-    d_idx = h_idx.cuda()
-    s = Searcher(w.params())
-
-    def step():
-        r = s.detect(d_idx)
-        m = r.M
-        r.free()
-        return m, s.stats()
-
-    acc = {k: 0.0 for k in STAGES}
-    counted = {"launches": 0, "on": False}
-
-    def timed_step():
-        M, st = step()
-        if counted["on"]:
-            for k in STAGES:
-                acc[k] += st["ms_" + k]
-            counted["launches"] += st["n_launches"]
-        return M, st
-
-    clocks = Clocks(local_rank)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-
-    def start():
-        clocks.start()
-        counted["on"] = True
-        ev0.record()
-
-    def stop():
-        ev1.record()
-        torch.cuda.synchronize()
-        return ev0.elapsed_time(ev1)
-
-    ms, (M, last) = timed_steps(timed_step, args.steps, args.warmup, dist, torch.cuda.synchronize, (start, stop))
-    clk = clocks.stop()
-    launches = counted["launches"]
-    ms = max_over_ranks(ms, dist, "cuda")
-    n_total = w.N * world
-    value = weak_value([w.N] * world, ms)
-
-    # end to end through the host entry point: pinned input in, pinned result out
-    e2e_steps = max(1, min(args.steps, args.e2e_steps))
-    h_i = torch.empty(M, dtype=torch.int32, pin_memory=True)
-    h_j = torch.empty(M, dtype=torch.int32, pin_memory=True)
-    h_v = torch.empty(M, dtype=torch.uint8, pin_memory=True)
-    from paper_1803_09835_gb300 import fast_detect_host
-    fast_detect_host(s.ctx, h_idx, w.N, ld, h_i, h_j, h_v, M)  # warm-up: the library's pool grows once
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        m2 = fast_detect_host(s.ctx, h_idx, w.N, ld, h_i, h_j, h_v, M)
-    torch.cuda.synchronize()
-    e2e_ms = 1000 * (time.perf_counter() - t0) / e2e_steps
-    assert m2 == M
-    e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
-
-    # roofline of the dominant kernel (live CUDA-event times, algorithmic bytes)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    per = {k: acc[k] / args.steps for k in STAGES}
-    kernels = kernel_rooflines(w, per, last, peaks, torch.cuda.get_device_properties(local_rank).multi_processor_count)
-    dom = max((k for k in kernels if kernels[k]["single_kernel"]), key=lambda k: kernels[k]["ms"])
-    roof = dict(kernels[dom])
-    roof["kernel"] = dom
-    roof.pop("single_kernel")
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": workload_config(w, world, {"detections_per_station": M}),
-            "e2e": {"value": n_total / (e2e_ms / 1000), "unit": UNIT, "ms_per_step": e2e_ms,
-                    "h2d_bytes_per_step": w.N * ld * 2, "d2h_bytes_per_step": M * 9},
-            "gpu_launches": launches, "roofline": roof, "clocks": clk,
-            "kernels": {k: {kk: v[kk] for kk in ("ms", "bound", "achieved", "frac", "unit")}
-                        for k, v in kernels.items()},
-            "path_sol": path_sol(w, per, last, peaks, torch.cuda.get_device_properties(local_rank).multi_processor_count,
-                                 ms),
-            "stage_ms": per,
-            "counters": {k: last[k] for k in ("n_dropped", "n_emissions", "n_dense_pairs", "n_groups",
-                                              "n_detections", "map_slots", "query_parts", "sort_passes",
-                                              "n_long_rows", "n_huge_rows", "max_row", "n_pairs_small",
-                                              "n_overflow", "peak_bytes")}}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, thr, Ms = oracle_sample(w, args.cpu_sample)
-        line["cpu_baseline"] = {"value": args.cpu_sample / dt, "unit": UNIT, "cores": thr, "kind": "oracle",
-                                "sample": f"first {args.cpu_sample:,} windows of the same workload, whole path "
-                                          f"(keys on {thr} threads, filter, search single-threaded), "
-                                          f"{dt:.1f} s, {Ms:,} detections"}
-    s.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
-
-
-# ------------------------------------------------------------- batched stations
-
-C2_GROUPS = ((12,), (11,), (10,), (9,), (8,), (7,), (6, 1), (5, 2), (4, 3))  # stations by months, ~<= 31M windows
-
-
-def batch_arm(args):
-    """The 12-station workload (stations of 1..12 months, 202,176,000 windows),
-    searched as batches of whole stations that fit the device: one
-    fast_detect_batch per group, device time by CUDA events, inputs resident.
-    The (4, 3)-month group is also run as a batch plan (graph-replayed build,
-    autotuned search), and its stations are checked against single-station
-    searches (a batch must find exactly what each station finds alone)."""
-    import numpy as np
-    import torch
-
-    import synth
-    from paper_1803_09835_gb300 import Searcher
-    base = synth.workload("c2", station=0)
-    ld = ((base.K + 7) // 8) * 8
-    s = Searcher(dict(base.params(), query_part=args.query_part))
-    warm = min(args.warmup, 1)
-    groups = C2_GROUPS if not args.n else ((2, 1),)
-    if args.groups:
-        groups = tuple(tuple(int(m) for m in g.split("+")) for g in args.groups.split(","))
-    rows, tot_ms, tot_win, tot_det = [], 0.0, 0, 0
-    for grp in groups:
-        ws = [synth.workload("c2", station=m - 1) for m in grp]
-        if args.n:
-            ws = [synth.scaled("c2", args.n * m, station=m - 1) for m in grp]
-        t0 = time.perf_counter()
-        host = np.concatenate([synth.generate(w, ld=ld) for w in ws])
-        gen_s = time.perf_counter() - t0
-        d_idx = torch.from_numpy(host).cuda()
-        del host
-        lens = [w.N for w in ws]
-        for _ in range(warm):
-            for r in s.detect_batch(d_idx, lens):
-                r.free()
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record()
-        res = s.detect_batch(d_idx, lens)
-        ev1.record()
-        torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1)
-        det = [r.M for r in res]
-        row = {"months": list(grp), "windows": sum(lens), "ms": ms, "detections": det, "gen_s": gen_s}
-        if grp == (4, 3) or args.n:
-            # exactness across batching: each station alone
-            same = True
-            off = 0
-            for k, w in enumerate(ws):
-                alone = s.detect(d_idx[off:off + w.N])
-                same &= all(np.array_equal(a, b) for a, b in zip(alone.numpy(), res[k].numpy()))
-                alone.free()
-                off += w.N
-            row["batch_equals_alone"] = bool(same)
-            st = torch.cuda.Stream()
+    torch.cuda.set_device(0)
+    n = args.n or 1_000_000
+    base = synth.scaled("c1", n)
+    rows = []
+    for skew, corr in ((0.0, 0.0), (0.3, 0.0), (0.6, 0.3)):
+        w = replace(base, skew=skew, corr=corr)
+        d = torch.from_numpy(synth.generate(w, ld=400)).cuda()
+        for r in (4, 6, 8):
+            p = dict(w.params(), r=r)
+            s = Searcher(p)
+            sig = s.sig(d)
+            tb = s.build_tables(sig)
+            keys = tb.skey.view(p["b"], -1)
+            pairs, big, top = 0, 0, []
+            for t in range(p["b"]):  # bucket sizes of table t from its sorted keys (on the host)
+                k = keys[t].cpu().numpy()
+                cut = np.flatnonzero(np.diff(k)) + 1
+                sizes = np.diff(np.concatenate(([0], cut, [len(k)])))
+                pairs += int((sizes.astype(np.int64) * (sizes - 1) // 2).sum())
+                big = max(big, int(sizes.max()))
+                q = max(1, len(sizes) // 1000)
+                top.append(np.sort(sizes)[::-1][:q].sum() / len(k))
             torch.cuda.synchronize()
-            plan = s.plan(d_idx, lens, st)
-            for r in plan.run():  # first run: the autotuner times its candidates
-                r.free()
+            t0 = time.perf_counter()
+            res = s.search(tb)
             torch.cuda.synchronize()
-            p0 = time.perf_counter()
-            pres = plan.run()
-            torch.cuda.synchronize()
-            info = plan.info()
-            row["plan"] = {"ms_wall": 1000 * (time.perf_counter() - p0), "build_graph_ms": info["build_ms"],
-                           "graph_kernels": info["graph_kernels"], "best": info["best"],
-                           "same": bool(all(all(np.array_equal(a, b) for a, b in zip(x.numpy(), y.numpy()))
-                                            for x, y in zip(pres, res)))}
-            for r in pres:
-                r.free()
-            plan.close()
-        for r in res:
-            r.free()
-        del d_idx
+            ms = 1000 * (time.perf_counter() - t0)
+            st = s.stats()
+            row = {"skew": skew, "corr": corr, "r": r, "windows": n, "bucket_pairs": pairs,
+                   "selectivity": pairs / (p["b"] * n * (n - 1) / 2), "largest_bucket": big,
+                   "top0.1%_bucket_share": float(np.mean(top)), "detections": res.M, "dropped": st["n_dropped"],
+                   "search_ms": ms}
+            print(json.dumps(row), flush=True)
+            rows.append(row)
+            res.free()
+            tb.free()
+            s.close()
+            del sig
+        del d
         torch.cuda.empty_cache()
-        rows.append(row)
-        tot_ms += ms
-        tot_win += sum(lens)
-        tot_det += sum(det)
-        print(json.dumps(row), flush=True)
-    line = {"metric": "fingerprints/sec searched, stations batched", "value": tot_win / (tot_ms / 1000),
-            "unit": UNIT, "n_gpus": 1, "data": "synthetic", "dtype": "u32",
-            "config": {"workload": "c2: 12 stations of 1..12 months (N_s = s x 2,592,000), shared templates",
-                       "windows": tot_win, "batches": [list(g) for g in groups], "query_part": args.query_part},
-            "ms_total": tot_ms, "detections": tot_det}
-    print(json.dumps(line), flush=True)
-    s.close()
     return 0
 
 
@@ -630,8 +826,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("gb300", "reference"), default="gb300")
-    ap.add_argument("--workload", default="c1")
-    ap.add_argument("--n", type=int, default=0, help="override N (windows per station) for quick runs")
+    ap.add_argument("--workload", default="c2", help="c2 (12 stations, the default), or one station: c0, c1")
+    ap.add_argument("--n", type=int, default=0,
+                    help="quick runs: windows per station (one station) or per month (c2)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=300_000)
     ap.add_argument("--ref-sample", type=int, default=100_000)
@@ -642,9 +839,10 @@ def main():
     ap.add_argument("--duration", type=float, default=5.0)
     ap.add_argument("--budget-gb", type=int, default=150)
     ap.add_argument("--plain-requests", type=int, default=3)
-    ap.add_argument("--batch", action="store_true", help="12-station workload (c2) searched in station batches")
-    ap.add_argument("--query-part", type=int, default=4, help="query partitions of the pair buffer for --batch")
-    ap.add_argument("--groups", default="", help="--batch station groups by months, e.g. '12,6+1'")
+    ap.add_argument("--sweep", action="store_true", help="bucket statistics vs r on uniform and skewed fingerprints")
+    ap.add_argument("--no-c1", action="store_true", help="skip the single-station diagnostic beside the headline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host memory) leg of the headline")
+    ap.add_argument("--no-plan", action="store_true", help="skip the batch-plan leg of the headline")
     ap.add_argument("--record-traffic", default="", metavar="CSV",
                     help="write profiles/dram_traffic.json from an ncu dram-bytes capture of this workload")
     ap.add_argument("--record-command", default="", help="the ncu command line to note beside --record-traffic")
@@ -655,8 +853,8 @@ def main():
         return 0
     if args.serving:
         return serving_arm(args)
-    if args.batch:
-        return batch_arm(args)
+    if args.sweep:
+        return sweep_arm(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -122,12 +122,18 @@ typedef struct {
     /* the sparse stage of the row-partitioned search, split: counting the
        small/medium-bucket pairs per row group, writing them, voting */
     float ms_pair_count, ms_pair_emit, ms_vote;
-    /* single kernels inside those: the small-bucket pair writer, the group vote */
+    /* single kernels inside those, summed over the query partitions: the
+       small-bucket pair writer, the warp-per-group vote */
     float ms_k_pairs, ms_k_vote;
     uint64_t n_pairs_small;   /* of n_emissions: pairs of buckets with at most 32 entries */
     uint64_t peak_bytes;      /* most device memory held at once during the call    */
     uint64_t n_overflow;      /* single-pass pairs past their group's region slots   */
     uint64_t max_group;       /* members of the largest dense group                  */
+    /* more single kernels of the sparse stage (ms, summed over the query
+       partitions): the medium-bucket pair writer, the block-level votes
+       (groups and rows too large for a warp), and, when pairs are counted
+       before they are written, the two counting kernels */
+    float ms_k_medium, ms_k_vote_block, ms_k_count_small, ms_k_count_medium;
 } fast_stats;
 
 /*
@@ -418,6 +424,25 @@ fast_status fast_server_hold_budget(fast_server *srv, uint64_t bytes);
  * instead of running; every other request is unaffected.
  */
 fast_status fast_server_inject_failure(fast_server *srv, uint64_t req_id);
+
+/*
+ * Query-only hashing (§6.4 "Partition", last paragraph: hash only the query
+ * items, then check every other item against their buckets).  d_batch holds
+ * n new windows (ld >= K uint16 each) that follow a station's N0 history
+ * windows d_hist on its timeline (ids N0 .. N0 + n - 1).  Only the batch is
+ * put into hash tables; the history's keys are computed and streamed past
+ * them, so no table of the history is built.  *out receives every pair
+ * (i, j) with j in the batch and i < j (i in the history or the batch),
+ * neither dropped, j - i > excl, votes >= v, sorted by (i, j) -- the same
+ * list as the batch streamed to a server right after that history
+ * (fast_stream_submit).  d_hist_drop: N0 flags (1 = dropped) of the history
+ * windows, e.g. fast_tables_view's drop mask of the history; NULL = none
+ * dropped.  A batch window is dropped when its key falls in a heavy history
+ * bucket (occ_den * size > occ_num * N0, sizes over all N0 history windows)
+ * in more than b/2 tables.  N0 + n < 2^28.  Synchronises `stream`.
+ */
+fast_status fast_query_only(fast_ctx *ctx, const uint16_t *d_hist, uint64_t N0, const uint8_t *d_hist_drop,
+                            const uint16_t *d_batch, uint64_t n, uint32_t ld, fast_result **out, void *stream);
 
 /* ------------------------------------------------------------------ */
 /* Alignment: the steps that take the search's output (§7)             */

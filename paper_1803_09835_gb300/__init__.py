@@ -196,6 +196,12 @@ class Searcher:
     def stats(self) -> dict:
         return fast_get_stats(self.ctx)
 
+    def query_only(self, hist, batch, hist_drop=None, stream=None) -> Result:
+        """Query-only hashing: the batch's pairs against the history (ids continue
+        after it) without building tables of the history."""
+        return Result(_lib.fast_query_only(self.ctx, hist, hist.shape[0], hist_drop, batch, batch.shape[0],
+                                           batch.shape[1], stream))
+
     def channel_merge(self, results, N: int, thr: int, stream=None) -> Merged:
         """Channel level: the channels' Results summed per pair, kept at >= thr."""
         lists = [(r.M, r.i, r.j, r.votes) for r in results]

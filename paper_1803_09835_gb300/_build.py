@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfast.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["fast_api.cu", "k_sig.cu", "k_sort.cu", "k_scan.cu", "k_search.cu", "serve.cu", "plan.cu",
-           "k_align.cu"]
+           "k_align.cu", "k_query.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 

@@ -42,7 +42,9 @@ class fast_stats(ctypes.Structure):
                [("query_parts", ctypes.c_uint32), ("sort_passes", ctypes.c_uint32)] + \
                [(n, ctypes.c_float) for n in ("ms_pair_count", "ms_pair_emit", "ms_vote", "ms_k_pairs", "ms_k_vote")] + \
                [("n_pairs_small", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
-                ("n_overflow", ctypes.c_uint64), ("max_group", ctypes.c_uint64)]
+                ("n_overflow", ctypes.c_uint64), ("max_group", ctypes.c_uint64)] + \
+               [(n, ctypes.c_float) for n in ("ms_k_medium", "ms_k_vote_block", "ms_k_count_small",
+                                              "ms_k_count_medium")]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -109,6 +111,7 @@ def load():
         "fast_stream_release": (st, [vp, u64]),
         "fast_server_inject_failure": (st, [vp, u64]),
         "fast_server_hold_budget": (st, [vp, u64]),
+        "fast_query_only": (st, [vp, vp, u64, vp, vp, u64, u32, pp(vp), vp]),
         "fast_channel_merge": (st, [vp, u64, u32, vp, vp, vp, vp, u32, pp(vp), vp]),
         "fast_merged_view": (st, [vp, pp(u64), pp(vp), pp(vp), pp(vp)]),
         "fast_merged_free": (None, [vp]),
@@ -279,6 +282,13 @@ def fast_result_view(res, owner=None):
 
 def fast_result_free(res):
     load().fast_result_free(res)
+
+
+def fast_query_only(ctx, d_hist, N0: int, d_hist_drop, d_batch, n: int, ld: int, stream=None):
+    out = ctypes.c_void_p()
+    _check(ctx, load().fast_query_only(ctx, _dptr(d_hist), N0, _dptr(d_hist_drop), _dptr(d_batch), n, ld,
+                                       ctypes.byref(out), _stream(stream)))
+    return out
 
 
 def fast_channel_merge(ctx, N: int, lists, thr: int, stream=None):

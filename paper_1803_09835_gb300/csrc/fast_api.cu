@@ -125,8 +125,6 @@ void stats_times(fast_ctx *c, bool whole) {
     s.ms_pair_count = stage_ms(c, 5, 10);
     s.ms_pair_emit = stage_ms(c, 10, 11);
     s.ms_vote = stage_ms(c, 11, 6);
-    s.ms_k_pairs = stage_ms(c, 10, 12);
-    s.ms_k_vote = stage_ms(c, 13, 14);
 }
 
 // Tables and search over keys already in d_sig ([b][N]); the rest of fast_detect.

@@ -169,7 +169,7 @@ struct fast_ctx {
     uint32_t group_slots = 0;   // region slots per row group of the single pass (0 = about twice the expected)
     // instrumentation
     fast_stats stats{};
-    cudaEvent_t ev[16] = {};
+    cudaEvent_t ev[24] = {};
     // host entry: input copied in chunks on a second stream while the signature kernel runs
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t cev[kCopyChunks + 1] = {};

@@ -2231,10 +2231,29 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     unsigned long long *scal = reinterpret_cast<unsigned long long *>(c->d_scal);
     fast_status st;
     const uint64_t ng = (N + (1ull << gshift) - 1) >> gshift;
+    c->stats.ms_k_pairs = c->stats.ms_k_medium = c->stats.ms_k_vote = c->stats.ms_k_vote_block = 0.f;
+    c->stats.ms_k_count_small = c->stats.ms_k_count_medium = 0.f;
+    // the pair buffers live only as long as this function: they are given
+    // back before the detection list is allocated
+    std::vector<std::pair<void *, size_t>> local;
+    struct Freer {
+        fast_ctx *c;
+        cudaStream_t s;
+        std::vector<std::pair<void *, size_t>> &v;
+        ~Freer() {
+            for (auto &x : v) dfree(c, x.first, x.second, s);
+        }
+    } freer{c, s, local};
+    auto lalloc = [&](auto **ptr, size_t count) -> fast_status {
+        using T = std::remove_reference_t<decltype(**ptr)>;
+        fast_status r = dalloc_t(c, ptr, count ? count : 1, s);
+        if (!r) local.push_back({(void *)*ptr, (count ? count : 1) * sizeof(T)});
+        return r;
+    };
     uint32_t *gcnt = nullptr, *gcur = nullptr;
     uint64_t *goff = nullptr;
     PT *ent = nullptr;
-    if ((st = alloc(&gcnt, ng)) || (st = alloc(&gcur, ng)) || (st = alloc(&goff, ng + 1))) return st;
+    if ((st = lalloc(&gcnt, ng)) || (st = lalloc(&gcur, ng)) || (st = lalloc(&goff, ng + 1))) return st;
     cudaMemsetAsync(gcnt, 0, ng * 4, s);
     cudaMemsetAsync(gcur, 0, ng * 4, s);
     // small-bucket pairs: warps over runs of 32-entry tiles
@@ -2266,7 +2285,7 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
         const uint64_t room = room_bytes(c) / 2;
         uint32_t *region = nullptr;
         unsigned long long *ovf = nullptr;
-        if (need <= room && !(st = alloc(&region, ng * cap)) && !(st = alloc(&ovf, ovf_cap))) {
+        if (need <= room && !(st = lalloc(&region, ng * cap)) && !(st = lalloc(&ovf, ovf_cap))) {
             EnumArgs e1 = ea;  // ids flagged from the bitmap, no flagged copy
             e1.fsid = nullptr;
             e1.fsid_out = nullptr;
@@ -2279,11 +2298,14 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
             if (nmedium)
                 k_medium_grp<2, PT><<<mg, 256, 0, s>>>(e1, medium, scal + Scal::NMEDIUM, gshift, nbits, nullptr,
                                                        nullptr, gcur, nullptr, all, rs), FAST_LAUNCHED(c);
+            stage_mark(c, 19, s);
             if ((st = scan_excl(c, gcur, goff, ng, 1, goff + ng, s))) return st;
             cudaMemcpyAsync(&S, goff + ng, 8, cudaMemcpyDeviceToHost, s);
             cudaMemcpyAsync(c->h_scal + Scal::NSMALLEMIT, scal + Scal::NSMALLEMIT, 8, cudaMemcpyDeviceToHost, s);
             cudaMemcpyAsync(c->h_scal + Scal::NOVF, scal + Scal::NOVF, 8, cudaMemcpyDeviceToHost, s);
             if ((st = sync_check(c, s, "pair pass"))) return st;
+            c->stats.ms_k_pairs += stage_ms(c, 10, 12);
+            c->stats.ms_k_medium += stage_ms(c, 12, 19);
             const uint64_t novf = c->h_scal[Scal::NOVF];
             c->stats.n_overflow = novf;
             if (novf <= ovf_cap) {  // the vote reads the regions and the sorted overflow list in place
@@ -2293,7 +2315,7 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
                 if (novf) {
                     unsigned long long *ovf2 = nullptr;
                     uint64_t *srt = nullptr;
-                    if ((st = alloc(&ovf2, novf)) || (st = alloc(&ostart, ng))) return st;
+                    if ((st = lalloc(&ovf2, novf)) || (st = lalloc(&ostart, ng))) return st;
                     if ((st = sort_u64(c, novf, reinterpret_cast<uint64_t *>(ovf), reinterpret_cast<uint64_t *>(ovf2),
                                        32, 32 + bits_for(ng), &srt, s)))
                         return st;
@@ -2314,15 +2336,20 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
         }
     }
     if (!single) {
+        stage_mark(c, 16, s);
         k_pairs_grp<0, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, tpw, gcnt, nullptr, nullptr, nullptr,
                                               scal + Scal::NSMALLEMIT, all), FAST_LAUNCHED(c);
+        stage_mark(c, 17, s);
         if (nmedium)
             k_medium_grp<0, PT><<<mg, 256, 0, s>>>(ea, medium, scal + Scal::NMEDIUM, gshift, nbits, gcnt, nullptr,
                                                    nullptr, nullptr, all), FAST_LAUNCHED(c);
+        stage_mark(c, 18, s);
         if ((st = scan_excl(c, gcnt, goff, ng, 1, goff + ng, s))) return st;
         cudaMemcpyAsync(&S, goff + ng, 8, cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(c->h_scal + Scal::NSMALLEMIT, scal + Scal::NSMALLEMIT, 8, cudaMemcpyDeviceToHost, s);
         if ((st = sync_check(c, s, "pair count"))) return st;
+        c->stats.ms_k_count_small = stage_ms(c, 16, 17);
+        c->stats.ms_k_count_medium = stage_ms(c, 17, 18);
     }
     S_out = S;
     c->stats.n_pairs_small = c->h_scal[Scal::NSMALLEMIT];
@@ -2354,7 +2381,7 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
         for (size_t q = 0; q + 1 < cut.size(); q++) part_max = std::max(part_max, hg[cut[q + 1]] - hg[cut[q]]);
     }
     c->stats.query_parts = (uint32_t)(cut.size() - 1);
-    if (!single && (st = alloc(&ent, part_max))) return st;
+    if (!single && (st = lalloc(&ent, part_max))) return st;
 
     // hash capacity: twice the power of two above the target (group sizes vary), at least 4096
     uint32_t vcap = 64;
@@ -2369,7 +2396,7 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     int wper = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper, k_warp_vote<PT>, kVW * 32, wsm);
     uint2 *slow = nullptr;  // (group, rows r0 << 16 | r1) left to the block kernel
-    if ((st = alloc(&slow, 8 * ng))) return st;
+    if ((st = lalloc(&slow, 8 * ng))) return st;
     const size_t rsm = (size_t)2 * kRowBlockSlots * 4;
     cudaFuncSetAttribute(k_long_vote<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
     uint64_t sp_cap = std::max<uint64_t>(N, 1 << 20);
@@ -2422,7 +2449,14 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
             stage_mark(c, 14, s);
             k_group_vote<PT><<<(unsigned)std::max<uint64_t>(1, (uint64_t)c->num_sms * std::max(vper, 1)), 256, vsm,
                                s>>>(va, ent, slow, scal + Scal::NSLOW), FAST_LAUNCHED(c);
+            stage_mark(c, 15, s);
             if ((st = read_scal(c, s, "row votes"))) return st;
+            if (!single) {  // the single pass's writes were timed with it
+                c->stats.ms_k_pairs += stage_ms(c, 10, 12);
+                c->stats.ms_k_medium += stage_ms(c, 12, 11);
+            }
+            c->stats.ms_k_vote += stage_ms(c, 13, 14);
+            c->stats.ms_k_vote_block += stage_ms(c, 14, 15);
             const uint64_t nlong = c->h_scal[Scal::NLONG];
             if (nlong > N) return set_error(c, FAST_EINTERNAL, "long-row list overflow");
             c->stats.n_long_rows += nlong;
@@ -2444,11 +2478,14 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
                 }
                 uint32_t *gscr = nullptr;
                 uint64_t *d_gofs = nullptr;
-                if ((st = alloc(&gscr, gtot)) || (st = alloc(&d_gofs, nlong))) return st;
+                if ((st = lalloc(&gscr, gtot)) || (st = lalloc(&d_gofs, nlong))) return st;
                 cudaMemcpyAsync(d_gofs, gofs.data(), nlong * 8, cudaMemcpyHostToDevice, s);
+                stage_mark(c, 20, s);
                 k_long_vote<PT><<<(unsigned)std::min<uint64_t>(nlong, c->num_sms * 2), 512, rsm, s>>>(
                     va, ent, long_rows, nlong, gscr, d_gofs), FAST_LAUNCHED(c);
+                stage_mark(c, 21, s);
                 if ((st = read_scal(c, s, "long rows"))) return st;
+                c->stats.ms_k_vote_block += stage_ms(c, 20, 21);
             }
         }
         const uint64_t used = c->h_scal[Scal::CUR_SPARSE];
@@ -2969,6 +3006,8 @@ fast_status search_run(fast_ctx *c, const fast_tables *tb, const uint32_t *d_sig
         return FAST_OK;
     }
     c->stats.max_group = 0;
+    c->stats.ms_k_pairs = c->stats.ms_k_medium = c->stats.ms_k_vote = c->stats.ms_k_vote_block = 0.f;
+    c->stats.ms_k_count_small = c->stats.ms_k_count_medium = 0.f;
     return c->vote_map ? search_map(c, tb, d_sig, out, s) : search_rows(c, tb, d_sig, out, s);
 }
 

@@ -20,6 +20,11 @@ Workloads (all ids are 0-based window indices, 1 window = 1 s lag):
 * ``c4``  N=157,680,000 (5 years); 20,000 templates x U{3..200} at 15 %;
           periodic sources every 30, 60, 90, 3600 and 86400 s at 5 %.
 
+Any workload can draw imbalanced bits (``skew``: bit weights
+(1 + rank)^-skew over a random ranking of the D bits) with co-occurring
+pairs (``corr``: a drawn bit's rank neighbour is set with it at that
+probability), the structure §6.3 blames for oversized buckets.
+
 ``scaled(name, n)`` keeps a workload's shape (densities per window, periods,
 parameters) at a smaller N for tests.
 """
@@ -71,6 +76,8 @@ class Workload:
     tpl_seed: int = 0
     place_range: int = 0
     tpl_offset_max: int = 0
+    skew: float = 0.0  # bit weights (1 + rank)^-skew over a random ranking of the D bits (0 = uniform)
+    corr: float = 0.0  # probability that a drawn bit's partner (neighbouring rank) is set with it
     extra: dict = field(default_factory=dict, compare=False)
 
     def params(self) -> dict:
@@ -126,7 +133,7 @@ def _load():
                                    u64, u64, u32, i32, vp]
     lib.synth_generate_rows.restype = i32
     lib.synth_generate_rows.argtypes = [u64, u64, u64, u32, u32, vp, u32, u64, u32, vp, dbl, u32, u32, u32, dbl,
-                                        u64, u64, u32, i32, vp]
+                                        u64, u64, u32, i32, vp, dbl, dbl]
     return lib
 
 
@@ -134,7 +141,7 @@ def build() -> str:
     """Compile gen.c into libsynth.so (plain C, no GPU)."""
     tmp = _LIB + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC", "-pthread",
-                           _SRC, "-o", tmp])
+                           _SRC, "-o", tmp, "-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -168,7 +175,7 @@ def generate(w: Workload, ld: int | None = None, out=None, threads: int = 0, own
     rc = _lib.synth_generate_rows(w.N, r0, n, w.D, w.K, ptr, ld, w.seed, len(w.periods), periods, w.per_redraw,
                                   w.n_templates, w.rep_lo, w.rep_hi, w.tpl_redraw, w.tpl_seed or w.seed,
                                   w.place_range, w.tpl_offset_max, threads,
-                                  own.ctypes.data if owner else None)
+                                  own.ctypes.data if owner else None, float(w.skew), float(w.corr))
     if rc < 0:
         raise ValueError("synth_generate: bad arguments")
     return (out, own) if owner else out

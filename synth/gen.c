@@ -25,6 +25,7 @@
  * draw is a pure function of (seed, stream, counter), so rows are generated
  * independently and in parallel, identically on every machine.
  */
+#include <math.h>
 #include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -63,7 +64,23 @@ static uint64_t syn_below(syn_rng *g, uint64_t m)
 }
 
 enum { DOM_ROW = 1, DOM_PBASE = 2, DOM_PPHASE = 3, DOM_TBASE = 4, DOM_TPLACE = 5, DOM_NOISE = 6,
-       DOM_TOFF = 7 };
+       DOM_TOFF = 7, DOM_SKEW = 8 };
+
+/*
+ * Optional imbalance of the bits (the paper's observation that some
+ * fingerprint elements are non-zero far more often than others, and that
+ * some co-occur, §6.3 "Cause of hash collisions"): bit x has weight
+ * (1 + rank(x))^-skew, ranks a random permutation of [0, D) drawn from the
+ * station seed; after a bit is drawn, its partner -- the bit of the
+ * neighbouring rank, rank ^ 1 -- is also set with probability corr.
+ * skew = corr = 0 is the uniform generator, draw for draw.
+ */
+typedef struct {
+    const double *cdf;    /* cdf[r] = total weight of ranks 0..r; NULL = uniform */
+    const uint16_t *bit;  /* bit of rank r */
+    const uint16_t *rank; /* rank of bit x */
+    double corr;
+} syn_skew;
 
 #define OWNER_RANDOM 0u
 #define OWNER_PERIODIC (1u << 30)
@@ -83,24 +100,54 @@ static uint32_t syn_emit(const uint64_t *bm, uint32_t D, uint16_t *out)
     return n;
 }
 
-/* Uniform random K-subset of [0, D), ascending. */
-static void syn_subset(syn_rng *g, uint32_t D, uint32_t K, uint64_t *bm, uint16_t *out)
+/* One bit: uniform on [0, D), or by the skew weights. */
+static uint32_t syn_draw(syn_rng *g, const syn_skew *sk, uint32_t D)
+{
+    if (!sk || !sk->cdf) return (uint32_t)syn_below(g, D);
+    const double u = (double)(syn_next(g) >> 11) * (1.0 / 9007199254740992.0) * sk->cdf[D - 1];
+    uint32_t lo = 0, hi = D - 1; /* first rank whose cumulative weight exceeds u */
+    while (lo < hi) {
+        const uint32_t m = (lo + hi) / 2;
+        if (sk->cdf[m] > u) hi = m;
+        else lo = m + 1;
+    }
+    return sk->bit[lo];
+}
+
+/* Sets bit x unless set; with skew and corr > 0 also, at probability corr,
+ * its partner (while fewer than `want` bits are set).  Returns the bits added. */
+static uint32_t syn_take(syn_rng *g, const syn_skew *sk, uint32_t D, uint64_t *bm, uint32_t x, uint32_t have,
+                         uint32_t want)
+{
+    if (bm[x >> 6] >> (x & 63) & 1) return 0;
+    bm[x >> 6] |= 1ULL << (x & 63);
+    uint32_t added = 1;
+    if (sk && sk->cdf && sk->corr > 0 && have + 1 < want) {
+        const double c = (double)(syn_next(g) >> 11) * (1.0 / 9007199254740992.0);
+        const uint32_t r = sk->rank[x] ^ 1u;
+        if (c < sk->corr && r < D) {
+            const uint32_t y = sk->bit[r];
+            if (!(bm[y >> 6] >> (y & 63) & 1)) {
+                bm[y >> 6] |= 1ULL << (y & 63);
+                added++;
+            }
+        }
+    }
+    return added;
+}
+
+/* Random K-subset of [0, D) (uniform, or by the skew), ascending. */
+static void syn_subset(syn_rng *g, const syn_skew *sk, uint32_t D, uint32_t K, uint64_t *bm, uint16_t *out)
 {
     memset(bm, 0, sizeof(uint64_t) * ((D + 63) / 64));
     uint32_t have = 0;
-    while (have < K) {
-        uint32_t x = (uint32_t)syn_below(g, D);
-        if (!(bm[x >> 6] >> (x & 63) & 1)) {
-            bm[x >> 6] |= 1ULL << (x & 63);
-            have++;
-        }
-    }
+    while (have < K) have += syn_take(g, sk, D, bm, syn_draw(g, sk, D), have, K);
     syn_emit(bm, D, out);
 }
 
 /* Noisy copy of the ascending K-set `base`: remove m = round(x*K) uniformly
  * chosen members, then add m uniform bits of D outside the remaining set. */
-static void syn_copy(syn_rng *g, const uint16_t *base, uint32_t D, uint32_t K, double x,
+static void syn_copy(syn_rng *g, const syn_skew *sk, const uint16_t *base, uint32_t D, uint32_t K, double x,
                      uint64_t *bm, uint32_t *perm, uint16_t *out)
 {
     uint32_t m = (uint32_t)(x * K + 0.5);
@@ -116,13 +163,7 @@ static void syn_copy(syn_rng *g, const uint16_t *base, uint32_t D, uint32_t K, d
     for (uint32_t k = m; k < K; k++) bm[base[perm[k]] >> 6] |= 1ULL << (base[perm[k]] & 63);
     /* the removed bits may come back: D minus the *remaining* set is eligible */
     uint32_t added = 0;
-    while (added < m) {
-        uint32_t y = (uint32_t)syn_below(g, D);
-        if (!(bm[y >> 6] >> (y & 63) & 1)) {
-            bm[y >> 6] |= 1ULL << (y & 63);
-            added++;
-        }
-    }
+    while (added < m) added += syn_take(g, sk, D, bm, syn_draw(g, sk, D), added, m);
     syn_emit(bm, D, out);
 }
 
@@ -133,6 +174,7 @@ typedef struct {
     const uint32_t *owner; /* indexed by w - row0 */
     const uint16_t *pbase, *tbase;
     double per_redraw, tpl_redraw;
+    const syn_skew *sk;
 } syn_job;
 
 static void *syn_worker(void *arg)
@@ -146,13 +188,13 @@ static void *syn_worker(void *arg)
         uint32_t kind = own & (3u << 30), id = own & ((1u << 30) - 1);
         if (kind == OWNER_RANDOM) {
             syn_rng g = {syn_stream(j->seed, DOM_ROW, w), 0};
-            syn_subset(&g, j->D, j->K, bm, row);
+            syn_subset(&g, j->sk, j->D, j->K, bm, row);
         } else {
             syn_rng g = {syn_stream(j->seed, DOM_NOISE, w), 0};
             if (kind == OWNER_PERIODIC)
-                syn_copy(&g, j->pbase + (uint64_t)id * j->K, j->D, j->K, j->per_redraw, bm, perm, row);
+                syn_copy(&g, j->sk, j->pbase + (uint64_t)id * j->K, j->D, j->K, j->per_redraw, bm, perm, row);
             else
-                syn_copy(&g, j->tbase + (uint64_t)id * j->K, j->D, j->K, j->tpl_redraw, bm, perm, row);
+                syn_copy(&g, j->sk, j->tbase + (uint64_t)id * j->K, j->D, j->K, j->tpl_redraw, bm, perm, row);
         }
         for (uint32_t k = j->K; k < j->ld; k++) row[k] = 0xFFFF; /* row padding */
     }
@@ -180,10 +222,38 @@ int synth_generate_rows(uint64_t N, uint64_t row0, uint64_t nrows, uint32_t D, u
                         uint32_t ld, uint64_t seed, uint32_t n_periodic, const uint64_t *periods,
                         double per_redraw, uint32_t n_templates, uint32_t rep_lo, uint32_t rep_hi,
                         double tpl_redraw, uint64_t tpl_seed, uint64_t place_range, uint32_t tpl_offset_max,
-                        int nthreads, uint32_t *owner_out)
+                        int nthreads, uint32_t *owner_out, double skew, double corr)
 {
     if (D == 0 || D > 65536 || K == 0 || K > D || ld < K || rep_hi < rep_lo) return -1;
     if (row0 > N || nrows > N - row0) return -1;
+    if (!(skew >= 0) || !(corr >= 0 && corr <= 1)) return -1;
+    /* the skew: ranks drawn from the station seed (a Fisher-Yates shuffle) */
+    syn_skew skv = {NULL, NULL, NULL, corr};
+    double *cdf = NULL;
+    uint16_t *sbit = NULL, *srank = NULL;
+    if (skew > 0) {
+        cdf = malloc(sizeof(double) * D);
+        sbit = malloc(sizeof(uint16_t) * D);
+        srank = malloc(sizeof(uint16_t) * D);
+        for (uint32_t x = 0; x < D; x++) sbit[x] = (uint16_t)x;
+        syn_rng q = {syn_stream(seed, DOM_SKEW, 0), 0};
+        for (uint32_t x = D - 1; x > 0; x--) {
+            const uint32_t y = (uint32_t)syn_below(&q, (uint64_t)x + 1);
+            const uint16_t t = sbit[x];
+            sbit[x] = sbit[y];
+            sbit[y] = t;
+        }
+        double acc = 0;
+        for (uint32_t r = 0; r < D; r++) {
+            acc += pow(1.0 + r, -skew);
+            cdf[r] = acc;
+            srank[sbit[r]] = (uint16_t)r;
+        }
+        skv.cdf = cdf;
+        skv.bit = sbit;
+        skv.rank = srank;
+    }
+    const syn_skew *sk = skew > 0 ? &skv : NULL;
     if (place_range == 0) place_range = N;
     const uint64_t row1 = row0 + nrows;
     uint32_t *owner = owner_out ? owner_out : malloc(sizeof(uint32_t) * (nrows ? nrows : 1));
@@ -193,7 +263,7 @@ int synth_generate_rows(uint64_t N, uint64_t row0, uint64_t nrows, uint32_t D, u
     uint16_t *pbase = malloc(sizeof(uint16_t) * (uint64_t)K * (n_periodic ? n_periodic : 1));
     for (uint32_t p = 0; p < n_periodic; p++) {
         syn_rng g = {syn_stream(seed, DOM_PBASE, p), 0};
-        syn_subset(&g, D, K, bm, pbase + (uint64_t)p * K);
+        syn_subset(&g, sk, D, K, bm, pbase + (uint64_t)p * K);
         syn_rng h = {syn_stream(seed, DOM_PPHASE, p), 0};
         uint64_t P = periods[p] ? periods[p] : 1;
         uint64_t w = syn_below(&h, P);
@@ -204,7 +274,7 @@ int synth_generate_rows(uint64_t N, uint64_t row0, uint64_t nrows, uint32_t D, u
     uint16_t *tbase = malloc(sizeof(uint16_t) * (uint64_t)K * (n_templates ? n_templates : 1));
     for (uint32_t t = 0; t < n_templates; t++) {
         syn_rng g = {syn_stream(tpl_seed, DOM_TBASE, t), 0};
-        syn_subset(&g, D, K, bm, tbase + (uint64_t)t * K);
+        syn_subset(&g, sk, D, K, bm, tbase + (uint64_t)t * K);
         syn_rng pl = {syn_stream(tpl_seed, DOM_TPLACE, t), 0};
         uint32_t reps = rep_lo + (uint32_t)syn_below(&pl, (uint64_t)(rep_hi - rep_lo) + 1);
         syn_rng off = {syn_stream(seed, DOM_TOFF, t), 0};
@@ -226,7 +296,7 @@ int synth_generate_rows(uint64_t N, uint64_t row0, uint64_t nrows, uint32_t D, u
     syn_job *jobs = malloc(sizeof(syn_job) * T);
     for (int k = 0; k < T; k++) {
         jobs[k] = (syn_job){N,   row0 + nrows * k / T, row0 + nrows * (k + 1) / T, row0, seed, D, K, ld,
-                            out, owner, pbase, tbase, per_redraw, tpl_redraw};
+                            out, owner, pbase, tbase, per_redraw, tpl_redraw, sk};
         pthread_create(&th[k], NULL, syn_worker, &jobs[k]);
     }
     for (int k = 0; k < T; k++) pthread_join(th[k], NULL);
@@ -234,6 +304,9 @@ int synth_generate_rows(uint64_t N, uint64_t row0, uint64_t nrows, uint32_t D, u
     free(jobs);
     free(pbase);
     free(tbase);
+    free(cdf);
+    free(sbit);
+    free(srank);
     if (!owner_out) free(owner);
     return T;
 }
@@ -246,5 +319,6 @@ int synth_generate(uint64_t N, uint32_t D, uint32_t K, uint16_t *out, uint32_t l
                    int nthreads, uint32_t *owner_out)
 {
     return synth_generate_rows(N, 0, N, D, K, out, ld, seed, n_periodic, periods, per_redraw, n_templates, rep_lo,
-                               rep_hi, tpl_redraw, tpl_seed, place_range, tpl_offset_max, nthreads, owner_out);
+                               rep_hi, tpl_redraw, tpl_seed, place_range, tpl_offset_max, nthreads, owner_out, 0.0,
+                               0.0);
 }

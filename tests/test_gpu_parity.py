@@ -111,6 +111,9 @@ DETECT_CASES = [
     ("c4", 50_000, dict(table_group=10), dict(large_min=32)),
     ("c4", 50_000, dict(table_group=10, query_part=5), dict()),
     ("c1", 20_000, dict(table_group=7), dict(single_pass=0)),  # 100 = 14 x 7 + 2: a short last group
+    # imbalanced, co-occurring bits (§6.3): large background buckets
+    ("c1", 30_000, dict(skew=0.6, corr=0.3), dict()),
+    ("c1", 30_000, dict(skew=0.3, r=8, v=3), dict()),
 ]
 
 

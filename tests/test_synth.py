@@ -62,3 +62,40 @@ def test_row_ranges_equal_the_whole_station():
     import pytest
     with pytest.raises(ValueError):
         synth.generate(w, rows=(10, 50_001))
+
+
+def _bit_stats(a, D=8192, top=300):
+    f = np.bincount(a.ravel(), minlength=D) / len(a)
+    idx = np.argsort(f)[::-1][:top]
+    m = np.zeros((len(a), D), bool)
+    m[np.arange(len(a))[:, None], a] = True
+    x = m[:, idx].astype(np.float64)
+    p = x.mean(0)
+    lift = (x.T @ x / len(a)) / np.outer(p, p)
+    np.fill_diagonal(lift, 0)
+    return f, lift
+
+
+def test_skewed_and_correlated_bits():
+    # §6.3: some fingerprint elements are non-zero far more often than
+    # others, and some co-occur; the generator's skew and corr draw that
+    from dataclasses import replace
+    w = replace(synth.scaled("c1", 20_000), n_templates=0, periods=())
+    uni = synth.generate(w)
+    assert np.array_equal(uni, synth.generate(replace(w, skew=0.0, corr=0.0)))
+    f0, l0 = _bit_stats(uni)
+    assert f0.max() < 0.1 and l0.max() < 2.0
+    sk = synth.generate(replace(w, skew=0.6))
+    assert np.all(np.diff(sk.astype(np.int32), axis=1) > 0) and sk.max() < w.D
+    f1, l1 = _bit_stats(sk)
+    top1 = np.sort(f1)[::-1][:w.D // 100].sum() / f1.sum()
+    assert f1.max() > 0.5 and top1 > 5 * 0.01 * 1.5  # the top 1 % of bits hold several times their share
+    assert l1.max() < 1.5                            # imbalance alone adds no co-occurrence
+    co = synth.generate(replace(w, skew=0.6, corr=0.5))
+    _, l2 = _bit_stats(co)
+    assert l2.max() > 3.0                            # partners co-occur
+    # noisy copies keep exactly K bits under the skew too
+    ws = replace(synth.scaled("c1", 20_000), skew=0.6, corr=0.3)
+    a, own = synth.generate(ws, owner=True)
+    assert np.all(np.diff(a.astype(np.int32), axis=1) > 0)
+    assert (own >= synth.OWNER_TEMPLATE).sum() > 0
