@@ -733,6 +733,76 @@ def sweep_arm(args):
     return 0
 
 
+# ------------------------------------------------------------------ alignment
+
+def align_arm(args):
+    """The steps after the search (§7.1, §7.2) on one 3-month station
+    searched three times with independent hash families (its three
+    channels): channel level (fast_channel_merge: the lists summed per pair,
+    threshold 3v) and station level (fast_station_clusters on the merged
+    list).  Device time by CUDA events over --steps runs after --warmup."""
+    import torch
+
+    import synth
+    from paper_1803_09835_gb300 import Searcher
+    torch.cuda.set_device(0)
+    w = synth.scaled("c1", args.n) if args.n else synth.workload("c1")
+    d = torch.from_numpy(synth.generate(w, ld=400)).cuda()
+    ctxs, lists = [], []
+    for k in range(3):
+        s = Searcher(dict(w.params(), seed=w.params()["seed"] + 1000 * k))
+        ctxs.append(s)
+        lists.append(s.detect(d))
+    del d
+    torch.cuda.empty_cache()
+    s = ctxs[0]
+    thr = 3 * w.v
+    T = sum(r.M for r in lists)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t_merge = t_clu = 0.0
+    for k in range(args.warmup + args.steps):
+        ev[0].record()
+        m = s.channel_merge(lists, N=w.N, thr=thr)
+        ev[1].record()
+        c = s.station_clusters(m, gap=args.gap, width=args.width, min_n=args.min_n)
+        ev[2].record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            t_merge += ev[0].elapsed_time(ev[1])
+            t_clu += ev[1].elapsed_time(ev[2])
+        M, nc = m.M, c.n
+        c.free()
+        m.free()
+    t_merge /= args.steps
+    t_clu /= args.steps
+    hbm = float(_peaks().get("hbm_gbs", 6800.0))
+    merge_bytes = T * 9 + M * 10      # read every channel's (i, j, votes), write (i, j, sim)
+    clu_bytes = M * 10 + nc * 48      # read the merged list, write 6 x 8 bytes per cluster
+    line = {"metric": "alignment entries/s (channel merge + station clusters)", "unit": "entries/s",
+            "value": T / ((t_merge + t_clu) / 1000), "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "data": "synthetic", "dtype": "u32",
+            "config": {"workload": f"{w.name}: {w.N:,} windows, three channels = three hash seeds, "
+                                   f"merge threshold {thr}, clusters gap={args.gap} width={args.width} "
+                                   f"min_n={args.min_n}",
+                       "channel_entries": T, "merged_entries": M, "clusters": nc},
+            "channel_merge": {"ms": t_merge, "entries_per_s": T / (t_merge / 1000),
+                              "roofline": {"bound": "hbm", "achieved": merge_bytes / (t_merge / 1000) / 1e9,
+                                           "peak": hbm, "unit": "GB/s",
+                                           "frac": merge_bytes / (t_merge / 1000) / 1e9 / hbm,
+                                           "algorithmic_bytes": merge_bytes}},
+            "station_clusters": {"ms": t_clu, "entries_per_s": M / (t_clu / 1000),
+                                 "roofline": {"bound": "hbm", "achieved": clu_bytes / (t_clu / 1000) / 1e9,
+                                              "peak": hbm, "unit": "GB/s",
+                                              "frac": clu_bytes / (t_clu / 1000) / 1e9 / hbm,
+                                              "algorithmic_bytes": clu_bytes}}}
+    for r in lists:
+        r.free()
+    for c_ in ctxs:
+        c_.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ serving leg
 
 def serving_arm(args):
@@ -839,6 +909,10 @@ def main():
     ap.add_argument("--duration", type=float, default=5.0)
     ap.add_argument("--budget-gb", type=int, default=150)
     ap.add_argument("--plain-requests", type=int, default=3)
+    ap.add_argument("--align", action="store_true", help="channel merge + station clusters on three searches")
+    ap.add_argument("--gap", type=int, default=5)
+    ap.add_argument("--width", type=int, default=3)
+    ap.add_argument("--min-n", type=int, default=2)
     ap.add_argument("--sweep", action="store_true", help="bucket statistics vs r on uniform and skewed fingerprints")
     ap.add_argument("--no-c1", action="store_true", help="skip the single-station diagnostic beside the headline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host memory) leg of the headline")
@@ -855,6 +929,8 @@ def main():
         return serving_arm(args)
     if args.sweep:
         return sweep_arm(args)
+    if args.align:
+        return align_arm(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -134,6 +134,9 @@ typedef struct {
        (groups and rows too large for a warp), and, when pairs are counted
        before they are written, the two counting kernels */
     float ms_k_medium, ms_k_vote_block, ms_k_count_small, ms_k_count_medium;
+    uint32_t dense_fallback;  /* 1 when the cluster-mask scratch did not fit and every
+                                 dense group was voted by direct key comparison   */
+    uint32_t large_min;       /* the dense-group threshold the search used         */
 } fast_stats;
 
 /*

@@ -44,7 +44,8 @@ class fast_stats(ctypes.Structure):
                [("n_pairs_small", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
                 ("n_overflow", ctypes.c_uint64), ("max_group", ctypes.c_uint64)] + \
                [(n, ctypes.c_float) for n in ("ms_k_medium", "ms_k_vote_block", "ms_k_count_small",
-                                              "ms_k_count_medium")]
+                                              "ms_k_count_medium")] + \
+               [("dense_fallback", ctypes.c_uint32), ("large_min", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -2524,6 +2524,7 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
     c->stats.n_dropped = tb->n_dropped;
     c->stats.n_long_rows = c->stats.n_huge_rows = c->stats.max_row = 0;
     c->stats.query_parts = 1;
+    c->stats.dense_fallback = 0;
     uint32_t large_min = large_min_for(c, N);
     const unsigned blocksN = std::max(1u, std::min<unsigned>(ceil_div(N, 256), c->num_sms * 8));
 
@@ -2560,6 +2561,7 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
         if ((st = read_scal(c, s, "bucket classify"))) return fail(st);
     }
     const uint64_t nlarge = c->h_scal[Scal::NLARGE], nmedium = c->h_scal[Scal::NMEDIUM];
+    c->stats.large_min = large_min;
     stage_mark(c, 4, s);
 
     // ---- dense groups: labels, members, keys, tile schedule, per-row counts
@@ -2681,6 +2683,7 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
             c->err.clear();
             MB = nullptr;
             cudaMemsetAsync(gover, 0x01, ngroups * 4, s);  // every group by direct comparison
+            c->stats.dense_fallback = 1;
         }
         cudaFuncSetAttribute(k_dense_rowcount, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
         const unsigned dg = (unsigned)std::min<uint64_t>(tiles.size(), (uint64_t)c->num_sms * 4);

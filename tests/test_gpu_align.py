@@ -98,19 +98,19 @@ def _three_channels(n):
     w = synth.scaled("c1", n)
     idx = synth.generate(w, ld=400)
     ps = [dict(w.params(), seed=w.params()["seed"] + 1000 * k) for k in range(3)]
-    gpu, want = [], []
+    gpu, want, ctxs = [], [], []
     for p in ps:
         s = _searcher(p)
+        ctxs.append(s)  # a result may not outlive the context that made it
         gpu.append(s.detect(torch.from_numpy(idx).cuda()))
         keys = oracle.keys(p, idx)
         want.append(oracle.search(p, keys, oracle.drop(p, keys)))
         _eq(gpu[-1].numpy(), want[-1])
-        s.close()
-    return w, gpu, want
+    return w, gpu, want, ctxs
 
 
 def test_channel_merge_then_station_clusters_on_three_searches():
-    w, gpu, want = _three_channels(60_000)
+    w, gpu, want, ctxs = _three_channels(60_000)
     assert all(len(x[0]) > 0 for x in want)
     s = _searcher(w.params())
     for thr in (0, w.v + 1, 3 * w.v):
@@ -125,6 +125,8 @@ def test_channel_merge_then_station_clusters_on_three_searches():
         m.free()
     for r in gpu:
         r.free()
+    for c in ctxs:
+        c.close()
     s.close()
 
 

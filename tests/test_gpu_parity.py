@@ -182,6 +182,41 @@ def test_row_partitions_identical_and_forced_by_budget():
     assert split >= 1
 
 
+def test_dense_votes_fall_back_when_the_cluster_scratch_does_not_fit():
+    # budgets from the unconstrained peak down: every search either reports
+    # the budget or gives the oracle's list; somewhere in between the cluster
+    # masks no longer fit, the dense groups are voted by direct key
+    # comparison, and the list is still exact
+    from paper_1803_09835_gb300 import FastError, Searcher, _lib
+    w = synth.scaled("c1", 30_000)
+    idx = synth.generate(w, ld=400)
+    d = torch.from_numpy(idx).cuda()
+    p = w.params()
+    s = _searcher(p, large_min=16)
+    s.detect(d).free()
+    st = s.stats()
+    peak = st["peak_bytes"]
+    assert st["n_groups"] > 0 and st["dense_fallback"] == 0
+    s.close()
+    _, _, want = _oracle_run(p, idx, w.K)
+    ok = fallback = 0
+    for k in range(40):
+        budget = int(peak * (1 - 0.015 * k))
+        sb = Searcher(p, hbm_budget_bytes=budget, large_min=16)
+        try:
+            r = sb.detect(d)
+        except FastError as e:
+            assert e.status in (_lib.FAST_EBUDGET, _lib.FAST_ENOMEM)
+            sb.close()
+            continue
+        _assert_lists(r.numpy(), want)
+        r.free()
+        ok += 1
+        fallback += sb.stats()["dense_fallback"]
+        sb.close()
+    assert ok > 1 and fallback >= 1
+
+
 @pytest.mark.parametrize("name,n,over", [("c1", 60_000, dict()), ("c0", 8192, dict(v=1, excl=0))])
 def test_single_pass_and_overflow_identical(name, n, over):
     # pairs written once into fixed group regions (default), counted then
@@ -279,6 +314,7 @@ def test_chunked_signatures_and_fill_failure():
                             chunk_rows=6000)
     _, _, want = _oracle_run(p, idx, w.K)
     _assert_lists(good.numpy(), want)
+    good.free()
     s.close()
 
 
