@@ -2560,9 +2560,7 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
             FAST_LAUNCHED(c);
         if ((st = read_scal(c, s, "bucket classify"))) return fail(st);
     }
-    const uint64_t nlarge = c->h_scal[Scal::NLARGE], nmedium = c->h_scal[Scal::NMEDIUM];
-    c->stats.large_min = large_min;
-    stage_mark(c, 4, s);
+    uint64_t nlarge = c->h_scal[Scal::NLARGE], nmedium = c->h_scal[Scal::NMEDIUM];
 
     // ---- dense groups: labels, members, keys, tile schedule, per-row counts
     uint32_t *label = nullptr, *GT = nullptr, *ids = nullptr, *dense_cnt = nullptr;
@@ -2574,9 +2572,22 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
     DenseStrip *d_strips = nullptr;
     const size_t dsm = (size_t)2 * nb * kDT * 4;
     if ((st = alloc(&label, N)) || (st = alloc(&dense_cnt, N))) return fail(st);
-    cudaMemsetAsync(label, 0xFF, N * 4, s);
     cudaMemsetAsync(dense_cnt, 0, N * 4, s);
-    if (nlarge) {
+    std::vector<uint64_t> hm;
+    uint64_t *sorted = nullptr;  // members as (group << 32 | id), sorted
+    // Groups are the connected components of the large buckets.  With the
+    // automatic threshold a group must stay dense: comparing all its member
+    // pairs may not cost more than the large buckets' own pairs (which the
+    // sparse path would count); a group chained from many mid-size buckets
+    // fails that, and the threshold doubles (measured on a 40,000,000-window
+    // station of the 5-year shape: one 465,786-member group, 1.1e11 pair
+    // comparisons, 2.55 s; after the check a 12,641-member group, 1.35 s;
+    // identical lists).
+    for (int round = 0;; round++) {
+        cudaMemsetAsync(label, 0xFF, N * 4, s);
+        nm = 0;
+        hm.clear();
+        if (!nlarge) break;
         const unsigned lg = (unsigned)std::min<uint64_t>(nlarge, c->num_sms * 8);
         k_label_init<<<lg, 256, 0, s>>>(large, nlarge, tb->d_sid, tb->d_drop, N, label), FAST_LAUNCHED(c);
         int it = 0;
@@ -2595,13 +2606,37 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
         if ((st = read_scal(c, s, "group members"))) return fail(st);
         nm = c->h_scal[Scal::NMEMB];
         if ((st = alloc(&memb2, nm))) return fail(st);
-        uint64_t *sorted = nullptr;
         if ((st = sort_u64(c, nm, reinterpret_cast<uint64_t *>(memb), reinterpret_cast<uint64_t *>(memb2), 0,
                            32 + bits_for(N), &sorted, s)))
             return fail(st);
-        std::vector<uint64_t> hm(nm);
+        hm.resize(nm);
+        std::vector<uint4> hl(nlarge);
         cudaMemcpyAsync(hm.data(), sorted, nm * 8, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(hl.data(), large, nlarge * sizeof(uint4), cudaMemcpyDeviceToHost, s);
         if ((st = sync_check(c, s, "group members copy"))) return fail(st);
+        if (c->large_min || round >= 8) break;
+        uint64_t gp = 0, lp = 0;  // member pairs of the groups, pairs of the large buckets
+        for (uint64_t g0 = 0, g1; g0 < nm; g0 = g1) {
+            for (g1 = g0 + 1; g1 < nm && (hm[g1] >> 32) == (hm[g0] >> 32); g1++) {
+            }
+            gp += (g1 - g0) * (g1 - g0 - 1) / 2;
+        }
+        for (const uint4 &e : hl) lp += (uint64_t)e.w * (e.w - 1) / 2;
+        if (gp <= lp) break;
+        large_min = large_min < (1u << 30) ? 2 * large_min : large_min + 1;  // and classify again
+        cudaMemsetAsync(scal + Scal::NLARGE, 0, 8, s);
+        cudaMemsetAsync(scal + Scal::NMEDIUM, 0, 8, s);
+        cudaMemsetAsync(scal + Scal::PART0, 0, 8 * (kScal - Scal::PART0), s);
+        k_big_classify<<<cg, 256, 0, s>>>(ea, big, scal + Scal::NBIG, big_cap, large_min, large,
+                                          scal + Scal::NLARGE, medium, scal + Scal::NMEDIUM, scal + Scal::PART0),
+            FAST_LAUNCHED(c);
+        if ((st = read_scal(c, s, "bucket classify"))) return fail(st);
+        nlarge = c->h_scal[Scal::NLARGE];
+        nmedium = c->h_scal[Scal::NMEDIUM];
+    }
+    c->stats.large_min = large_min;
+    stage_mark(c, 4, s);
+    if (nlarge) {
         if ((st = alloc(&GT, (size_t)nm * nb)) || (st = alloc(&ids, nm))) return fail(st);
         k_gather_keys<<<std::max(1u, std::min<unsigned>(ceil_div(nm, 128), c->num_sms * 8)), 128, 0, s>>>(
             reinterpret_cast<unsigned long long *>(sorted), nm, d_sig, N, nb, GT, ids), FAST_LAUNCHED(c);
