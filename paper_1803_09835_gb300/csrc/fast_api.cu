@@ -40,10 +40,19 @@ fast_status dalloc(fast_ctx *c, void **p, size_t bytes, cudaStream_t s) {
         return set_error(c, FAST_EBUDGET,
                          "HBM budget exceeded: " + std::to_string(c->live + bytes) + " > " + std::to_string(c->budget));
     cudaError_t e = cudaMallocFromPoolAsync(p, bytes, c->pool, s);
+    if (e == cudaErrorMemoryAllocation && !c->capturing) {
+        // the pool's cached blocks may be free but too fragmented for this
+        // request: give them back to the driver and try once more
+        cudaGetLastError();
+        cudaStreamSynchronize(s);
+        cudaMemPoolTrimTo(c->pool, 0);
+        e = cudaMallocFromPoolAsync(p, bytes, c->pool, s);
+    }
     if (e != cudaSuccess) {
         *p = nullptr;
         const std::string what = "device allocation of " + std::to_string(bytes) + " bytes (" +
-                                 std::to_string(c->live) + " held)";
+                                 std::to_string(c->live) + " held, after stage mark " +
+                                 std::to_string(c->last_stage) + ")";
         return cuda_fail(c, e, what.c_str());
     }
     c->live += bytes;
@@ -81,6 +90,7 @@ static thread_local uint32_t g_marked = 0;  // stage slots recorded by the curre
 void stage_reset() { g_marked = 0; }
 
 void stage_mark(fast_ctx *c, int slot, cudaStream_t s) {
+    c->last_stage = slot;
     if (!c->timing || c->capturing) return;
     cudaEventRecord(c->ev[slot], s);
     g_marked |= 1u << slot;

@@ -179,6 +179,7 @@ struct fast_ctx {
     size_t h_stage_bytes = 0;
     cudaEvent_t chev[4] = {};
     bool timing = true;
+    int last_stage = 0;  // the most recent stage mark (named in allocation failures)
     std::string err;
 };
 

@@ -854,38 +854,67 @@ __global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, const uint4 *__r
             if (s_lab[x] == kNone || s_lab[x] != s_lab[0]) s_mixed = 1;
         __syncthreads();
         if (s_mixed) {  // block-uniform
+            // A warp takes 32 consecutive rows, a lane each.  Members are in
+            // ascending id order, so a row's partners past the near-time
+            // exclusion are one contiguous range [y0, nl), found by binary
+            // search; only a dense-group member has to skip partners of its
+            // own group.  The lanes reserve their rows' slots together, then
+            // the warp writes row after row with consecutive stores.
             for (;;) {
-                uint32_t x = 0;
-                if (lane == 0) x = atomicAdd(&s_next, 1u);
-                x = __shfl_sync(~0u, x, 0);
-                if (x + 1 >= nl) break;  // warp-uniform
-                const uint32_t i = s_id[x], li = s_lab[x], g = i >> gshift;
-                if (MODE == 1 && !gr.has(g)) continue;  // warp-uniform: one row per warp
-                uint32_t c = 0;
-                for (uint32_t y = x + 1 + lane; y < nl; y += 32) {
-                    const uint32_t lj = s_lab[y];
-                    c += s_id[y] - i > a.excl && (li == kNone || li != lj);
-                }
-#pragma unroll
-                for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(~0u, c, o);
-                if (!c) continue;
-                if (MODE == 0) {
-                    if (lane == 0) atomicAdd(gcnt + g, c);
-                } else {
-                    uint64_t o = 0;
-                    if (lane == 0) o = MODE == 2 ? atomicAdd(gcur + g, c) : goff[g] - gr.ebase + atomicAdd(gcur + g, c);
-                    o = __shfl_sync(~0u, o, 0);
-                    for (uint32_t y0 = x + 1; y0 < nl; y0 += 32) {
-                        const uint32_t y = y0 + lane;
-                        const uint32_t j = y < nl ? s_id[y] : 0u;
-                        const bool keep = y < nl && j - i > a.excl && (li == kNone || li != s_lab[y]);
-                        const uint32_t m = __ballot_sync(~0u, keep);
-                        if (keep) {
-                            const uint64_t slot = o + __popc(m & ((1u << lane) - 1));
-                            if (MODE == 2) rs.put(g, slot, (uint32_t)pack_entry<PT>(i & lmask, j, nbits));
-                            else ent[slot] = pack_entry<PT>(i & lmask, j, nbits);
+                uint32_t x0 = 0;
+                if (lane == 0) x0 = atomicAdd(&s_next, 32u);
+                x0 = __shfl_sync(~0u, x0, 0);
+                if (x0 + 1 >= nl) break;  // warp-uniform
+                const uint32_t x = x0 + lane;
+                uint32_t i = 0, li = kNone, y0 = nl, c = 0;
+                if (x + 1 < nl) {
+                    i = s_id[x];
+                    li = s_lab[x];
+                    if (MODE != 1 || gr.has(i >> gshift)) {
+                        const uint64_t lim = (uint64_t)i + a.excl;
+                        uint32_t lo = x + 1, hi = nl;
+                        while (lo < hi) {
+                            const uint32_t m = (lo + hi) >> 1;
+                            if (s_id[m] <= lim) lo = m + 1;
+                            else hi = m;
                         }
-                        o += __popc(m);
+                        y0 = lo;
+                        c = nl - y0;
+                        if (li != kNone)
+                            for (uint32_t y = y0; y < nl; y++) c -= s_lab[y] == li;
+                    }
+                }
+                const uint32_t g = i >> gshift;
+                if (MODE == 0) {
+                    if (c) atomicAdd(gcnt + g, c);
+                    continue;
+                }
+                uint64_t base = 0;
+                if (c) base = MODE == 2 ? atomicAdd(gcur + g, c) : goff[g] - gr.ebase + atomicAdd(gcur + g, c);
+                for (uint32_t todo = __ballot_sync(~0u, c != 0); todo; todo &= todo - 1) {
+                    const int r = __ffs(todo) - 1;
+                    const uint32_t ri = __shfl_sync(~0u, i, r), rli = __shfl_sync(~0u, li, r);
+                    const uint32_t ry0 = __shfl_sync(~0u, y0, r), rg = ri >> gshift;
+                    uint64_t o = __shfl_sync(~0u, base, r);
+                    if (rli == kNone) {
+                        for (uint32_t y = ry0 + lane; y < nl; y += 32) {
+                            const PT e = pack_entry<PT>(ri & lmask, s_id[y], nbits);
+                            if (MODE == 2) rs.put(rg, o + (y - ry0), (uint32_t)e);
+                            else ent[o + (y - ry0)] = e;
+                        }
+                    } else {
+                        for (uint32_t yb = ry0; yb < nl; yb += 32) {
+                            const uint32_t y = yb + lane;
+                            const bool keep = y < nl && s_lab[y] != rli;
+                            const uint32_t m = __ballot_sync(~0u, keep);
+                            if (keep) {
+                                const PT e = pack_entry<PT>(ri & lmask, s_id[y], nbits);
+                                const uint64_t slot = o + __popc(m & ((1u << lane) - 1));
+                                if (MODE == 2) rs.put(rg, slot, (uint32_t)e);
+                                else ent[slot] = e;
+                            }
+                            o += __popc(m);
+                        }
                     }
                 }
             }
@@ -2221,6 +2250,24 @@ __global__ void k_ovf_starts(const unsigned long long *__restrict__ ovf, uint64_
     }
 }
 
+// cut[2q] = first row group whose pair offset reaches q/nparts of all S
+// pairs, cut[2q + 1] = that group's offset (q = 0 .. nparts)
+__global__ void k_part_cuts(const uint64_t *__restrict__ goff, uint64_t ng, uint64_t S, uint32_t nparts,
+                            uint64_t *__restrict__ cut) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q > nparts) return;
+    const uint64_t want = (uint64_t)((unsigned __int128)S * q / nparts);
+    uint64_t lo = 0, hi = ng + 1;  // first g with goff[g] >= want
+    while (lo < hi) {
+        const uint64_t m = (lo + hi) / 2;
+        if (goff[m] < want) lo = m + 1;
+        else hi = m;
+    }
+    const uint64_t g = min(lo, ng);
+    cut[2 * q] = g;
+    cut[2 * q + 1] = goff[g];
+}
+
 template <typename PT, typename Alloc>
 static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *medium, uint64_t nmedium,
                                  uint32_t gshift, uint32_t nbits, uint32_t *sp_cnt, uint64_t *sp_start,
@@ -2364,24 +2411,37 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
         if (room && need > room) nparts = std::max<uint64_t>(nparts, (need + room - 1) / room);
     }
     nparts = (uint32_t)std::min<uint64_t>(nparts, std::max<uint64_t>(1, ng));
-    std::vector<uint64_t> cut{0, ng};  // group boundaries of the partitions
+    std::vector<uint64_t> cut{0, ng}, hgb{0, S};  // group boundaries of the partitions, goff there
     uint64_t part_max = S;
-    if (nparts > 1) {
-        std::vector<uint64_t> hg(ng + 1);
-        cudaMemcpyAsync(hg.data(), goff, (ng + 1) * 8, cudaMemcpyDeviceToHost, s);
-        if ((st = sync_check(c, s, "partition offsets"))) return st;
-        cut.assign(1, 0);
-        for (uint32_t q = 1; q < nparts; q++) {
-            const uint64_t want = S * q / nparts;
-            const uint64_t g = std::lower_bound(hg.begin(), hg.end(), want) - hg.begin();
-            if (g > cut.back() && g < ng) cut.push_back(g);
+    uint64_t *d_cut = nullptr;
+    if ((st = lalloc(&d_cut, 2 * (4096 + 1)))) return st;
+    for (;;) {
+        if (nparts > 1) {  // cuts of about equal pair counts, found on the device
+            k_part_cuts<<<ceil_div(nparts + 1, 128), 128, 0, s>>>(goff, ng, S, nparts, d_cut), FAST_LAUNCHED(c);
+            std::vector<uint64_t> hc(2 * (nparts + 1));
+            cudaMemcpyAsync(hc.data(), d_cut, hc.size() * 8, cudaMemcpyDeviceToHost, s);
+            if ((st = sync_check(c, s, "partition cuts"))) return st;
+            cut.assign(1, 0);
+            hgb.assign(1, 0);
+            for (uint32_t q = 1; q < nparts; q++)
+                if (hc[2 * q] > cut.back() && hc[2 * q] < ng) {
+                    cut.push_back(hc[2 * q]);
+                    hgb.push_back(hc[2 * q + 1]);
+                }
+            cut.push_back(ng);
+            hgb.push_back(S);
+            part_max = 0;
+            for (size_t q = 0; q + 1 < cut.size(); q++) part_max = std::max(part_max, hgb[q + 1] - hgb[q]);
         }
-        cut.push_back(ng);
-        part_max = 0;
-        for (size_t q = 0; q + 1 < cut.size(); q++) part_max = std::max(part_max, hg[cut[q + 1]] - hg[cut[q]]);
+        if (single || !(st = lalloc(&ent, part_max))) break;
+        // the buffer did not fit after all (the pool's free memory can be
+        // fragmented): twice the partitions
+        if ((st != FAST_ENOMEM && st != FAST_EBUDGET) || nparts >= std::min<uint64_t>(ng, 4096)) return st;
+        st = FAST_OK;
+        c->err.clear();
+        nparts = (uint32_t)std::min<uint64_t>(std::min<uint64_t>(ng, 4096), 2ull * nparts);
     }
     c->stats.query_parts = (uint32_t)(cut.size() - 1);
-    if (!single && (st = lalloc(&ent, part_max))) return st;
 
     // hash capacity: twice the power of two above the target (group sizes vary), at least 4096
     uint32_t vcap = 64;
@@ -2403,11 +2463,6 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     VoteArgs va{goff, ng, N, 0, ng, 0, gshift, nbits, p.v, vcap, sp_cnt, sp_start, nullptr, nullptr, 0,
                 scal + Scal::CUR_SPARSE, long_rows, scal + Scal::NLONG, N,
                 single ? gcur : nullptr, rcap, ovf_sorted, ostart};
-    std::vector<uint64_t> hgb(cut.size());  // goff at the cuts
-    if (cut.size() > 2) {
-        for (size_t q = 0; q < cut.size(); q++) cudaMemcpyAsync(&hgb[q], goff + cut[q], 8, cudaMemcpyDeviceToHost, s);
-        if ((st = sync_check(c, s, "partition bases"))) return st;
-    }
     for (int attempt = 0; attempt < 2; attempt++) {
         uint32_t *sp_j = nullptr;
         uint8_t *sp_v = nullptr;
