@@ -28,11 +28,19 @@ __all__ = ["Searcher", "Plan", "Result", "Merged", "Clusters", "Tables", "FastEr
            "fast_stream_poll", "fast_stream_latency", "fast_stream_release", "fast_server_inject_failure"]
 
 
+def _track(searcher, obj):
+    """Registers a library object with the context that made it: closing the
+    context frees it first (an object may not outlive its context)."""
+    if searcher is not None:
+        searcher._live.add(obj)
+
+
 class Result:
     """A detection list held in device memory by the library."""
 
-    def __init__(self, handle):
+    def __init__(self, handle, searcher=None):
         self.handle = handle
+        _track(searcher, self)
         self.M, self.i, self.j, self.votes = fast_result_view(handle, owner=self)
 
     def numpy(self):
@@ -55,8 +63,9 @@ class Result:
 class Merged:
     """A channel-merged list (i, j, summed votes) in (dt, idx1) order, in device memory."""
 
-    def __init__(self, handle):
+    def __init__(self, handle, searcher=None):
         self.handle = handle
+        _track(searcher, self)
         self.M, self.i, self.j, self.sim = _lib.fast_merged_view(handle, owner=self)
 
     def numpy(self):
@@ -79,8 +88,9 @@ class Merged:
 class Clusters:
     """Station-level clusters: rows (dt_min, dt_max, idx1_min, idx1_max, entries, sim)."""
 
-    def __init__(self, handle):
+    def __init__(self, handle, searcher=None):
         self.handle = handle
+        _track(searcher, self)
         self.n, self.box = _lib.fast_clusters_view(handle, owner=self)
 
     def numpy(self):
@@ -101,8 +111,9 @@ class Clusters:
 class Tables:
     """Per-table sorted (key, id) arrays and the drop mask, in device memory."""
 
-    def __init__(self, handle, sig):
+    def __init__(self, handle, sig, searcher=None):
         self.handle = handle
+        _track(searcher, self)
         self.sig = sig  # the keys must outlive the tables (fast_search reads them)
         self.skey, self.sid, self.drop = fast_tables_view(handle, owner=self)
 
@@ -125,6 +136,8 @@ class Searcher:
         import torch
         if not torch.cuda.is_available():
             raise FastError(_lib.FAST_ECUDA, "no CUDA device: this library has no CPU fallback")
+        import weakref
+        self._live = weakref.WeakSet()  # results, tables, ... made by this context
         self.params = dict(params)
         self.ctx = fast_create(self.params, hbm_budget_bytes)
         for k, v in options.items():
@@ -132,6 +145,8 @@ class Searcher:
 
     def close(self):
         if getattr(self, "ctx", None):
+            for obj in list(self._live):  # nothing may outlive the context
+                obj.free()
             fast_destroy(self.ctx)
             self.ctx = None
 
@@ -159,23 +174,24 @@ class Searcher:
         _lib.fast_sig_rows(self.ctx, idx, n, ld, sig, sig.shape[1], col0, stream)
 
     def build_tables(self, sig, stream=None) -> Tables:
-        return Tables(fast_build_tables(self.ctx, sig, sig.shape[1], stream), sig)
+        return Tables(fast_build_tables(self.ctx, sig, sig.shape[1], stream), sig, self)
 
     def search(self, tables: Tables, stream=None) -> Result:
-        return Result(fast_search(self.ctx, tables.handle, stream))
+        return Result(fast_search(self.ctx, tables.handle, stream), self)
 
     def detect(self, idx, stream=None) -> Result:
         N, ld = idx.shape
-        return Result(fast_detect(self.ctx, idx, N, ld, stream))
+        return Result(fast_detect(self.ctx, idx, N, ld, stream), self)
 
     def detect_chunked(self, N: int, ld: int, fill, chunk_rows: int = 1 << 22, stream=None) -> Result:
         """Whole path over a station produced chunk by chunk: fill(row0, n, rows)
         writes windows row0 .. row0 + n - 1 into the [n, ld] uint16 array rows."""
-        return Result(_lib.fast_detect_chunked(self.ctx, N, ld, chunk_rows, fill, stream))
+        return Result(_lib.fast_detect_chunked(self.ctx, N, ld, chunk_rows, fill, stream), self)
 
     def detect_batch(self, idx, station_N, stream=None):
         """Several stations in one pass: idx holds their rows one after another."""
-        return [Result(h) for h in _lib.fast_detect_batch(self.ctx, idx, list(station_N), idx.shape[1], stream)]
+        return [Result(h, self) for h in _lib.fast_detect_batch(self.ctx, idx, list(station_N), idx.shape[1],
+                                                                stream)]
 
     def plan(self, idx, station_N, stream) -> "Plan":
         """A batch plan over idx (refill it between runs); see :class:`Plan`."""
@@ -200,17 +216,18 @@ class Searcher:
         """Query-only hashing: the batch's pairs against the history (ids continue
         after it) without building tables of the history."""
         return Result(_lib.fast_query_only(self.ctx, hist, hist.shape[0], hist_drop, batch, batch.shape[0],
-                                           batch.shape[1], stream))
+                                           batch.shape[1], stream), self)
 
     def channel_merge(self, results, N: int, thr: int, stream=None) -> Merged:
         """Channel level: the channels' Results summed per pair, kept at >= thr."""
         lists = [(r.M, r.i, r.j, r.votes) for r in results]
-        return Merged(_lib.fast_channel_merge(self.ctx, N, lists, thr, stream))
+        return Merged(_lib.fast_channel_merge(self.ctx, N, lists, thr, stream), self)
 
     def station_clusters(self, merged, gap: int, width: int, min_n: int, stream=None) -> Clusters:
         """Station level over a (dt, idx1)-ordered list (a Merged, or (i, j, sim) device tensors)."""
         i, j, sim = (merged.i, merged.j, merged.sim) if isinstance(merged, Merged) else merged
-        return Clusters(_lib.fast_station_clusters(self.ctx, i, j, sim, i.shape[0], gap, width, min_n, stream))
+        return Clusters(_lib.fast_station_clusters(self.ctx, i, j, sim, i.shape[0], gap, width, min_n, stream),
+                        self)
 
 
 class Plan:
@@ -222,9 +239,11 @@ class Plan:
         self.n_st = len(station_N)
         self.stream = stream
         self.handle = _lib.fast_plan_create(searcher.ctx, idx, list(station_N), idx.shape[1], stream)
+        _track(searcher, self)
 
     def run(self):
-        return [Result(h) for h in _lib.fast_plan_run(self.searcher.ctx, self.handle, self.n_st, self.stream)]
+        return [Result(h, self.searcher) for h in _lib.fast_plan_run(self.searcher.ctx, self.handle, self.n_st,
+                                                                     self.stream)]
 
     def info(self) -> dict:
         return _lib.fast_plan_info(self.handle)
@@ -233,6 +252,8 @@ class Plan:
         if getattr(self, "handle", None):
             _lib.fast_plan_destroy(self.handle)
             self.handle = None
+
+    free = close
 
     def __del__(self):
         try:

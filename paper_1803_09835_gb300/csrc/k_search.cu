@@ -674,7 +674,8 @@ struct RegionSink {
 };
 
 struct PairSmem {  // one warp's tile window and its pair bookkeeping
-    uint32_t id[64], lab[64], pre[32], cnt[32];
+    uint32_t id[64], lab[64], pre[32];
+    uint64_t keep[32];  // per row: window positions of its kept partners
     uint64_t base[32];
 };
 
@@ -731,26 +732,37 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
             W.lab[lane] = c.lab;
             W.lab[32 + lane] = n.lab;
             W.pre[lane] = incl - cand;
-            W.cnt[lane] = 0;
             __syncwarp();
-            for (uint32_t k = lane; k < P; k += 32) {
-                uint32_t L = 0;
-#pragma unroll
-                for (uint32_t step = 16; step; step >>= 1)
-                    if (W.pre[L + step] <= k) L += step;
-                const uint32_t y = L + 1 + (k - W.pre[L]);
-                const uint32_t i = W.id[L], li = W.lab[L], j = W.id[y], lj = W.lab[y];
-                if (lj != kLabDrop && j - i > a.excl && (li == kNone || li != lj) && (MODE == 0 || gr.has(i >> gshift)))
-                    atomicAdd(&W.cnt[L], 1u);
+            // This lane's row: its kept partners as a mask over the window.
+            // Ids ascend inside a bucket, so the partners past the near-time
+            // exclusion start at one position p0 (binary search); dropped
+            // entries are cleared by the live mask; only a dense-group member
+            // has to clear partners of its own group one by one.
+            const uint64_t live = (uint64_t)__ballot_sync(~0u, n.lab != kLabDrop) << 32 |
+                                  __ballot_sync(~0u, c.lab != kLabDrop);
+            uint64_t keep = 0;
+            if (cand && (MODE == 0 || gr.has(c.id >> gshift))) {
+                const uint64_t lim = (uint64_t)c.id + a.excl;
+                uint32_t lo = lane + 1, hi = (uint32_t)e;
+                while (lo < hi) {
+                    const uint32_t m = (lo + hi) >> 1;
+                    if (W.id[m] <= lim) lo = m + 1;
+                    else hi = m;
+                }
+                keep = live & (((e >= 64 ? 0ull : 1ull << e) - 1) & ~((1ull << lo) - 1));
+                if (c.lab != kNone)
+                    for (uint64_t m = keep; m; m &= m - 1) {
+                        const int y = __ffsll((long long)m) - 1;
+                        if (W.lab[y] == c.lab) keep &= ~(1ull << y);
+                    }
             }
-            __syncwarp();
-            const uint32_t cnt = W.cnt[lane], g = c.id >> gshift;
+            const uint32_t cnt = __popcll(keep), g = c.id >> gshift;
             if (MODE != 1) emitted += cnt;
             if (MODE == 0) {
                 if (cnt) atomicAdd(gcnt + g, cnt);
             } else if (__any_sync(~0u, cnt != 0)) {
+                W.keep[lane] = keep;
                 W.base[lane] = !cnt ? 0 : MODE == 2 ? atomicAdd(gcur + g, cnt) : goff[g] - gr.ebase + atomicAdd(gcur + g, cnt);
-                W.cnt[lane] = 0;
                 __syncwarp();
                 for (uint32_t k = lane; k < P; k += 32) {
                     uint32_t L = 0;
@@ -758,9 +770,10 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
                     for (uint32_t step = 16; step; step >>= 1)
                         if (W.pre[L + step] <= k) L += step;
                     const uint32_t y = L + 1 + (k - W.pre[L]);
-                    const uint32_t i = W.id[L], li = W.lab[L], j = W.id[y], lj = W.lab[y];
-                    if (lj != kLabDrop && j - i > a.excl && (li == kNone || li != lj) && gr.has(i >> gshift)) {
-                        const uint64_t slot = W.base[L] + atomicAdd(&W.cnt[L], 1u);
+                    const uint64_t kl = W.keep[L];
+                    if (kl >> y & 1) {
+                        const uint32_t i = W.id[L], j = W.id[y];
+                        const uint64_t slot = W.base[L] + __popcll(kl & ((1ull << y) - 1));
                         if (MODE == 2) rs.put(i >> gshift, slot, (uint32_t)pack_entry<PT>(i & lmask, j, nbits));
                         else ent[slot] = pack_entry<PT>(i & lmask, j, nbits);
                     }

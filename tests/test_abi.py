@@ -53,3 +53,35 @@ def test_no_gpu_means_an_error_not_a_fallback():
     from paper_1803_09835_gb300 import FastError, Searcher
     with pytest.raises(FastError):
         Searcher(dict(D=2048, K=100, b=16, r=4, kind=0, seed=1, v=2, excl=5, occ_num=0, occ_den=1))
+
+
+def test_closing_a_searcher_frees_what_it_made():
+    # a result may not outlive its context: the wrapper frees every live
+    # object of a context before destroying it (checked without a GPU on a
+    # stand-in object)
+    import paper_1803_09835_gb300 as pkg
+
+    class Obj:
+        freed = 0
+
+        def free(self):
+            Obj.freed += 1
+
+    s = pkg.Searcher.__new__(pkg.Searcher)
+    import weakref
+    s._live = weakref.WeakSet()
+    keep = [Obj(), Obj()]
+    for o in keep:
+        pkg._track(s, o)
+    s.ctx = None  # no context: close() has nothing to destroy
+    s.close()
+    assert Obj.freed == 0  # without a context nothing is touched
+    calls = []
+    pkg_destroy = pkg.fast_destroy
+    try:
+        pkg.fast_destroy = lambda ctx: calls.append(ctx)
+        s.ctx = "ctx"
+        s.close()
+    finally:
+        pkg.fast_destroy = pkg_destroy
+    assert Obj.freed == 2 and calls == ["ctx"] and s.ctx is None

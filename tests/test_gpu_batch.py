@@ -75,3 +75,38 @@ def test_batch_of_one_and_empty_stations():
     parts = s.detect_batch(a, [0, 2500, 0])
     assert parts[0].M == 0 and parts[2].M == 0 and _eq(parts[1].numpy(), ref)
     s.close()
+
+
+@pytest.mark.slow
+def test_c2_four_and_three_month_batch_full_size():
+    """Two stations of the 12-station workload at full size (4 and 3 months,
+    18,144,000 windows) in one batch: each station's drop count equals the
+    oracle's, its list is sorted, unique and within the rules, and sampled
+    rows equal the oracle's rows."""
+    from paper_1803_09835_gb300 import Searcher
+    ws = [synth.workload("c2", station=3), synth.workload("c2", station=2)]
+    idx = [synth.generate(w, ld=400) for w in ws]
+    p = ws[0].params()
+    s = Searcher(dict(p, table_group=10))
+    res = s.detect_batch(torch.from_numpy(np.concatenate(idx)).cuda(), [w.N for w in ws])
+    got = [r.numpy() for r in res]
+    for r in res:
+        r.free()
+    s.close()
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(7)
+    for (gi, gj, gv), w, a in zip(got, ws, idx):
+        assert len(gi) > 10**8
+        assert np.all(gi < gj) and np.all(gj.astype(np.int64) - gi > p["excl"]) and np.all(gv >= p["v"])
+        key = (gi.astype(np.uint64) << np.uint64(32)) | gj
+        assert np.all(key[1:] > key[:-1])
+        del key
+        keys = oracle.keys(p, a)
+        drop = oracle.drop(p, keys)
+        assert not drop[gi].any() and not drop[gj].any()
+        rows = np.concatenate([rng.choice(np.unique(gi[::9973]), 6, replace=False), rng.integers(0, w.N, 4)])
+        starts, ends = np.searchsorted(gi, rows), np.searchsorted(gi, rows, side="right")
+        for row, lo, hi in zip(rows, starts, ends):
+            wj, wv = oracle.search_row(p, keys, drop, int(row))
+            assert np.array_equal(gj[lo:hi], wj) and np.array_equal(gv[lo:hi], wv), f"row {row}"
+        del keys

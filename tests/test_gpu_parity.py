@@ -191,7 +191,7 @@ def test_dense_votes_fall_back_when_the_cluster_scratch_does_not_fit():
     w = synth.scaled("c1", 30_000)
     idx = synth.generate(w, ld=400)
     d = torch.from_numpy(idx).cuda()
-    p = w.params()
+    p = dict(w.params(), table_group=1)  # one table sorted at a time: the build is not the peak
     s = _searcher(p, large_min=16)
     s.detect(d).free()
     st = s.stats()
@@ -200,8 +200,8 @@ def test_dense_votes_fall_back_when_the_cluster_scratch_does_not_fit():
     s.close()
     _, _, want = _oracle_run(p, idx, w.K)
     ok = fallback = 0
-    for k in range(40):
-        budget = int(peak * (1 - 0.015 * k))
+    for k in range(80):
+        budget = int(peak * (1 - 0.005 * k))
         sb = Searcher(p, hbm_budget_bytes=budget, large_min=16)
         try:
             r = sb.detect(d)

@@ -181,3 +181,54 @@ def test_admission_wait_is_bounded_and_short_polls_pend():
     with pytest.raises(FastError):
         srv.set_option("admit_timeout_ms", -1)
     srv.close()
+
+
+def test_c3_shape_requests_match_serial_replay():
+    # the streaming configuration's own shape: D = 8192, K = 400, Min-Max
+    # b = 100 x r = 4, v = 4, E = 10, 0.5 % filter frozen on the history;
+    # each request element-wise equal to the replay, alone and in the mix
+    from paper_1803_09835_gb300 import Server
+    n0 = 20_000
+    stations = []
+    for st in range(2):
+        w = synth.scaled("c3", n0 + sum(SIZES), station=st)
+        stations.append((w, synth.generate(w, ld=400)))
+    p = stations[0][0].params()
+    want = []
+    for w, idx in stations:
+        keys = oracle.keys(p, idx)
+        hd = oracle.drop(p, np.ascontiguousarray(keys[:, :n0]))
+        rows, j0 = [], n0
+        for n in SIZES:
+            rows.append(oracle.stream_query(p, np.ascontiguousarray(keys[:, :j0 + n]), n0, j0, hd))
+            j0 += n
+        want.append(rows)
+    assert sum(len(r[0]) for st in want for r in st) > 0
+
+    def run(mixed):
+        srv = Server(p, 2, max_stream_windows=sum(SIZES) + 16)
+        for s, (w, idx) in enumerate(stations):
+            srv.load_history(s, idx[:n0])
+        out = [[None] * len(SIZES) for _ in stations]
+        if mixed:
+            ids = []
+            for q in range(len(SIZES)):
+                for s, (w, idx) in enumerate(stations):
+                    j0 = n0 + sum(SIZES[:q])
+                    ids.append((s, q, srv.submit(s, idx[j0:j0 + SIZES[q]])))
+            for s, q, r in ids:
+                out[s][q] = srv.wait(r)
+        else:
+            for s, (w, idx) in enumerate(stations):
+                for q in range(len(SIZES)):
+                    j0 = n0 + sum(SIZES[:q])
+                    out[s][q] = srv.wait(srv.submit(s, idx[j0:j0 + SIZES[q]]))
+        srv.close()
+        return out
+
+    for got in (run(False), run(True)):
+        for s in range(2):
+            for q in range(len(SIZES)):
+                first, i, j, v = got[s][q]
+                assert first == n0 + sum(SIZES[:q])
+                assert _same((i, j, v), want[s][q]), f"station {s} request {q}"
