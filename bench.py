@@ -234,17 +234,18 @@ def _kernel_source_hash(rel: str) -> str:
     return hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest()[:16]
 
 
-def _traffic(kernel: str, units: float):
-    """DRAM bytes per launch from the committed ncu capture of this kernel
-    (profiles/dram_traffic.json: bytes per unit, scaled to this launch), or
-    None when there is none or the kernel's source changed since."""
+def _traffic(kernel: str, units: dict):
+    """DRAM bytes of a kernel over a step, from the committed ncu record of
+    that kernel (profiles/dram_traffic.json: bytes per unit of its work,
+    scaled to the step's units), or None when there is none or the kernel's
+    source changed since."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))[kernel]
     except (OSError, ValueError, KeyError):
         return None
-    if _kernel_source_hash(rec["source"]) != rec["source_sha256_16"]:
+    if _kernel_source_hash(rec["source"]) != rec["source_sha256_16"] or rec.get("unit") not in units:
         return None
-    return rec["bytes_per_unit"] * units
+    return rec["bytes_per_unit"] * units[rec["unit"]]
 
 
 def _peaks():
@@ -270,9 +271,12 @@ class KernelBytes:
         self.w = w
         self.b = {k: 0.0 for k in ("k_sig_walk", "radix sort", "k_pairs_grp", "k_medium_grp", "k_pairs_grp count",
                                    "k_warp_vote", "output")}
+        self.units = {}
 
     def add(self, N, st):
         w, b = self.w, self.b
+        for k, v in units_of(st, N).items():
+            self.units[k] = self.units.get(k, 0) + v
         b["k_sig_walk"] += N * (2 * w.K + 4 * w.b)
         b["radix sort"] += N * w.b * 12
         b["k_pairs_grp"] += N * w.b * 8 + st["n_pairs_small"] * 4
@@ -287,7 +291,7 @@ KERNEL_MS = {"k_sig_walk": "sig", "radix sort": "sort", "k_pairs_grp": "k_pairs"
 SINGLE = {"k_sig_walk", "k_pairs_grp", "k_medium_grp", "k_pairs_grp count", "k_warp_vote"}
 
 
-def kernel_rooflines(kb, per, steps, peaks, units):
+def kernel_rooflines(kb, per, steps, peaks):
     """Per heavy kernel: live ms per step (CUDA events on the launching
     stream, summed over the step's launches), algorithmic bytes per step and
     the HBM roofline fraction they reach; ``traffic`` is DRAM bytes from the
@@ -300,7 +304,8 @@ def kernel_rooflines(kb, per, steps, peaks, units):
         nbytes = kb.b[name] / steps
         ach = nbytes / (ms / 1000) / 1e9 if ms > 0 else 0.0
         out[name] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                     "traffic": _traffic(name, units), "peak_source": f"{src} ({hbm:g} GB/s)",
+                     "traffic": (lambda t: t / steps if t is not None else None)(
+                         _traffic(name, kb.units)), "peak_source": f"{src} ({hbm:g} GB/s)",
                      "algorithmic_bytes": nbytes, "ms": ms, "single_kernel": name in SINGLE}
     return out
 
@@ -411,7 +416,7 @@ def station_arm(args, rank, world, local_rank, w, steps, warmup, e2e=True):
         line["e2e"] = {"value": n_total / (e2e_ms / 1000), "unit": UNIT, "ms_per_step": e2e_ms,
                        "h2d_bytes_per_step": w.N * ld * 2, "d2h_bytes_per_step": M * 9}
     per = {k: meter.acc[k] / steps for k in STAGES}
-    kernels = kernel_rooflines(meter.kb, per, steps, _peaks(), w.N)
+    kernels = kernel_rooflines(meter.kb, per, steps, _peaks())
     line["roofline"] = dominant(kernels)
     line["kernels"] = {k: {kk: v[kk] for kk in ("ms", "bound", "achieved", "frac", "unit")} for k, v in kernels.items()}
     line["stage_ms"] = per
@@ -570,7 +575,7 @@ def c2_arm(args, rank, world, local_rank):
     torch.cuda.empty_cache()
 
     per = {k: meter.acc[k] / args.steps for k in STAGES}
-    kernels = kernel_rooflines(meter.kb, per, args.steps, _peaks(), N_all)
+    kernels = kernel_rooflines(meter.kb, per, args.steps, _peaks())
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
@@ -626,19 +631,34 @@ def gpu_arm(args, rank, world, local_rank):
     return 0
 
 
-TRAFFIC_KERNELS = {  # kernel-name prefix in the ncu list -> (roofline name, source file)
-    "k_sig_walk": ("k_sig_walk", "paper_1803_09835_gb300/csrc/k_sig.cu"),
-    "k_pairs_grp<2": ("k_pairs_grp<2>", "paper_1803_09835_gb300/csrc/k_search.cu"),
-    "k_warp_vote": ("k_warp_vote", "paper_1803_09835_gb300/csrc/k_search.cu"),
+TRAFFIC_KERNELS = {  # kernel-name prefix in the ncu list -> (roofline name, source file, unit)
+    "k_sig_walk": ("k_sig_walk", "paper_1803_09835_gb300/csrc/k_sig.cu", "fingerprint"),
+    "k_pairs_grp<2": ("k_pairs_grp", "paper_1803_09835_gb300/csrc/k_search.cu", "small-bucket pair"),
+    "k_pairs_grp<1": ("k_pairs_grp", "paper_1803_09835_gb300/csrc/k_search.cu", "small-bucket pair"),
+    "k_medium_grp<2": ("k_medium_grp", "paper_1803_09835_gb300/csrc/k_search.cu", "medium-bucket pair"),
+    "k_medium_grp<1": ("k_medium_grp", "paper_1803_09835_gb300/csrc/k_search.cu", "medium-bucket pair"),
+    "k_warp_vote": ("k_warp_vote", "paper_1803_09835_gb300/csrc/k_search.cu", "emission"),
 }
 
 
-def record_traffic(csv_path: str, n_windows: int, command: str, out_path: str | None = None) -> dict:
+def units_of(st: dict, N: int) -> dict:
+    """Units of the traffic record in one search, from its counters."""
+    return {"fingerprint": N, "small-bucket pair": st["n_pairs_small"],
+            "medium-bucket pair": st["n_emissions"] - st["n_pairs_small"], "emission": st["n_emissions"]}
+
+
+def record_traffic(csv_path: str, line_path: str, command: str, out_path: str | None = None) -> dict:
     """profiles/dram_traffic.json from one ncu --csv capture of
-    dram__bytes_read.sum and dram__bytes_write.sum: per kernel of
-    TRAFFIC_KERNELS, the first launch's bytes per window of the workload,
-    with the hash of the kernel's source file at capture time."""
+    dram__bytes_read.sum and dram__bytes_write.sum over a single-station run
+    of bench.py, and that run's own JSON line (its counters): per kernel of
+    TRAFFIC_KERNELS, the DRAM bytes of its launches per unit of its work
+    (fingerprints, pairs written, emissions voted), with the hash of the
+    kernel's source file at capture time.  A launch of the pair kernels is
+    scaled by pairs, not windows: their bytes follow the pairs they write."""
     import csv
+    line = json.loads([x for x in open(line_path) if x.startswith("{")][-1])
+    N = line["config"]["N_per_station"]
+    units = units_of(line["counters"], N)
     scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
     rows = list(csv.reader(open(csv_path)))
     hdr = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
@@ -652,21 +672,23 @@ def record_traffic(csv_path: str, n_windows: int, command: str, out_path: str | 
         name = re.sub(r"\((?:int|bool|unsigned int|long|unsigned long)\)", "", name.replace("unnamed>::", ""))
         name = name.split("(")[0].split("::")[-1]
         key = next((k for k in TRAFFIC_KERNELS if name.startswith(k)), None)
-        if key is None or (key in seen and seen[key]["id"] != r[ii]):
+        if key is None:
             continue
-        rec = seen.setdefault(key, {"id": r[ii], "read": 0.0, "write": 0.0})
+        rec = seen.setdefault(TRAFFIC_KERNELS[key][0], {"ids": set(), "read": 0.0, "write": 0.0, "key": key})
+        rec["ids"].add(r[ii])
         v = float(r[vi].replace(",", "")) * scale.get(r[ui], 1)
         if r[mi] == "dram__bytes_read.sum":
-            rec["read"] = v
+            rec["read"] += v
         elif r[mi] == "dram__bytes_write.sum":
-            rec["write"] = v
+            rec["write"] += v
     out = {}
-    for key, rec in seen.items():
-        name, src = TRAFFIC_KERNELS[key]
+    for name, rec in seen.items():
+        _, src, unit = TRAFFIC_KERNELS[rec["key"]]
+        n = max(1, units[unit])
         out[name] = {"source": src, "source_sha256_16": _kernel_source_hash(src),
-                     "bytes_per_unit": (rec["read"] + rec["write"]) / n_windows, "unit": "fingerprint",
-                     "captured_on": f"{n_windows:,} windows, first launch", "dram_read_bytes": rec["read"],
-                     "dram_write_bytes": rec["write"], "command": command}
+                     "bytes_per_unit": (rec["read"] + rec["write"]) / n, "unit": unit,
+                     "captured_on": f"{N:,} windows, {len(rec['ids'])} launch(es), {n:,} {unit}s",
+                     "dram_read_bytes": rec["read"], "dram_write_bytes": rec["write"], "command": command}
     with open(out_path or os.path.join(ROOT, "profiles", "dram_traffic.json"), "w") as f:
         json.dump(out, f, indent=1)
         f.write("\n")
@@ -919,11 +941,11 @@ def main():
     ap.add_argument("--no-plan", action="store_true", help="skip the batch-plan leg of the headline")
     ap.add_argument("--record-traffic", default="", metavar="CSV",
                     help="write profiles/dram_traffic.json from an ncu dram-bytes capture of this workload")
+    ap.add_argument("--record-line", default="", help="the JSON line of the captured run (its counters)")
     ap.add_argument("--record-command", default="", help="the ncu command line to note beside --record-traffic")
     args = ap.parse_args()
     if args.record_traffic:
-        w = station_workload(args.workload, 0, args.n)
-        print(json.dumps(record_traffic(args.record_traffic, w.N, args.record_command), indent=1))
+        print(json.dumps(record_traffic(args.record_traffic, args.record_line, args.record_command), indent=1))
         return 0
     if args.serving:
         return serving_arm(args)

@@ -1,6 +1,7 @@
-"""bench.py --record-traffic: DRAM bytes per launch from an ncu CSV capture,
-recorded with each kernel's source hash, and used by the roofline only while
-the source is unchanged (CPU only, synthetic CSV)."""
+"""bench.py --record-traffic: DRAM bytes per unit of work from an ncu CSV
+capture and the captured run's own JSON line (its counters), recorded with
+each kernel's source hash, and used by the roofline only while the source is
+unchanged (CPU only, synthetic CSV)."""
 import csv
 import json
 import os
@@ -32,19 +33,27 @@ def test_record_traffic(tmp_path):
         (0, "void fastgb::(anonymous namespace)::k_sig_walk<(bool)1>(const unsigned short *, unsigned long)",
          "6.2", "3,000.5"),
         (1, "void fastgb::<unnamed>::k_pairs_grp<(int)2, unsigned int>(EnumArgs, unsigned int)", "17.0", "12,800"),
-        (2, "void unnamed>::k_pairs_grp<(int)2, unsigned int>(EnumArgs, unsigned int)", "99", "99"),  # second launch
-        (3, "void unnamed>::k_warp_vote<unsigned int>(VoteArgs, const T1 *)", "5.4", "2"),
-        (4, "void unnamed>::k_scatter<unsigned int, 1, 0, 0>(const T1 *)", "1", "1"),  # not recorded
+        (2, "void unnamed>::k_medium_grp<(int)2, unsigned int>(EnumArgs, const uint4 *)", "3", "1,000"),
+        (3, "void unnamed>::k_medium_grp<(int)2, unsigned int>(EnumArgs, const uint4 *)", "1", "500"),
+        (4, "void unnamed>::k_warp_vote<unsigned int>(VoteArgs, const T1 *)", "5.4", "2"),
+        (5, "void unnamed>::k_scatter<unsigned int, 1, 0, 0>(const T1 *)", "1", "1"),  # not recorded
     ]
     src = tmp_path / "t.csv"
     out = tmp_path / "dt.json"
+    line = tmp_path / "line.log"
     _write_csv(src, launches)
-    rec = bench.record_traffic(str(src), 1_000_000, "cmd", str(out))
-    assert set(rec) == {"k_sig_walk", "k_pairs_grp<2>", "k_warp_vote"}
-    assert rec["k_sig_walk"]["dram_read_bytes"] == 6.2e9
+    counters = {"n_pairs_small": 2_000_000, "n_emissions": 2_500_000}
+    line.write_text("noise\n" + json.dumps({"config": {"N_per_station": 1_000_000}, "counters": counters}) + "\n")
+    rec = bench.record_traffic(str(src), str(line), "cmd", str(out))
+    assert set(rec) == {"k_sig_walk", "k_pairs_grp", "k_medium_grp", "k_warp_vote"}
+    assert rec["k_sig_walk"]["dram_read_bytes"] == 6.2e9 and rec["k_sig_walk"]["unit"] == "fingerprint"
     assert rec["k_sig_walk"]["dram_write_bytes"] == 3000.5e6
-    assert rec["k_pairs_grp<2>"]["dram_read_bytes"] == 17.0e9  # the first launch only
-    assert abs(rec["k_warp_vote"]["bytes_per_unit"] - (5.4e9 + 2e6) / 1e6) < 1e-6
+    assert abs(rec["k_sig_walk"]["bytes_per_unit"] - (6.2e9 + 3000.5e6) / 1e6) < 1e-6
+    assert rec["k_pairs_grp"]["unit"] == "small-bucket pair"
+    assert abs(rec["k_pairs_grp"]["bytes_per_unit"] - (17.0e9 + 12800e6) / 2e6) < 1e-6
+    # both launches of the medium kernel, per medium-bucket pair (500,000 of them)
+    assert abs(rec["k_medium_grp"]["bytes_per_unit"] - (4e9 + 1500e6) / 5e5) < 1e-6
+    assert abs(rec["k_warp_vote"]["bytes_per_unit"] - (5.4e9 + 2e6) / 2.5e6) < 1e-6
     on_disk = json.load(open(out))
     assert on_disk == json.loads(json.dumps(rec))
     for name, r in rec.items():
@@ -52,11 +61,10 @@ def test_record_traffic(tmp_path):
 
 
 def test_committed_traffic_matches_its_sources():
-    # every committed record names a source file of this repository and the
-    # hash format the roofline checks against
+    # every committed record names a source file of this repository, a unit
+    # the roofline knows and the hash format it checks against
     rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
-    assert "k_sig_walk" in rec
     for name, r in rec.items():
         assert os.path.exists(os.path.join(ROOT, r["source"])), name
         assert len(r["source_sha256_16"]) == 16 and r["bytes_per_unit"] > 0
-        assert r["unit"] == "fingerprint"
+        assert r["unit"] in ("fingerprint", "small-bucket pair", "medium-bucket pair", "emission")
