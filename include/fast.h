@@ -327,6 +327,10 @@ fast_status fast_get_stats(const fast_ctx *ctx, fast_stats *out);
  *   "group_slots" region slots per row group of the single pass, 0 (= about
  *                twice the expected pairs per group) or in [1, 65536]; pairs
  *                past them go through the overflow list
+ *   "dense_masks" 1 = vote dense groups from cluster bit masks when their
+ *                scratch fits the memory (default), 0 = always by direct
+ *                comparison of the members' keys (what the search falls back
+ *                to when the masks' scratch does not fit)
  */
 fast_status fast_set_option(fast_ctx *ctx, const char *name, double value);
 

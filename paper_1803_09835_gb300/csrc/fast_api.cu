@@ -678,6 +678,7 @@ fast_status fast_set_option(fast_ctx *c, const char *name, double value) {
     } else if (!strcmp(name, "timing")) c->timing = value != 0;
     else if (!strcmp(name, "vote_map")) c->vote_map = value != 0;
     else if (!strcmp(name, "single_pass")) c->single_pass = value != 0;
+    else if (!strcmp(name, "dense_masks")) c->dense_masks = value != 0;
     else if (!strcmp(name, "group_slots")) {
         if (!(value >= 0 && value <= 65536)) return set_error(c, FAST_EINVAL, "group_slots must be in [0, 65536]");
         c->group_slots = (uint32_t)value;

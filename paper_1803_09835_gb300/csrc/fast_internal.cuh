@@ -167,6 +167,7 @@ struct fast_ctx {
     bool vote_map = false;      // sum sparse votes in one global hash map instead of per row
     bool single_pass = true;    // write the sparse pairs in one pass (fixed group regions) when they fit
     uint32_t group_slots = 0;   // region slots per row group of the single pass (0 = about twice the expected)
+    bool dense_masks = true;    // vote dense groups from cluster masks when their scratch fits
     // instrumentation
     fast_stats stats{};
     cudaEvent_t ev[24] = {};

@@ -2780,7 +2780,7 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
         };
         // only a lack of memory (or a group too large for the masks) falls
         // back to direct comparison; any other failure is the call's error
-        const fast_status cr = nm >= (1u << 24) || nb > 256 ? FAST_EBUDGET : clusters();
+        const fast_status cr = nm >= (1u << 24) || nb > 256 || !c->dense_masks ? FAST_EBUDGET : clusters();
         if (cr && cr != FAST_ENOMEM && cr != FAST_EBUDGET) return fail(cr);
         if (cr) {
             c->err.clear();
