@@ -867,20 +867,23 @@ __global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, const uint4 *__r
             if (s_lab[x] == kNone || s_lab[x] != s_lab[0]) s_mixed = 1;
         __syncthreads();
         if (s_mixed) {  // block-uniform
-            // A warp takes 32 consecutive rows, a lane each.  Members are in
-            // ascending id order, so a row's partners past the near-time
-            // exclusion are one contiguous range [y0, nl), found by binary
-            // search; only a dense-group member has to skip partners of its
-            // own group.  The lanes reserve their rows' slots together, then
-            // the warp writes row after row with consecutive stores.
+            // A warp takes R consecutive rows, a lane each (R = nl / 8
+            // rounded up, at most 32: every warp of the CTA gets rows of a
+            // small bucket too).  Members are in ascending id order, so a
+            // row's partners past the near-time exclusion are one contiguous
+            // range [y0, nl), found by binary search; only a dense-group
+            // member has to skip partners of its own group.  The lanes
+            // reserve their rows' slots together, then the warp writes row
+            // after row with consecutive stores.
+            const uint32_t R = min(32u, max(1u, (nl + 7) / 8));
             for (;;) {
                 uint32_t x0 = 0;
-                if (lane == 0) x0 = atomicAdd(&s_next, 32u);
+                if (lane == 0) x0 = atomicAdd(&s_next, R);
                 x0 = __shfl_sync(~0u, x0, 0);
                 if (x0 + 1 >= nl) break;  // warp-uniform
                 const uint32_t x = x0 + lane;
                 uint32_t i = 0, li = kNone, y0 = nl, c = 0;
-                if (x + 1 < nl) {
+                if (lane < R && x + 1 < nl) {
                     i = s_id[x];
                     li = s_lab[x];
                     if (MODE != 1 || gr.has(i >> gshift)) {
@@ -2532,28 +2535,40 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
                 std::vector<uint2> hl(nlong);
                 cudaMemcpyAsync(hl.data(), long_rows, nlong * sizeof(uint2), cudaMemcpyDeviceToHost, s);
                 if ((st = sync_check(c, s, "long rows"))) return st;
-                std::vector<uint64_t> gofs(nlong);
-                uint64_t gtot = 0;
+                // rows too long for a shared-memory hash use one in global
+                // memory; their scratch is handed out chunk by chunk of rows,
+                // at most kHugeWords words per launch (or one row's need)
+                constexpr uint64_t kHugeWords = 1ull << 29;
+                std::vector<uint64_t> gofs(nlong), chunk{0};
+                uint64_t gtot = 0, gmax = 0;
                 for (uint64_t r = 0; r < nlong; r++) {
                     uint64_t slots = 32;
                     while (slots < 2ull * hl[r].y) slots <<= 1;
                     c->stats.max_row = std::max<uint64_t>(c->stats.max_row, hl[r].y);
-                    gofs[r] = gtot;
-                    if (slots > kRowBlockSlots) {
-                        gtot += 2 * slots;
-                        c->stats.n_huge_rows++;
+                    const uint64_t need = slots > kRowBlockSlots ? 2 * slots : 0;
+                    if (need && gtot + need > kHugeWords && gtot) {  // the next chunk starts here
+                        chunk.push_back(r);
+                        gtot = 0;
                     }
+                    gofs[r] = gtot;
+                    gtot += need;
+                    gmax = std::max(gmax, gtot);
+                    c->stats.n_huge_rows += need != 0;
                 }
+                chunk.push_back(nlong);
                 uint32_t *gscr = nullptr;
                 uint64_t *d_gofs = nullptr;
-                if ((st = lalloc(&gscr, gtot)) || (st = lalloc(&d_gofs, nlong))) return st;
+                if ((st = lalloc(&gscr, gmax)) || (st = lalloc(&d_gofs, nlong))) return st;
                 cudaMemcpyAsync(d_gofs, gofs.data(), nlong * 8, cudaMemcpyHostToDevice, s);
-                stage_mark(c, 20, s);
-                k_long_vote<PT><<<(unsigned)std::min<uint64_t>(nlong, c->num_sms * 2), 512, rsm, s>>>(
-                    va, ent, long_rows, nlong, gscr, d_gofs), FAST_LAUNCHED(c);
-                stage_mark(c, 21, s);
-                if ((st = read_scal(c, s, "long rows"))) return st;
-                c->stats.ms_k_vote_block += stage_ms(c, 20, 21);
+                for (size_t k = 0; k + 1 < chunk.size(); k++) {
+                    const uint64_t r0 = chunk[k], nr = chunk[k + 1] - r0;
+                    stage_mark(c, 20, s);
+                    k_long_vote<PT><<<(unsigned)std::min<uint64_t>(nr, c->num_sms * 2), 512, rsm, s>>>(
+                        va, ent, long_rows + r0, nr, gscr, d_gofs + r0), FAST_LAUNCHED(c);
+                    stage_mark(c, 21, s);
+                    if ((st = read_scal(c, s, "long rows"))) return st;
+                    c->stats.ms_k_vote_block += stage_ms(c, 20, 21);
+                }
             }
         }
         const uint64_t used = c->h_scal[Scal::CUR_SPARSE];
