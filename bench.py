@@ -755,6 +755,60 @@ def sweep_arm(args):
     return 0
 
 
+# ------------------------------------------------------------ query-only hashing
+
+def query_arm(args):
+    """Query-only hashing (§6.4: hash only the queries, check every other
+    item against their buckets) against hashing everything, for a small
+    number of queries on a large data set: --queries new windows after an
+    N-window C1-shaped history (default 1,000 on 1,000,000, the paper's
+    example), occurrence filter off so that both ways define the same list.
+    Hashing everything: fast_detect over history + queries, the pairs with j
+    among the queries kept.  Query-only: fast_query_only.  Device time by
+    CUDA events, mean of --steps runs after --warmup."""
+    import torch
+
+    import synth
+    from paper_1803_09835_gb300 import Searcher
+    torch.cuda.set_device(0)
+    n0 = args.n or 1_000_000
+    nq = args.queries
+    w = synth.scaled("c1", n0 + nq, occ_num=0)
+    d = torch.from_numpy(synth.generate(w, ld=400)).cuda()
+    s = Searcher(w.params())
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        tot, out = 0.0, None
+        for k in range(args.warmup + args.steps):
+            ev[0].record()
+            out = fn()
+            ev[1].record()
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                tot += ev[0].elapsed_time(ev[1])
+            if k + 1 < args.warmup + args.steps:
+                out.free()
+        return tot / args.steps, out
+
+    ms_full, full = timed(lambda: s.detect(d))
+    ms_q, q = timed(lambda: s.query_only(d[:n0], d[n0:]))
+    fi, fj, fv = full.numpy()
+    keep = fj >= n0
+    same = all((a[keep] == b).all() if len(b) == keep.sum() else False for a, b in zip((fi, fj, fv), q.numpy()))
+    line = {"metric": "query-only hashing vs hashing everything", "unit": "ms", "higher_is_better": False,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic", "dtype": "u32",
+            "config": {"workload": f"{n0:,} history windows (C1 shape, filter off) + {nq:,} query windows, "
+                                   f"D={w.D}, K={w.K}, Min-Max b={w.b} x r={w.r}, v={w.v}"},
+            "hash_everything_ms": ms_full, "query_only_ms": ms_q, "speedup": ms_full / ms_q,
+            "query_pairs": q.M, "same_pairs": bool(same)}
+    full.free()
+    q.free()
+    s.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ alignment
 
 def align_arm(args):
@@ -931,6 +985,8 @@ def main():
     ap.add_argument("--duration", type=float, default=5.0)
     ap.add_argument("--budget-gb", type=int, default=150)
     ap.add_argument("--plain-requests", type=int, default=3)
+    ap.add_argument("--query", action="store_true", help="query-only hashing vs hashing everything")
+    ap.add_argument("--queries", type=int, default=1000)
     ap.add_argument("--align", action="store_true", help="channel merge + station clusters on three searches")
     ap.add_argument("--gap", type=int, default=5)
     ap.add_argument("--width", type=int, default=3)
@@ -953,6 +1009,8 @@ def main():
         return sweep_arm(args)
     if args.align:
         return align_arm(args)
+    if args.query:
+        return query_arm(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

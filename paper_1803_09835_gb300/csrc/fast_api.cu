@@ -85,6 +85,13 @@ fast_status sync_check(fast_ctx *c, cudaStream_t s, const char *where) {
     return set_error(c, FAST_EINTERNAL, w + ": device error flag " + std::to_string(flags));
 }
 
+void sig_release(fast_ctx *c, cudaStream_t s) {
+    if (!c->sig_owned) return;
+    dfree(c, c->sig_owned, c->sig_owned_bytes, s);
+    c->sig_owned = nullptr;
+    c->sig_owned_bytes = 0;
+}
+
 static thread_local uint32_t g_marked = 0;  // stage slots recorded by the current call on this thread
 
 void stage_reset() { g_marked = 0; }
@@ -378,10 +385,12 @@ fast_status fast_detect(fast_ctx *c, const uint16_t *d_idx, uint64_t N, uint32_t
     const size_t n = (size_t)c->p.b * N;
     fast_status st = dalloc_t(c, &sig, n ? n : 1, s);
     if (st) return st;
+    c->sig_owned = sig;
+    c->sig_owned_bytes = (n ? n : 1) * 4;
     st = sig_launch(c, d_idx, N, ld, sig, s);
     stage_mark(c, 1, s);
     if (!st) st = detect_from_sig(c, sig, N, out, s);
-    dfree(c, sig, n * 4, s);
+    sig_release(c, s);
     if (!st) stats_times(c, true);
     c->stats.n_fingerprints = N;
     c->stats.peak_bytes = c->peak;
@@ -490,6 +499,8 @@ fast_status fast_detect_batch(fast_ctx *c, const uint16_t *d_idx, const uint64_t
     const size_t n = (size_t)c->p.b * N;
     fast_status st = dalloc_t(c, &sig, n ? n : 1, s);
     if (st) return st;
+    c->sig_owned = sig;
+    c->sig_owned_bytes = (n ? n : 1) * 4;
     st = sig_launch(c, d_idx, N, ld, sig, s);
     stage_mark(c, 1, s);
     fast_tables *tb = nullptr;
@@ -497,7 +508,7 @@ fast_status fast_detect_batch(fast_ctx *c, const uint16_t *d_idx, const uint64_t
     if (!st) st = build_tables(c, sig, N, soff.data(), n_st, &tb, s);
     if (!st) st = search_run(c, tb, sig, &all, s);
     fast_tables_free(tb);
-    dfree(c, sig, n * 4, s);
+    sig_release(c, s);
     if (st) return st;
     if ((st = split_stations(c, all, soff, out, s))) return st;
     stats_times(c, true);
@@ -530,6 +541,8 @@ fast_status fast_detect_host(fast_ctx *c, const uint16_t *h_idx, uint64_t N, uin
         dfree(c, d_idx, bytes, s);
         return st;
     }
+    c->sig_owned = sig;
+    c->sig_owned_bytes = (nsig ? nsig : 1) * 4;
     // chunks of whole 32-row tiles: chunk k is copied on the copy stream while
     // the signature kernel works on chunk k - 1
     const uint64_t per = std::max<uint64_t>(32, ((N + kCopyChunks - 1) / kCopyChunks + 31) / 32 * 32);
@@ -545,7 +558,7 @@ fast_status fast_detect_host(fast_ctx *c, const uint16_t *h_idx, uint64_t N, uin
     stage_mark(c, 1, s);
     fast_result *res = nullptr;
     if (!st) st = detect_from_sig(c, sig, N, &res, s);
-    dfree(c, sig, nsig * 4, s);
+    sig_release(c, s);
     dfree(c, d_idx, bytes, s);
     if (st) return st;
     stats_times(c, true);
@@ -595,6 +608,10 @@ fast_status fast_detect_chunked(fast_ctx *c, uint64_t N, uint32_t ld, uint64_t c
     uint16_t *d_chunk[2] = {};
     const size_t nsig = (size_t)c->p.b * N;
     fast_status st = dalloc_t(c, &sig, nsig ? nsig : 1, s);
+    if (!st) {
+        c->sig_owned = sig;
+        c->sig_owned_bytes = (nsig ? nsig : 1) * 4;
+    }
     if (!st) st = dalloc(c, (void **)&d_chunk[0], cbytes, s);
     if (!st) st = dalloc(c, (void **)&d_chunk[1], cbytes, s);
     if (!st) {
@@ -627,7 +644,7 @@ fast_status fast_detect_chunked(fast_ctx *c, uint64_t N, uint32_t ld, uint64_t c
     dfree(c, d_chunk[1], cbytes, s);
     stage_mark(c, 1, s);
     if (!st) st = detect_from_sig(c, sig, N, out, s);
-    dfree(c, sig, nsig * 4, s);
+    sig_release(c, s);
     if (st) {
         cudaStreamSynchronize(c->copy_stream);  // no copy may still read the staging buffers
         return st;

@@ -181,6 +181,10 @@ struct fast_ctx {
     cudaEvent_t chev[4] = {};
     bool timing = true;
     int last_stage = 0;  // the most recent stage mark (named in allocation failures)
+    // the key array of the current call when the library allocated it: the
+    // search gives it back as soon as the dense groups have their keys
+    uint32_t *sig_owned = nullptr;
+    size_t sig_owned_bytes = 0;
     std::string err;
 };
 
@@ -293,6 +297,7 @@ struct HistGroups {
 fast_status history_groups(fast_ctx *c, const fast_tables *tb, const uint32_t *d_sig, HistGroups *g, cudaStream_t s);
 uint32_t large_min_for(const fast_ctx *c, uint64_t N);  // the dense-group threshold (option or automatic)
 uint64_t room_bytes(const fast_ctx *c);                 // device memory a call may still take
+void sig_release(fast_ctx *c, cudaStream_t s);          // frees the call's own key array, if any
 struct Scal {  // device scalar slots (ctx->d_scal)
     enum { NBIG, NLARGE, NMEDIUM, NHEAVY, NDROP, NMEMB, CUR_DENSE, CUR_SPARSE, CHANGED, NLONG, NMERGE, NMERGE_TOT,
            NCAND, NMID, SMALLPAIRS, NSMALLEMIT, NSLOW, NOVF, LMAX, PART0 };

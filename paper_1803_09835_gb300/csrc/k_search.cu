@@ -1983,6 +1983,14 @@ uint64_t room_bytes(const fast_ctx *c) {
     return avail > (1ull << 30) ? avail - (1ull << 30) : 0;
 }
 
+// Memory the pair buffer may take: the room less a reserve for what the
+// votes allocate beside it (the slow-group list, the sparse lists, long-row
+// scratch of at most 2 GiB): an eighth of the room, at least 4 GiB, at most half.
+static uint64_t pair_room(const fast_ctx *c) {
+    const uint64_t r = room_bytes(c);
+    return r - std::min<uint64_t>(r / 2, std::max<uint64_t>(r / 8, 4ull << 30));
+}
+
 // Tiles of 32 table entries per warp for the warp-window passes: enough warps
 // for ~16 resident per SM slot over all tables, at most 64 tiles each.
 static uint32_t tiles_per_warp(const fast_ctx *c, uint64_t N, uint32_t nb) {
@@ -2345,7 +2353,7 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
         if (c->group_slots) cap = c->group_slots;
         const uint64_t ovf_cap = c->group_slots ? S_ub + (1 << 20) : std::max<uint64_t>(1 << 20, S_ub / 8);
         const uint64_t need = ng * cap * 4 + ovf_cap * 16;
-        const uint64_t room = room_bytes(c) / 2;
+        const uint64_t room = pair_room(c);
         uint32_t *region = nullptr;
         unsigned long long *ovf = nullptr;
         if (need <= room && !(st = lalloc(&region, ng * cap)) && !(st = lalloc(&ovf, ovf_cap))) {
@@ -2422,7 +2430,7 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     // one range.  As many as query_part asks for, or as the HBM budget needs.
     uint32_t nparts = std::max<uint32_t>(1, p.query_part);
     if (!single) {
-        const uint64_t room = room_bytes(c) / 2;
+        const uint64_t room = pair_room(c);
         const uint64_t need = S * sizeof(PT);
         if (room && need > room) nparts = std::max<uint64_t>(nparts, (need + room - 1) / room);
     }
@@ -2813,6 +2821,7 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
                 FAST_LAUNCHED(c);
     }
     stage_mark(c, 5, s);
+    sig_release(c, s);  // the keys are not read past the dense groups: their memory goes to the pairs
 
     // ---- sparse pairs: group-partitioned emission, per-row votes
     ea.label = label;
@@ -2820,10 +2829,11 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
         uint32_t *bits = nullptr, *fsid = nullptr;
         const uint64_t n = (uint64_t)nb * N;
         if ((st = alloc(&bits, (N + 31) / 32))) return fail(st);
-        // the copy saves the pair passes' bitmap lookups but costs b * N * 4
-        // bytes: it is made only when that is a small part of the memory left
-        // (the pair buffer needs the rest); without it the passes read the bitmap
-        if (n * 16 <= room_bytes(c) && alloc(&fsid, n)) {
+        // the copy saves the pair passes' bitmap lookups (the bitmap, N/8
+        // bytes, mostly stays in L2) but costs b * N * 4 bytes: it is made
+        // only when that is a small part of the memory left (the pair buffer
+        // needs the rest); without it the passes read the bitmap
+        if (n * 64 <= room_bytes(c) && alloc(&fsid, n)) {
             fsid = nullptr;
             c->err.clear();
         }
