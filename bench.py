@@ -400,7 +400,7 @@ def station_arm(args, rank, world, local_rank, w, steps, warmup, e2e=True):
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": workload_config(w, world, {"detections_per_station": M}),
             "gpu_launches": meter.launches, "clocks": clk}
-    if e2e:  # end to end through the host entry point: pinned input in, pinned result out
+    if e2e and not args.no_e2e:  # end to end through the host entry point: pinned input in, pinned result out
         e2e_steps = max(1, min(steps, args.e2e_steps))
         h_i = torch.empty(M, dtype=torch.int32, pin_memory=True)
         h_j = torch.empty(M, dtype=torch.int32, pin_memory=True)

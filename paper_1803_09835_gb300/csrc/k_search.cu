@@ -2295,8 +2295,8 @@ __global__ void k_part_cuts(const uint64_t *__restrict__ goff, uint64_t ng, uint
 template <typename PT, typename Alloc>
 static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *medium, uint64_t nmedium,
                                  uint32_t gshift, uint32_t nbits, uint32_t *sp_cnt, uint64_t *sp_start,
-                                 uint32_t **sp_j_out, uint8_t **sp_v_out, uint2 *long_rows, uint64_t &S_out,
-                                 Alloc &alloc, cudaStream_t s, uint64_t S_ub) {
+                                 uint32_t **sp_j_out, uint8_t **sp_v_out, uint64_t *sp_n_out, uint2 *long_rows,
+                                 uint64_t &S_out, Alloc &alloc, cudaStream_t s, uint64_t S_ub) {
     const fast_params &p = c->p;
     const uint64_t N = ea.N;
     unsigned long long *scal = reinterpret_cast<unsigned long long *>(c->d_scal);
@@ -2487,14 +2487,33 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     VoteArgs va{goff, ng, N, 0, ng, 0, gshift, nbits, p.v, vcap, sp_cnt, sp_start, nullptr, nullptr, 0,
                 scal + Scal::CUR_SPARSE, long_rows, scal + Scal::NLONG, N,
                 single ? gcur : nullptr, rcap, ovf_sorted, ostart};
+    // the sparse detection lists outlive this function (the caller places
+    // them); a second attempt with their exact size first gives back the
+    // first attempt's, too short ones
+    struct SpLists {
+        fast_ctx *c;
+        cudaStream_t s;
+        uint32_t *j = nullptr;
+        uint8_t *v = nullptr;
+        uint64_t n = 0;
+        bool keep = false;
+        void drop() {
+            if (j) dfree(c, j, n * 4, s);
+            if (v) dfree(c, v, n, s);
+            j = nullptr;
+            v = nullptr;
+            n = 0;
+        }
+        ~SpLists() {
+            if (!keep) drop();
+        }
+    } sp{c, s};
     for (int attempt = 0; attempt < 2; attempt++) {
-        uint32_t *sp_j = nullptr;
-        uint8_t *sp_v = nullptr;
-        if ((st = alloc(&sp_j, sp_cap)) || (st = alloc(&sp_v, sp_cap))) return st;
-        *sp_j_out = sp_j;
-        *sp_v_out = sp_v;
-        va.sp_j = sp_j;
-        va.sp_v = sp_v;
+        sp.drop();
+        if ((st = dalloc_t(c, &sp.j, sp_cap, s)) || (st = dalloc_t(c, &sp.v, sp_cap, s))) return st;
+        sp.n = sp_cap;
+        va.sp_j = sp.j;
+        va.sp_v = sp.v;
         va.sp_cap = sp_cap;
         cudaMemsetAsync(sp_cnt, 0, N * 4, s);
         cudaMemsetAsync(scal + Scal::CUR_SPARSE, 0, 8, s);
@@ -2580,7 +2599,13 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
             }
         }
         const uint64_t used = c->h_scal[Scal::CUR_SPARSE];
-        if (used <= sp_cap) return FAST_OK;
+        if (used <= sp_cap) {
+            sp.keep = true;
+            *sp_j_out = sp.j;
+            *sp_v_out = sp.v;
+            *sp_n_out = sp.n;
+            return FAST_OK;
+        }
         if (attempt == 1) break;
         sp_cap = used;  // exact size for the second pass
     }
@@ -2857,13 +2882,16 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
         const uint32_t target = c->group_pairs ? c->group_pairs : kVTargetDefault;
         while (gshift < 12 && (double)(2ull << gshift) * avg <= target) gshift++;
         // 32-bit entries while entry + 1 cannot wrap to the empty key
+        uint64_t sp_n = 0;
         const fast_status r = gshift + nbits < 32
                                   ? sparse_groups<uint32_t>(c, ea, medium, nmedium, gshift, nbits, sp_cnt, sp_start,
-                                                            &sp_j, &sp_v, long_rows, S, alloc, s, S_ub)
+                                                            &sp_j, &sp_v, &sp_n, long_rows, S, alloc, s, S_ub)
                                   : sparse_groups<unsigned long long>(c, ea, medium, nmedium, gshift, nbits, sp_cnt,
-                                                                      sp_start, &sp_j, &sp_v, long_rows, S, alloc, s,
-                                                                      S_ub);
+                                                                      sp_start, &sp_j, &sp_v, &sp_n, long_rows, S,
+                                                                      alloc, s, S_ub);
         if (r) return fail(r);
+        owned.push_back({(void *)sp_j, sp_n * 4});  // freed with the search's other buffers
+        owned.push_back({(void *)sp_v, sp_n});
     }
     stage_mark(c, 6, s);
 
