@@ -743,7 +743,9 @@ def sweep_arm(args):
             row = {"skew": skew, "corr": corr, "r": r, "windows": n, "bucket_pairs": pairs,
                    "selectivity": pairs / (p["b"] * n * (n - 1) / 2), "largest_bucket": big,
                    "top0.1%_bucket_share": float(np.mean(top)), "detections": res.M, "dropped": st["n_dropped"],
-                   "search_ms": ms}
+                   "search_ms": ms, **{k: st[k] for k in ("n_emissions", "n_dense_pairs", "n_groups", "max_group",
+                                                          "n_long_rows", "n_huge_rows", "max_row", "large_min",
+                                                          "ms_enum", "ms_dense", "ms_sparse")}}
             print(json.dumps(row), flush=True)
             rows.append(row)
             res.free()
