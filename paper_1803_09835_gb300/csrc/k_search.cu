@@ -1983,12 +1983,14 @@ uint64_t room_bytes(const fast_ctx *c) {
     return avail > (1ull << 30) ? avail - (1ull << 30) : 0;
 }
 
-// Memory the pair buffer may take: the room less a reserve for what the
-// votes allocate beside it (the slow-group list, the sparse lists, long-row
-// scratch of at most 2 GiB): an eighth of the room, at least 4 GiB, at most half.
-static uint64_t pair_room(const fast_ctx *c) {
+// Memory the pair buffer may take: the room less what the votes allocate
+// beside it (`extra`: the slow-group list, the sparse lists, the long-row
+// offsets and scratch) and a margin of 1 GiB or a sixteenth of the room;
+// at most half the room when that reserve is most of it.
+static uint64_t pair_room(const fast_ctx *c, uint64_t extra) {
     const uint64_t r = room_bytes(c);
-    return r - std::min<uint64_t>(r / 2, std::max<uint64_t>(r / 8, 4ull << 30));
+    const uint64_t keep = std::max<uint64_t>(extra + (1ull << 30), r / 16);
+    return r > 2 * keep ? r - keep : r / 2;
 }
 
 // Tiles of 32 table entries per warp for the warp-window passes: enough warps
@@ -2302,6 +2304,9 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     unsigned long long *scal = reinterpret_cast<unsigned long long *>(c->d_scal);
     fast_status st;
     const uint64_t ng = (N + (1ull << gshift) - 1) >> gshift;
+    // what the votes allocate beside the pair buffer: slow-group list, long-row
+    // offsets, first sparse lists, long-row scratch (at most 2 GiB per launch)
+    const uint64_t vote_extra = 8 * ng + 8 * N + 5 * std::max<uint64_t>(N, 1 << 20) + (2ull << 30);
     c->stats.ms_k_pairs = c->stats.ms_k_medium = c->stats.ms_k_vote = c->stats.ms_k_vote_block = 0.f;
     c->stats.ms_k_count_small = c->stats.ms_k_count_medium = 0.f;
     // the pair buffers live only as long as this function: they are given
@@ -2353,7 +2358,7 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
         if (c->group_slots) cap = c->group_slots;
         const uint64_t ovf_cap = c->group_slots ? S_ub + (1 << 20) : std::max<uint64_t>(1 << 20, S_ub / 8);
         const uint64_t need = ng * cap * 4 + ovf_cap * 16;
-        const uint64_t room = pair_room(c);
+        const uint64_t room = pair_room(c, vote_extra);
         uint32_t *region = nullptr;
         unsigned long long *ovf = nullptr;
         if (need <= room && !(st = lalloc(&region, ng * cap)) && !(st = lalloc(&ovf, ovf_cap))) {
@@ -2430,7 +2435,7 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     // one range.  As many as query_part asks for, or as the HBM budget needs.
     uint32_t nparts = std::max<uint32_t>(1, p.query_part);
     if (!single) {
-        const uint64_t room = pair_room(c);
+        const uint64_t room = pair_room(c, vote_extra);
         const uint64_t need = S * sizeof(PT);
         if (room && need > room) nparts = std::max<uint64_t>(nparts, (need + room - 1) / room);
     }
@@ -2481,6 +2486,21 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper, k_warp_vote<PT>, kVW * 32, wsm);
     uint2 *slow = nullptr;  // (group, rows r0 << 16 | r1) left to the block kernel
     if ((st = lalloc(&slow, 8 * ng))) return st;
+    // long rows' offsets into their global hash scratch (one list for every
+    // partition); the scratch itself is allocated at the first need
+    uint64_t *d_gofs = nullptr;
+    if ((st = lalloc(&d_gofs, N))) return st;
+    uint32_t *gscr = nullptr;
+    uint64_t gscr_cap = 0;
+    struct Scratch {
+        fast_ctx *c;
+        cudaStream_t s;
+        uint32_t *&p;
+        uint64_t &n;
+        ~Scratch() {
+            if (p) dfree(c, p, n * 4, s);
+        }
+    } gscr_guard{c, s, gscr, gscr_cap};
     const size_t rsm = (size_t)2 * kRowBlockSlots * 4;
     cudaFuncSetAttribute(k_long_vote<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
     uint64_t sp_cap = std::max<uint64_t>(N, 1 << 20);
@@ -2583,9 +2603,13 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
                     c->stats.n_huge_rows += need != 0;
                 }
                 chunk.push_back(nlong);
-                uint32_t *gscr = nullptr;
-                uint64_t *d_gofs = nullptr;
-                if ((st = lalloc(&gscr, gmax)) || (st = lalloc(&d_gofs, nlong))) return st;
+                if (gmax > gscr_cap) {  // one scratch for every partition, grown only when a row needs more
+                    dfree(c, gscr, gscr_cap * 4, s);
+                    gscr = nullptr;
+                    gscr_cap = 0;
+                    if ((st = dalloc_t(c, &gscr, gmax, s))) return st;
+                    gscr_cap = gmax;
+                }
                 cudaMemcpyAsync(d_gofs, gofs.data(), nlong * 8, cudaMemcpyHostToDevice, s);
                 for (size_t k = 0; k + 1 < chunk.size(); k++) {
                     const uint64_t r0 = chunk[k], nr = chunk[k + 1] - r0;
@@ -2691,6 +2715,15 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
     cudaMemsetAsync(dense_cnt, 0, N * 4, s);
     std::vector<uint64_t> hm;
     uint64_t *sorted = nullptr;  // members as (group << 32 | id), sorted
+    std::vector<std::pair<void *, size_t>> round_bufs;  // the last grouping round's member buffers
+    struct RoundGuard {
+        fast_ctx *c;
+        cudaStream_t s;
+        std::vector<std::pair<void *, size_t>> &v;
+        ~RoundGuard() {
+            for (auto &b : v) dfree(c, b.first, b.second, s);
+        }
+    } round_guard{c, s, round_bufs};
     // Groups are the connected components of the large buckets.  With the
     // automatic threshold a group must stay dense: comparing all its member
     // pairs may not cost more than the large buckets' own pairs (which the
@@ -2716,12 +2749,16 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
         }
         if (it == 256) return fail(set_error(c, FAST_EINTERNAL, "group labels did not converge"));
         cudaMemsetAsync(scal + Scal::NMEMB, 0, 8, s);
+        for (auto &b : round_bufs) dfree(c, b.first, b.second, s);  // the previous round's members
+        round_bufs.clear();
         unsigned long long *memb = nullptr, *memb2 = nullptr;
-        if ((st = alloc(&memb, N))) return fail(st);
+        if ((st = dalloc_t(c, &memb, N, s))) return fail(st);
+        round_bufs.push_back({(void *)memb, N * 8});
         k_collect_members<<<blocksN, 256, 0, s>>>(label, N, memb, scal + Scal::NMEMB), FAST_LAUNCHED(c);
         if ((st = read_scal(c, s, "group members"))) return fail(st);
         nm = c->h_scal[Scal::NMEMB];
-        if ((st = alloc(&memb2, nm))) return fail(st);
+        if ((st = dalloc_t(c, &memb2, nm ? nm : 1, s))) return fail(st);
+        round_bufs.push_back({(void *)memb2, (nm ? nm : 1) * 8});
         if ((st = sort_u64(c, nm, reinterpret_cast<uint64_t *>(memb), reinterpret_cast<uint64_t *>(memb2), 0,
                            32 + bits_for(N), &sorted, s)))
             return fail(st);
@@ -2751,6 +2788,8 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
         nmedium = c->h_scal[Scal::NMEDIUM];
     }
     c->stats.large_min = large_min;
+    for (auto &b : round_bufs) owned.push_back(b);  // `sorted` lives in them: freed with the search's buffers
+    round_bufs.clear();
     stage_mark(c, 4, s);
     if (nlarge) {
         if ((st = alloc(&GT, (size_t)nm * nb)) || (st = alloc(&ids, nm))) return fail(st);
