@@ -647,18 +647,20 @@ def units_of(st: dict, N: int) -> dict:
             "medium-bucket pair": st["n_emissions"] - st["n_pairs_small"], "emission": st["n_emissions"]}
 
 
-def record_traffic(csv_path: str, line_path: str, command: str, out_path: str | None = None) -> dict:
+def record_traffic(csv_path: str, line_path: str, command: str, out_path: str | None = None, runs: int = 1) -> dict:
     """profiles/dram_traffic.json from one ncu --csv capture of
     dram__bytes_read.sum and dram__bytes_write.sum over a single-station run
     of bench.py, and that run's own JSON line (its counters): per kernel of
     TRAFFIC_KERNELS, the DRAM bytes of its launches per unit of its work
     (fingerprints, pairs written, emissions voted), with the hash of the
-    kernel's source file at capture time.  A launch of the pair kernels is
-    scaled by pairs, not windows: their bytes follow the pairs they write."""
+    kernel's source file at capture time.  `runs` = the searches the capture
+    covers (warm-up and timed steps; the line's counters are one search's).
+    A launch of the pair kernels is scaled by pairs, not windows: their
+    bytes follow the pairs they write."""
     import csv
     line = json.loads([x for x in open(line_path) if x.startswith("{")][-1])
     N = line["config"]["N_per_station"]
-    units = units_of(line["counters"], N)
+    units = {k: v * runs for k, v in units_of(line["counters"], N).items()}
     scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
     rows = list(csv.reader(open(csv_path)))
     hdr = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
@@ -687,7 +689,8 @@ def record_traffic(csv_path: str, line_path: str, command: str, out_path: str | 
         n = max(1, units[unit])
         out[name] = {"source": src, "source_sha256_16": _kernel_source_hash(src),
                      "bytes_per_unit": (rec["read"] + rec["write"]) / n, "unit": unit,
-                     "captured_on": f"{N:,} windows, {len(rec['ids'])} launch(es), {n:,} {unit}s",
+                     "captured_on": f"{N:,} windows, {runs} search(es), {len(rec['ids'])} launch(es), "
+                                    f"{n:,} {unit}s",
                      "dram_read_bytes": rec["read"], "dram_write_bytes": rec["write"], "command": command}
     with open(out_path or os.path.join(ROOT, "profiles", "dram_traffic.json"), "w") as f:
         json.dump(out, f, indent=1)
@@ -1000,10 +1003,12 @@ def main():
     ap.add_argument("--record-traffic", default="", metavar="CSV",
                     help="write profiles/dram_traffic.json from an ncu dram-bytes capture of this workload")
     ap.add_argument("--record-line", default="", help="the JSON line of the captured run (its counters)")
+    ap.add_argument("--record-runs", type=int, default=1, help="searches the capture covers")
     ap.add_argument("--record-command", default="", help="the ncu command line to note beside --record-traffic")
     args = ap.parse_args()
     if args.record_traffic:
-        print(json.dumps(record_traffic(args.record_traffic, args.record_line, args.record_command), indent=1))
+        print(json.dumps(record_traffic(args.record_traffic, args.record_line, args.record_command,
+                                        runs=args.record_runs), indent=1))
         return 0
     if args.serving:
         return serving_arm(args)
