@@ -134,6 +134,9 @@ def _load():
     lib.synth_generate_rows.restype = i32
     lib.synth_generate_rows.argtypes = [u64, u64, u64, u32, u32, vp, u32, u64, u32, vp, dbl, u32, u32, u32, dbl,
                                         u64, u64, u32, i32, vp, dbl, dbl]
+    lib.synth_generate_ids.restype = i32
+    lib.synth_generate_ids.argtypes = [u64, vp, u64, u32, u32, vp, u32, u64, u32, vp, dbl, u32, u32, u32, dbl,
+                                       u64, u64, u32, i32, vp, dbl, dbl]
     return lib
 
 
@@ -147,6 +150,44 @@ def build() -> str:
 
 
 _lib = None
+
+
+def owners(w: Workload, rows: tuple | None = None) -> np.ndarray:
+    """Only the source codes of windows r0 .. r1 - 1 (no fingerprints drawn):
+    0 random, OWNER_PERIODIC | p, OWNER_TEMPLATE | tau."""
+    global _lib
+    if _lib is None:
+        _lib = _load()
+    r0, r1 = rows if rows is not None else (0, w.N)
+    if not 0 <= r0 <= r1 <= w.N:
+        raise ValueError("rows outside the station")
+    own = np.empty(max(1, r1 - r0), dtype=np.uint32)
+    periods = (ctypes.c_uint64 * max(1, len(w.periods)))(*w.periods)
+    rc = _lib.synth_generate_rows(w.N, r0, r1 - r0, w.D, w.K, None, w.K, w.seed, len(w.periods), periods,
+                                  w.per_redraw, w.n_templates, w.rep_lo, w.rep_hi, w.tpl_redraw, w.tpl_seed or w.seed,
+                                  w.place_range, w.tpl_offset_max, 0, own.ctypes.data, float(w.skew), float(w.corr))
+    if rc < 0:
+        raise ValueError("synth_generate_rows: bad arguments")
+    return own[:r1 - r0]
+
+
+def generate_ids(w: Workload, ids, ld: int | None = None) -> np.ndarray:
+    """The windows ids (any order) of the station, [len(ids), ld] uint16: each
+    exactly that row of the whole station."""
+    global _lib
+    if _lib is None:
+        _lib = _load()
+    ld = ld or w.K
+    ids = np.ascontiguousarray(ids, dtype=np.uint64)
+    out = np.empty((max(1, len(ids)), ld), dtype=np.uint16)
+    periods = (ctypes.c_uint64 * max(1, len(w.periods)))(*w.periods)
+    rc = _lib.synth_generate_ids(w.N, ids.ctypes.data, len(ids), w.D, w.K, out.ctypes.data, ld, w.seed,
+                                 len(w.periods), periods, w.per_redraw, w.n_templates, w.rep_lo, w.rep_hi,
+                                 w.tpl_redraw, w.tpl_seed or w.seed, w.place_range, w.tpl_offset_max, 0, None,
+                                 float(w.skew), float(w.corr))
+    if rc < 0:
+        raise ValueError("synth_generate_ids: bad arguments")
+    return out[:len(ids)]
 
 
 def generate(w: Workload, ld: int | None = None, out=None, threads: int = 0, owner: bool = False,

@@ -172,6 +172,7 @@ typedef struct {
     uint32_t D, K, ld;
     uint16_t *out;
     const uint32_t *owner; /* indexed by w - row0 */
+    const uint64_t *ids;   /* when set: row w - row0 is window ids[w - row0] */
     const uint16_t *pbase, *tbase;
     double per_redraw, tpl_redraw;
     const syn_skew *sk;
@@ -182,9 +183,10 @@ static void *syn_worker(void *arg)
     syn_job *j = arg;
     uint64_t *bm = malloc(sizeof(uint64_t) * ((j->D + 63) / 64));
     uint32_t *perm = malloc(sizeof(uint32_t) * (j->K ? j->K : 1));
-    for (uint64_t w = j->w0; w < j->w1; w++) {
-        uint16_t *row = j->out + (w - j->row0) * (uint64_t)j->ld;
-        uint32_t own = j->owner[w - j->row0];
+    for (uint64_t r = j->w0; r < j->w1; r++) {
+        const uint64_t w = j->ids ? j->ids[r - j->row0] : r; /* the window drawn into row r - row0 */
+        uint16_t *row = j->out + (r - j->row0) * (uint64_t)j->ld;
+        uint32_t own = j->owner[r - j->row0];
         uint32_t kind = own & (3u << 30), id = own & ((1u << 30) - 1);
         if (kind == OWNER_RANDOM) {
             syn_rng g = {syn_stream(j->seed, DOM_ROW, w), 0};
@@ -204,7 +206,8 @@ static void *syn_worker(void *arg)
 }
 
 /*
- * Fills out[nrows][ld] (ld >= K) with windows row0 .. row0 + nrows - 1 of the
+ * Fills out[nrows][ld] (ld >= K; out == NULL: no rows, owners only) with
+ * windows row0 .. row0 + nrows - 1 of the
  * station's N windows and, when owner_out != NULL, owner_out[nrows] with each
  * window's source: 0 random, (1<<30)|p periodic source p, (2<<30)|tau
  * template tau.  Every window depends only on (seed, its index), so any range
@@ -218,14 +221,44 @@ static void *syn_worker(void *arg)
  * Periodic sources and everything else draw from `seed`.
  * Returns the number of threads used, or -1 on bad arguments.
  */
-int synth_generate_rows(uint64_t N, uint64_t row0, uint64_t nrows, uint32_t D, uint32_t K, uint16_t *out,
-                        uint32_t ld, uint64_t seed, uint32_t n_periodic, const uint64_t *periods,
+static int syn_cmp_u64(const void *a, const void *b)
+{
+    const uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : x > y;
+}
+
+/* position of w among the sorted distinct ids sid[0 .. m), or -1 */
+static int64_t syn_find(const uint64_t *sid, uint64_t m, uint64_t w)
+{
+    uint64_t lo = 0, hi = m;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) / 2;
+        if (sid[mid] < w) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < m && sid[lo] == w ? (int64_t)lo : -1;
+}
+
+/* rows row0 .. row0 + nrows - 1, or (ids != NULL) the windows ids[0 .. nrows) */
+static int syn_generate(uint64_t N, uint64_t row0, uint64_t nrows, const uint64_t *ids, uint32_t D, uint32_t K,
+                        uint16_t *out, uint32_t ld, uint64_t seed, uint32_t n_periodic, const uint64_t *periods,
                         double per_redraw, uint32_t n_templates, uint32_t rep_lo, uint32_t rep_hi,
                         double tpl_redraw, uint64_t tpl_seed, uint64_t place_range, uint32_t tpl_offset_max,
                         int nthreads, uint32_t *owner_out, double skew, double corr)
 {
     if (D == 0 || D > 65536 || K == 0 || K > D || ld < K || rep_hi < rep_lo) return -1;
-    if (row0 > N || nrows > N - row0) return -1;
+    if (!ids && (row0 > N || nrows > N - row0)) return -1;
+    uint64_t *sid = NULL, m = 0; /* the listed windows, sorted and distinct */
+    if (ids) {
+        for (uint64_t k = 0; k < nrows; k++)
+            if (ids[k] >= N) return -1;
+        sid = malloc(sizeof(uint64_t) * (nrows ? nrows : 1));
+        memcpy(sid, ids, sizeof(uint64_t) * nrows);
+        qsort(sid, nrows, sizeof(uint64_t), syn_cmp_u64);
+        for (uint64_t k = 0; k < nrows; k++)
+            if (m == 0 || sid[m - 1] != sid[k]) sid[m++] = sid[k];
+        row0 = 0;
+    }
     if (!(skew >= 0) || !(corr >= 0 && corr <= 1)) return -1;
     /* the skew: ranks drawn from the station seed (a Fisher-Yates shuffle) */
     syn_skew skv = {NULL, NULL, NULL, corr};
@@ -254,10 +287,12 @@ int synth_generate_rows(uint64_t N, uint64_t row0, uint64_t nrows, uint32_t D, u
         skv.rank = srank;
     }
     const syn_skew *sk = skew > 0 ? &skv : NULL;
+    const int rows_wanted = out != NULL; /* out == NULL: owner codes only */
     if (place_range == 0) place_range = N;
     const uint64_t row1 = row0 + nrows;
     uint32_t *owner = owner_out ? owner_out : malloc(sizeof(uint32_t) * (nrows ? nrows : 1));
     memset(owner, 0, sizeof(uint32_t) * nrows);
+    uint32_t *down = ids ? calloc(m ? m : 1, sizeof(uint32_t)) : NULL; /* owner of each distinct id */
     uint64_t *bm = malloc(sizeof(uint64_t) * ((D + 63) / 64));
 
     uint16_t *pbase = malloc(sizeof(uint16_t) * (uint64_t)K * (n_periodic ? n_periodic : 1));
@@ -267,6 +302,11 @@ int synth_generate_rows(uint64_t N, uint64_t row0, uint64_t nrows, uint32_t D, u
         syn_rng h = {syn_stream(seed, DOM_PPHASE, p), 0};
         uint64_t P = periods[p] ? periods[p] : 1;
         uint64_t w = syn_below(&h, P);
+        if (ids) {
+            for (uint64_t k = 0; k < m; k++)
+                if (sid[k] >= w && (sid[k] - w) % P == 0) down[k] = OWNER_PERIODIC | p;
+            continue;
+        }
         if (w < row0) w += (row0 - w + P - 1) / P * P; /* first copy at or after row0 */
         for (; w < row1; w += P) owner[w - row0] = OWNER_PERIODIC | p;
     }
@@ -281,10 +321,17 @@ int synth_generate_rows(uint64_t N, uint64_t row0, uint64_t nrows, uint32_t D, u
         uint64_t delta = syn_below(&off, (uint64_t)tpl_offset_max + 1);
         for (uint32_t k = 0; k < reps; k++) {
             uint64_t w = syn_below(&pl, place_range) + delta;
-            if (w < N && w >= row0 && w < row1) owner[w - row0] = OWNER_TEMPLATE | t;
+            if (ids) {
+                const int64_t q = w < N ? syn_find(sid, m, w) : -1;
+                if (q >= 0) down[q] = OWNER_TEMPLATE | t;
+            } else if (w < N && w >= row0 && w < row1) {
+                owner[w - row0] = OWNER_TEMPLATE | t;
+            }
         }
     }
     free(bm);
+    if (ids)
+        for (uint64_t k = 0; k < nrows; k++) owner[k] = down[syn_find(sid, m, ids[k])];
 
     int T = nthreads;
     if (T <= 0) {
@@ -292,11 +339,12 @@ int synth_generate_rows(uint64_t N, uint64_t row0, uint64_t nrows, uint32_t D, u
         T = n > 0 ? (int)n : 1;
     }
     if ((uint64_t)T > nrows / 4096 + 1) T = (int)(nrows / 4096 + 1);
-    pthread_t *th = malloc(sizeof(pthread_t) * T);
-    syn_job *jobs = malloc(sizeof(syn_job) * T);
+    if (!rows_wanted) T = 0;
+    pthread_t *th = malloc(sizeof(pthread_t) * (T ? T : 1));
+    syn_job *jobs = malloc(sizeof(syn_job) * (T ? T : 1));
     for (int k = 0; k < T; k++) {
         jobs[k] = (syn_job){N,   row0 + nrows * k / T, row0 + nrows * (k + 1) / T, row0, seed, D, K, ld,
-                            out, owner, pbase, tbase, per_redraw, tpl_redraw, sk};
+                            out, owner, ids, pbase, tbase, per_redraw, tpl_redraw, sk};
         pthread_create(&th[k], NULL, syn_worker, &jobs[k]);
     }
     for (int k = 0; k < T; k++) pthread_join(th[k], NULL);
@@ -307,8 +355,41 @@ int synth_generate_rows(uint64_t N, uint64_t row0, uint64_t nrows, uint32_t D, u
     free(cdf);
     free(sbit);
     free(srank);
+    free(down);
+    free(sid);
     if (!owner_out) free(owner);
     return T;
+}
+
+/*
+ * Fills out[nrows][ld] (ld >= K; out == NULL: owners only) with windows
+ * row0 .. row0 + nrows - 1 of the station's N windows; see syn_generate.
+ */
+int synth_generate_rows(uint64_t N, uint64_t row0, uint64_t nrows, uint32_t D, uint32_t K, uint16_t *out,
+                        uint32_t ld, uint64_t seed, uint32_t n_periodic, const uint64_t *periods,
+                        double per_redraw, uint32_t n_templates, uint32_t rep_lo, uint32_t rep_hi,
+                        double tpl_redraw, uint64_t tpl_seed, uint64_t place_range, uint32_t tpl_offset_max,
+                        int nthreads, uint32_t *owner_out, double skew, double corr)
+{
+    return syn_generate(N, row0, nrows, NULL, D, K, out, ld, seed, n_periodic, periods, per_redraw, n_templates,
+                        rep_lo, rep_hi, tpl_redraw, tpl_seed, place_range, tpl_offset_max, nthreads, owner_out, skew,
+                        corr);
+}
+
+/*
+ * Windows ids[0 .. n) of the station (any order, repeats allowed) into
+ * out[n][ld], each exactly the row the whole station has (owners as well,
+ * when owner_out != NULL); the sources' placements are walked once for all
+ * of them.
+ */
+int synth_generate_ids(uint64_t N, const uint64_t *ids, uint64_t n, uint32_t D, uint32_t K, uint16_t *out,
+                       uint32_t ld, uint64_t seed, uint32_t n_periodic, const uint64_t *periods, double per_redraw,
+                       uint32_t n_templates, uint32_t rep_lo, uint32_t rep_hi, double tpl_redraw, uint64_t tpl_seed,
+                       uint64_t place_range, uint32_t tpl_offset_max, int nthreads, uint32_t *owner_out,
+                       double skew, double corr)
+{
+    return syn_generate(N, 0, n, ids, D, K, out, ld, seed, n_periodic, periods, per_redraw, n_templates, rep_lo,
+                        rep_hi, tpl_redraw, tpl_seed, place_range, tpl_offset_max, nthreads, owner_out, skew, corr);
 }
 
 /* The whole station: rows 0 .. N - 1 (see synth_generate_rows). */

@@ -476,9 +476,7 @@ def test_c4_full_size_chunked_table_groups():
     rng = np.random.default_rng(4)
 
     def keys_of(ids):
-        ids = np.asarray(ids, np.int64)
-        rows = np.concatenate([synth.generate(w, ld=400, rows=(int(x), int(x) + 1)) for x in ids])
-        return oracle.keys(p, rows)
+        return oracle.keys(p, synth.generate_ids(w, np.asarray(ids, np.uint64), ld=400))
 
     # exact votes of sampled entries
     xs = rng.integers(0, len(gi), 2000)
@@ -487,10 +485,7 @@ def test_c4_full_size_chunked_table_groups():
     # recall on candidate pairs among windows of one template or source that
     # the filter cannot touch (sources repeating more often than every 200 s
     # are the only ones whose buckets can exceed 0.5 % of the station)
-    own = np.empty(w.N, np.uint32)
-    for r0 in range(0, w.N, 1 << 24):
-        r1 = min(w.N, r0 + (1 << 24))
-        own[r0:r1] = synth.generate(w, ld=400, rows=(r0, r1), owner=True)[1]
+    own = synth.owners(w)
     groups = {}
     for code in (synth.OWNER_PERIODIC + 3, synth.OWNER_PERIODIC + 4):  # 3600 s and 86400 s sources
         groups[code] = np.nonzero(own == code)[0]

@@ -99,3 +99,23 @@ def test_skewed_and_correlated_bits():
     a, own = synth.generate(ws, owner=True)
     assert np.all(np.diff(a.astype(np.int32), axis=1) > 0)
     assert (own >= synth.OWNER_TEMPLATE).sum() > 0
+
+
+def test_owners_only_and_listed_windows():
+    # the source codes alone, and arbitrary lists of windows, equal the whole
+    # station's (the full-size tests draw sampled windows this way)
+    for name, n in (("c4", 60_000), ("c2", 50_000)):
+        w = synth.scaled(name, n, station=3) if name == "c2" else synth.scaled(name, n)
+        full, own = synth.generate(w, ld=400, owner=True)
+        assert np.array_equal(synth.owners(w), own)
+        assert np.array_equal(synth.owners(w, rows=(1234, 40_000)), own[1234:40_000])
+        rng = np.random.default_rng(3)
+        ids = np.concatenate([rng.integers(0, n, 500), np.nonzero(own >= synth.OWNER_TEMPLATE)[0][:100],
+                              np.nonzero((own >= synth.OWNER_PERIODIC) & (own < synth.OWNER_TEMPLATE))[0][:50],
+                              [0, n - 1, 7, 7]])
+        assert np.array_equal(synth.generate_ids(w, ids, ld=400), full[ids])
+    from dataclasses import replace
+    ws = replace(synth.scaled("c1", 20_000), skew=0.6, corr=0.3)
+    full = synth.generate(ws)
+    ids = np.array([19_999, 5, 5, 12_345])
+    assert np.array_equal(synth.generate_ids(ws, ids), full[ids])
