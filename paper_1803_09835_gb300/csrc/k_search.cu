@@ -244,7 +244,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *wsum, 
 // Classifies big buckets by live size: >= large_min -> large list (dense
 // path), otherwise medium list; counts medium pairs per query partition
 // (each live member i pairs with the live members after it).
-__global__ void __launch_bounds__(256) k_big_classify(EnumArgs a, const uint4 *__restrict__ big,
+__global__ void __launch_bounds__(256) k_big_classify(EnumArgs a, uint4 *__restrict__ big,
                                                       const unsigned long long *__restrict__ nbig, uint64_t big_cap,
                                                       uint32_t large_min, uint4 *__restrict__ large,
                                                       unsigned long long *__restrict__ nlarge, uint4 *__restrict__ medium,
@@ -259,20 +259,30 @@ __global__ void __launch_bounds__(256) k_big_classify(EnumArgs a, const uint4 *_
     for (uint64_t bi = blockIdx.x; bi < n; bi += gridDim.x) {
         const uint4 e = big[bi];
         const uint32_t *s = a.sid + (uint64_t)e.x * a.N;
-        uint32_t live = 0;
-        for (uint32_t q = e.y + threadIdx.x; q < e.z; q += blockDim.x) live += !a.drop[s[q]];
-        for (int o = 16; o; o >>= 1) live += __shfl_down_sync(~0u, live, o);
-        if (threadIdx.x == 0) s_live = 0;
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) atomicAdd(&s_live, live);
-        __syncthreads();
-        const uint32_t nl = s_live;
+        // live members: counted once per table set and kept in the entry's w
+        // (live + 1; 0 = not counted yet): they depend only on the drop mask
+        uint32_t nl;
+        if (e.w) {  // block-uniform
+            nl = e.w - 1;
+        } else {
+            uint32_t live = 0;
+            for (uint32_t q = e.y + threadIdx.x; q < e.z; q += blockDim.x) live += !a.drop[s[q]];
+            for (int o = 16; o; o >>= 1) live += __shfl_down_sync(~0u, live, o);
+            if (threadIdx.x == 0) s_live = 0;
+            __syncthreads();
+            if ((threadIdx.x & 31) == 0) atomicAdd(&s_live, live);
+            __syncthreads();
+            nl = s_live;
+            if (threadIdx.x == 0) big[bi].w = nl + 1;
+        }
         if (threadIdx.x == 0 && lmax) atomicMax(lmax, (unsigned long long)nl);
         if (threadIdx.x == 0 && nl >= 2) {
             if (nl >= large_min) large[atomicAdd(nlarge, 1ull)] = make_uint4(e.x, e.y, e.z, nl);
             else medium[atomicAdd(nmedium, 1ull)] = make_uint4(e.x, e.y, e.z, nl);
         }
-        if (nl >= 2 && nl < large_min) {
+        if (a.nparts == 1) {  // one partition: the bucket's pairs are C(nl, 2)
+            if (threadIdx.x == 0 && nl >= 2 && nl < large_min) s_cnt[0] += (unsigned long long)nl * (nl - 1) / 2;
+        } else if (nl >= 2 && nl < large_min) {
             uint32_t rank0 = 0;
             for (uint32_t q0 = e.y; q0 < e.z; q0 += blockDim.x) {
                 const uint32_t q = q0 + threadIdx.x;
