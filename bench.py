@@ -320,7 +320,8 @@ def dominant(kernels):
 
 
 COUNTERS = ("n_dropped", "n_emissions", "n_dense_pairs", "n_groups", "n_detections", "query_parts", "sort_passes",
-            "n_long_rows", "n_huge_rows", "max_row", "n_pairs_small", "n_overflow", "peak_bytes")
+            "n_long_rows", "n_huge_rows", "max_row", "n_pairs_small", "n_overflow", "peak_bytes", "max_group",
+            "large_min", "dense_fallback")
 
 
 class Meter:

@@ -289,28 +289,22 @@ fast_status build_tables(fast_ctx *c, const uint32_t *d_sig, uint64_t N, const u
     if (!c->capturing)  // a captured build gets its offsets uploaded once by the plan
         cudaMemcpyAsync(tb->d_soff, tb->soff.data(), (nst + 1) * 8, cudaMemcpyHostToDevice, s);
     c->stats.sort_passes = 0;
+    // several stations: every station's part of a table is sorted on its own
+    uint64_t smax = 0;
+    for (uint32_t x = 0; x < nst; x++) smax = std::max<uint64_t>(smax, tb->soff[x + 1] - tb->soff[x]);
+    const Stations S = nst > 1 ? Stations{tb->d_soff, nst} : Stations{nullptr, 1};
     for (uint32_t t0 = 0; t0 < nb && !st && N; t0 += grp) {
         const uint32_t gn = std::min(grp, nb - t0);
         const size_t off = (size_t)t0 * N, m = (size_t)gn * N;
         uint32_t *dk = tb->d_skey + off, *dv = tb->d_sid + off;
         uint32_t *ko = nullptr, *vo = nullptr;
-        st = sort_u32(c, gn, N, d_sig + off, nullptr, ka, va, dk, dv, 0, 32, &ko, &vo, s, &c->stats.sort_passes);
+        st = sort_u32(c, gn, N, d_sig + off, nullptr, ka, va, dk, dv, 0, 32, &ko, &vo, s, &c->stats.sort_passes, S,
+                      smax);
         if (!st && ko != dk) {  // odd number of passes: result sits in the scratch pair
             cudaMemcpyAsync(dk, ko, m * 4, cudaMemcpyDeviceToDevice, s);
             cudaMemcpyAsync(dv, vo, m * 4, cudaMemcpyDeviceToDevice, s);
         }
-        if (!st && nst > 1) {  // stable station pass into the scratch pair
-            st = sort_station_pass(c, gn, N, dk, dv, ka, va, Stations{tb->d_soff, nst}, s);
-            if (!st && grp == nb) {  // one group: the scratch pair becomes the table
-                std::swap(tb->d_skey, ka);
-                std::swap(tb->d_sid, va);
-            } else if (!st) {
-                cudaMemcpyAsync(dk, ka, m * 4, cudaMemcpyDeviceToDevice, s);
-                cudaMemcpyAsync(dv, va, m * 4, cudaMemcpyDeviceToDevice, s);
-            }
-        }
     }
-    if (nst > 1 && N) c->stats.sort_passes++;
     dfree(c, ka, ns * 4, s);
     dfree(c, va, ns * 4, s);
     stage_mark(c, 2, s);

@@ -259,15 +259,15 @@ struct SortScratch {
     uint64_t *offsets = nullptr;  // [nseg][256][nchunks]
     size_t cap_entries = 0;
 };
+// With stations (S.nst > 1, device offsets), each of the nseg rows is sorted
+// station by station (seg_max: the longest station), which orders it by
+// (station, key, id).
 fast_status sort_u32(fast_ctx *c, uint32_t nseg, uint64_t len, const uint32_t *keys_in, const uint32_t *vals_in,
                      uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, uint32_t bit0,
-                     uint32_t bit1, uint32_t **keys_out, uint32_t **vals_out, cudaStream_t s, uint32_t *passes);
+                     uint32_t bit1, uint32_t **keys_out, uint32_t **vals_out, cudaStream_t s, uint32_t *passes,
+                     Stations S = Stations{nullptr, 1}, uint64_t seg_max = 0);
 fast_status sort_u64(fast_ctx *c, uint64_t len, uint64_t *keys_a, uint64_t *keys_b, uint32_t bit0, uint32_t bit1,
                      uint64_t **keys_out, cudaStream_t s);
-// One more stable pass that orders every segment by the station of its
-// values (ids): (key, id) runs become (station, key, id) runs.  nst <= 256.
-fast_status sort_station_pass(fast_ctx *c, uint32_t nseg, uint64_t len, const uint32_t *keys_in, const uint32_t *vals_in,
-                              uint32_t *keys_out, uint32_t *vals_out, Stations S, cudaStream_t s);
 
 // k_scan.cu: out[seg][k] = sum of in[seg][0..k), nseg segments of n counts;
 // totals[seg] (optional, device) receives each segment's sum.
@@ -300,7 +300,8 @@ uint64_t room_bytes(const fast_ctx *c);                 // device memory a call 
 void sig_release(fast_ctx *c, cudaStream_t s);          // frees the call's own key array, if any
 struct Scal {  // device scalar slots (ctx->d_scal)
     enum { NBIG, NLARGE, NMEDIUM, NHEAVY, NDROP, NMEMB, CUR_DENSE, CUR_SPARSE, CHANGED, NLONG, NMERGE, NMERGE_TOT,
-           NCAND, NMID, SMALLPAIRS, NSMALLEMIT, NSLOW, NOVF, LMAX, PART0 };
+           NCAND, NMID, SMALLPAIRS, NSMALLEMIT, NSLOW, NOVF, LMAX, NMEDW, NMEDF, NMEDB, NMEDH, MEDNEXT, MEDNEXTH,
+           PART0 };
 };
 void history_groups_free(HistGroups *g);
 

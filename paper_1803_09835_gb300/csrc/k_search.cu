@@ -800,31 +800,102 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
     }
 }
 
-// Medium buckets (more than kSmall entries, fewer than large_min live): one
-// CTA per bucket.  Live members (id, group label) are compacted in shared
-// memory; a bucket whose members all lie in one dense group has no sparse
-// pairs and is skipped.  Rows x are handed to warps one at a time and a warp's
-// lanes take the row's partners y > x 32 at a time, so the triangle of pairs
-// is shared evenly.  Buckets too large for shared memory fall back to one
-// thread per row over global memory.
+// Medium buckets (more than kSmall entries, fewer than large_min live) are
+// split by their number of entries: up to kWarpMed go to one warp each
+// (k_medium_warp), larger ones to one CTA each (k_medium_grp).  The CTAs take
+// buckets from a shared counter, those of more than kMedFirst entries first,
+// so that no large bucket starts last.  Buckets of more than kMedCap live
+// members get a launch of their own with the shared memory they need (up to
+// kMedHugeCap members).
+constexpr uint32_t kWarpMed = 128;
+constexpr uint32_t kMedFirst = 1024;
 constexpr uint32_t kMedCap = 4096;
+constexpr uint32_t kMedHugeCap = 28672;  // 224 KiB of members and labels
 
+struct MedLists {
+    const uint4 *warp;  // [*nwarp] buckets of <= kWarpMed entries
+    const uint4 *cta;   // [cap]: *nfront from the front, *nback from the back
+    const uint4 *huge;  // [*nhuge] buckets of more than kMedCap live members
+    const unsigned long long *nwarp, *nfront, *nback, *nhuge;
+    uint64_t cap;
+    unsigned long long *next, *next_h;  // the CTA launches' work counters, zeroed before each launch
+    __device__ __forceinline__ uint4 cta_at(uint64_t v, uint64_t nf) const {
+        return v < nf ? cta[v] : cta[cap - 1 - (v - nf)];
+    }
+};
+
+// Splits the medium list into the warp list and the CTA list (warp-aggregated
+// appends; the order inside each class does not matter).
+__global__ void __launch_bounds__(256) k_med_split(const uint4 *__restrict__ medium,
+                                                   const unsigned long long *__restrict__ nmedium,
+                                                   uint4 *__restrict__ wl, unsigned long long *__restrict__ nw,
+                                                   uint4 *__restrict__ cl, uint64_t cap,
+                                                   unsigned long long *__restrict__ nf,
+                                                   unsigned long long *__restrict__ nb, uint4 *__restrict__ hl,
+                                                   unsigned long long *__restrict__ nh) {
+    const uint64_t n = *nmedium;
+    const uint32_t lane = threadIdx.x & 31, lt = (1u << lane) - 1;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    for (uint64_t base = ((uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32) * 32; base < n;
+         base += nwarps * 32) {
+        const uint64_t x = base + lane;
+        uint4 e = make_uint4(0, 0, 0, 0);
+        uint32_t cls = 4;
+        if (x < n) {
+            e = medium[x];
+            const uint32_t raw = e.z - e.y;  // e.w: live members
+            cls = raw <= kWarpMed ? 0 : e.w > kMedCap ? 3 : raw > kMedFirst ? 1 : 2;
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < 4; k++) {
+            const uint32_t m = __ballot_sync(~0u, cls == k);
+            if (!m) continue;
+            const int leader = __ffs(m) - 1;
+            unsigned long long b0 = 0;
+            if ((int)lane == leader)
+                b0 = atomicAdd(k == 0 ? nw : k == 1 ? nf : k == 2 ? nb : nh, (unsigned long long)__popc(m));
+            b0 = __shfl_sync(~0u, b0, leader);
+            if (cls == k) {
+                const uint64_t q = b0 + __popc(m & lt);
+                if (k == 0) wl[q] = e;
+                else if (k == 1) cl[q] = e;
+                else if (k == 2) cl[cap - 1 - q] = e;
+                else hl[q] = e;
+            }
+        }
+    }
+}
+
+// One CTA per bucket.  Live members (id, group label) are compacted in shared
+// memory (mcap of them: dynamic shared memory of 8 mcap bytes); a bucket
+// whose members all lie in one dense group has no sparse pairs and is
+// skipped.  Rows x are handed to warps one at a time and a warp's lanes take
+// the row's partners y > x 32 at a time, so the triangle of pairs is shared
+// evenly.  Buckets too large for shared memory fall back to one thread per
+// row over global memory.
 template <int MODE, typename PT>
-__global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, const uint4 *__restrict__ medium,
-                                                    const unsigned long long *__restrict__ nmedium, uint32_t gshift,
-                                                    uint32_t nbits, uint32_t *__restrict__ gcnt,
+__global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, MedLists ml, bool huge, uint32_t mcap,
+                                                    uint32_t gshift, uint32_t nbits, uint32_t *__restrict__ gcnt,
                                                     const uint64_t *__restrict__ goff, uint32_t *__restrict__ gcur,
                                                     PT *__restrict__ ent, GroupRange gr,
                                                     RegionSink rs = RegionSink{}) {
-    __shared__ uint32_t s_id[kMedCap], s_lab[kMedCap];
+    extern __shared__ uint32_t med_dyn[];
+    uint32_t *s_id = med_dyn, *s_lab = med_dyn + mcap;
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t s_next, s_mixed;
-    const uint64_t n = *nmedium;
+    __shared__ unsigned long long s_bi;
+    const uint64_t nf = huge ? *ml.nhuge : *ml.nfront, n = huge ? nf : nf + *ml.nback;
+    unsigned long long *next = huge ? ml.next_h : ml.next;
     const uint32_t lmask = (1u << gshift) - 1, lane = threadIdx.x & 31;
-    for (uint64_t bi = blockIdx.x; bi < n; bi += gridDim.x) {
-        const uint4 e = medium[bi];
+    for (;;) {
+        // every thread has read the previous s_bi: the body ends with a barrier
+        if (threadIdx.x == 0) s_bi = atomicAdd(next, 1ull);
+        __syncthreads();
+        const uint64_t bi = s_bi;
+        if (bi >= n) break;  // block-uniform
+        const uint4 e = huge ? ml.huge[bi] : ml.cta_at(bi, nf);
         const uint32_t *s = a.sid + (uint64_t)e.x * a.N;
-        if (e.w > kMedCap) {  // block-uniform: fallback over global memory
+        if (e.w > mcap) {  // block-uniform: fallback over global memory
             for (uint32_t x = e.y + threadIdx.x; x < e.z; x += blockDim.x) {
                 const uint32_t i = s[x];
                 if (a.drop[i] || (MODE == 1 && !gr.has(i >> gshift))) continue;
@@ -865,13 +936,13 @@ __global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, const uint4 *__r
             }
             uint32_t tot;
             const uint32_t pos = block_excl_scan(live, wsum, &tot);
-            if (live && nl + pos < kMedCap) {
+            if (live && nl + pos < mcap) {
                 s_id[nl + pos] = id;
                 s_lab[nl + pos] = a.label ? __ldg(a.label + id) : kNone;
             }
             nl += tot;
         }
-        nl = min(nl, kMedCap);
+        nl = min(nl, mcap);
         __syncthreads();
         for (uint32_t x = threadIdx.x; x < nl; x += blockDim.x)
             if (s_lab[x] == kNone || s_lab[x] != s_lab[0]) s_mixed = 1;
@@ -946,6 +1017,139 @@ __global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, const uint4 *__r
             }
         }
         __syncthreads();
+    }
+}
+
+// One warp per bucket of at most kWarpMed entries: up to four entries a lane,
+// live members compacted into the warp's shared-memory slice in id order.
+// Each row's partners past the near-time exclusion are one range [y0, nl)
+// (binary search); the rows' slots are reserved lane by lane, then the
+// warp writes the bucket's pairs of rows outside dense groups as one
+// flattened sequence (pair k -> its row by a search over the rows' prefix
+// counts), consecutive stores within a row.  Rows of dense-group members
+// skip their own group's partners with one ballot per 32 partners.
+struct MedWarpSmem {
+    uint32_t id[kWarpMed], lab[kWarpMed], pre[kWarpMed], y0[kWarpMed];
+    unsigned long long base[kWarpMed];
+};
+
+template <int MODE, typename PT>
+__global__ void __launch_bounds__(256) k_medium_warp(EnumArgs a, MedLists ml, uint32_t gshift, uint32_t nbits,
+                                                     uint32_t *__restrict__ gcnt, const uint64_t *__restrict__ goff,
+                                                     uint32_t *__restrict__ gcur, PT *__restrict__ ent,
+                                                     GroupRange gr, RegionSink rs = RegionSink{}) {
+    __shared__ MedWarpSmem msm[8];
+    MedWarpSmem &W = msm[threadIdx.x / 32];
+    const uint32_t lane = threadIdx.x & 31, lt = (1u << lane) - 1, lmask = (1u << gshift) - 1;
+    const uint64_t n = *ml.nwarp, nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    for (uint64_t bi = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; bi < n; bi += nwarps) {
+        const uint4 e = ml.warp[bi];
+        const uint32_t *s = a.sid + (uint64_t)e.x * a.N;
+        const uint32_t raw = e.z - e.y;
+        uint32_t id[4], lab[4];
+        bool live[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) id[u] = u * 32 + lane < raw ? __ldg(s + e.y + u * 32 + lane) : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; u++) live[u] = u * 32 + lane < raw && !a.drop[id[u]];
+#pragma unroll
+        for (int u = 0; u < 4; u++) lab[u] = live[u] && a.label ? __ldg(a.label + id[u]) : kNone;
+        __syncwarp();  // the previous bucket's reads of W are done
+        uint32_t nl = 0;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t m = __ballot_sync(~0u, live[u]);
+            if (live[u]) {
+                const uint32_t pos = nl + __popc(m & lt);
+                W.id[pos] = id[u];
+                W.lab[pos] = lab[u];
+            }
+            nl += __popc(m);
+        }
+        __syncwarp();
+        if (nl < 2) continue;  // warp-uniform
+        const uint32_t l0 = W.lab[0];
+        bool mixed = false;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t x = u * 32 + lane;
+            if (x < nl) mixed |= W.lab[x] == kNone || W.lab[x] != l0;
+        }
+        if (!__any_sync(~0u, mixed)) continue;  // one dense group: no sparse pairs
+        uint32_t P = 0;  // pairs of rows outside dense groups, in row order
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t x = u * 32 + lane;
+            uint32_t c = 0, y0 = nl, i = 0, li = kNone;
+            if (x + 1 < nl) {
+                i = W.id[x];
+                li = W.lab[x];
+                if (MODE != 1 || gr.has(i >> gshift)) {
+                    const uint64_t lim = (uint64_t)i + a.excl;
+                    uint32_t lo = x + 1, hi = nl;
+                    while (lo < hi) {
+                        const uint32_t m = (lo + hi) >> 1;
+                        if (W.id[m] <= lim) lo = m + 1;
+                        else hi = m;
+                    }
+                    y0 = lo;
+                    c = nl - y0;
+                    if (li != kNone)
+                        for (uint32_t y = y0; y < nl; y++) c -= W.lab[y] == li;
+                }
+            }
+            const uint32_t g = i >> gshift;
+            if (MODE == 0) {
+                if (c) atomicAdd(gcnt + g, c);
+                continue;
+            }
+            unsigned long long b = 0;
+            if (c) b = MODE == 2 ? atomicAdd(gcur + g, c) : goff[g] - gr.ebase + atomicAdd(gcur + g, c);
+            const uint32_t cu = li == kNone ? c : 0u;
+            uint32_t inc = cu;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(~0u, inc, o);
+                if ((int)lane >= o) inc += y;
+            }
+            W.pre[x] = P + inc - cu;
+            W.y0[x] = y0;
+            W.base[x] = b;
+            P += __shfl_sync(~0u, inc, 31);
+            // rows of dense-group members: partners of other groups only
+            for (uint32_t todo = __ballot_sync(~0u, li != kNone && c != 0); todo; todo &= todo - 1) {
+                const int r = __ffs(todo) - 1;
+                const uint32_t ri = __shfl_sync(~0u, i, r), rli = __shfl_sync(~0u, li, r);
+                const uint32_t ry0 = __shfl_sync(~0u, y0, r);
+                unsigned long long o = __shfl_sync(~0u, b, r);
+                for (uint32_t yb = ry0; yb < nl; yb += 32) {
+                    const uint32_t y = yb + lane;
+                    const bool keep = y < nl && W.lab[y] != rli;
+                    const uint32_t m = __ballot_sync(~0u, keep);
+                    if (keep) {
+                        const PT ev = pack_entry<PT>(ri & lmask, W.id[y], nbits);
+                        const unsigned long long slot = o + __popc(m & lt);
+                        if (MODE == 2) rs.put(ri >> gshift, slot, (uint32_t)ev);
+                        else ent[slot] = ev;
+                    }
+                    o += __popc(m);
+                }
+            }
+        }
+        if (MODE == 0) continue;
+        __syncwarp();
+        // pair k: the last row x < nl - 1 with pre[x] <= k (rows without
+        // pairs share their successor's prefix, so x has pairs left)
+        for (uint32_t k = lane; k < P; k += 32) {
+            uint32_t x = 0;
+#pragma unroll
+            for (uint32_t step = kWarpMed / 2; step; step >>= 1)
+                if (x + step + 1 < nl && W.pre[x + step] <= k) x += step;
+            const uint32_t d = k - W.pre[x], i = W.id[x];
+            const PT ev = pack_entry<PT>(i & lmask, W.id[W.y0[x] + d], nbits);
+            if (MODE == 2) rs.put(i >> gshift, W.base[x] + d, (uint32_t)ev);
+            else ent[W.base[x] + d] = ev;
+        }
     }
 }
 
@@ -2304,9 +2508,42 @@ __global__ void k_part_cuts(const uint64_t *__restrict__ goff, uint64_t ng, uint
     cut[2 * q + 1] = goff[g];
 }
 
+// The medium-bucket writers of one pass: the warp kernel over the small
+// buckets, then the CTA kernel over the rest (persistent grids: every
+// resident CTA takes work until the lists are done).
+template <int MODE, typename PT>
+static void medium_launch(fast_ctx *c, const EnumArgs &ea, const MedLists &ml, uint32_t large_min, uint32_t gshift,
+                          uint32_t nbits, uint32_t *gcnt, const uint64_t *goff, uint32_t *gcur, PT *ent,
+                          GroupRange gr, RegionSink rs, cudaStream_t s) {
+    static int occ_w = 0, occ_c = 0;
+    const size_t csm = (size_t)2 * kMedCap * 4;
+    cudaFuncSetAttribute(k_medium_grp<MODE, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(2 * kMedHugeCap * 4));
+    if (!occ_w) {  // occupancies are the same on every device of this architecture
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_medium_warp<MODE, PT>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, k_medium_grp<MODE, PT>, 256, csm);
+        occ_w = std::max(occ_w, 1);
+        occ_c = std::max(occ_c, 1);
+    }
+    k_medium_warp<MODE, PT><<<c->num_sms * occ_w, 256, 0, s>>>(ea, ml, gshift, nbits, gcnt, goff, gcur, ent, gr,
+                                                                 rs), FAST_LAUNCHED(c);
+    if (large_min > kMedCap + 1) {  // live members of a medium bucket stay below large_min
+        const uint32_t hcap = std::min(large_min, kMedHugeCap);
+        const size_t hsm = (size_t)2 * hcap * 4;
+        int occ_h = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_h, k_medium_grp<MODE, PT>, 256, hsm);
+        cudaMemsetAsync(ml.next_h, 0, 8, s);
+        k_medium_grp<MODE, PT><<<c->num_sms * std::max(occ_h, 1), 256, hsm, s>>>(
+            ea, ml, true, hcap, gshift, nbits, gcnt, goff, gcur, ent, gr, rs), FAST_LAUNCHED(c);
+    }
+    cudaMemsetAsync(ml.next, 0, 8, s);
+    k_medium_grp<MODE, PT><<<c->num_sms * occ_c, 256, csm, s>>>(ea, ml, false, kMedCap, gshift, nbits, gcnt, goff,
+                                                                  gcur, ent, gr, rs), FAST_LAUNCHED(c);
+}
+
 template <typename PT, typename Alloc>
 static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *medium, uint64_t nmedium,
-                                 uint32_t gshift, uint32_t nbits, uint32_t *sp_cnt, uint64_t *sp_start,
+                                 uint32_t large_min, uint32_t gshift, uint32_t nbits, uint32_t *sp_cnt, uint64_t *sp_start,
                                  uint32_t **sp_j_out, uint8_t **sp_v_out, uint64_t *sp_n_out, uint2 *long_rows,
                                  uint64_t &S_out, Alloc &alloc, cudaStream_t s, uint64_t S_ub) {
     const fast_params &p = c->p;
@@ -2347,7 +2584,19 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     const uint32_t tpw = tiles_per_warp(c, N, p.b);
     const uint64_t nwarps = (ntiles + tpw - 1) / tpw;
     const dim3 eg((unsigned)std::max<uint64_t>(1, (nwarps + 7) / 8), p.b);
-    const unsigned mg = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(nmedium, c->num_sms * 8));
+    // medium buckets: the warp list and the CTA list (largest first)
+    uint4 *med_w = nullptr, *med_c = nullptr, *med_h = nullptr;
+    if ((st = lalloc(&med_w, nmedium)) || (st = lalloc(&med_c, nmedium)) ||
+        (large_min > kMedCap + 1 && (st = lalloc(&med_h, nmedium))))
+        return st;
+    cudaMemsetAsync(scal + Scal::NMEDW, 0, 8 * 4, s);
+    if (nmedium)
+        k_med_split<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(nmedium, 256), c->num_sms * 8)),
+                      256, 0, s>>>(medium, scal + Scal::NMEDIUM, med_w, scal + Scal::NMEDW, med_c, nmedium,
+                                   scal + Scal::NMEDF, scal + Scal::NMEDB, med_h ? med_h : med_c,
+                                   scal + Scal::NMEDH), FAST_LAUNCHED(c);
+    const MedLists ml{med_w, med_c, med_h, scal + Scal::NMEDW, scal + Scal::NMEDF, scal + Scal::NMEDB,
+                      scal + Scal::NMEDH, nmedium, scal + Scal::MEDNEXT, scal + Scal::MEDNEXTH};
     cudaMemsetAsync(scal + Scal::NSMALLEMIT, 0, 8, s);
     const GroupRange all{0, ng, 0};
     uint64_t S = 0;
@@ -2382,8 +2631,7 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
                                                   scal + Scal::NSMALLEMIT, all, rs), FAST_LAUNCHED(c);
             stage_mark(c, 12, s);
             if (nmedium)
-                k_medium_grp<2, PT><<<mg, 256, 0, s>>>(e1, medium, scal + Scal::NMEDIUM, gshift, nbits, nullptr,
-                                                       nullptr, gcur, nullptr, all, rs), FAST_LAUNCHED(c);
+                medium_launch<2, PT>(c, e1, ml, large_min, gshift, nbits, nullptr, nullptr, gcur, nullptr, all, rs, s);
             stage_mark(c, 19, s);
             if ((st = scan_excl(c, gcur, goff, ng, 1, goff + ng, s))) return st;
             cudaMemcpyAsync(&S, goff + ng, 8, cudaMemcpyDeviceToHost, s);
@@ -2427,8 +2675,7 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
                                               scal + Scal::NSMALLEMIT, all), FAST_LAUNCHED(c);
         stage_mark(c, 17, s);
         if (nmedium)
-            k_medium_grp<0, PT><<<mg, 256, 0, s>>>(ea, medium, scal + Scal::NMEDIUM, gshift, nbits, gcnt, nullptr,
-                                                   nullptr, nullptr, all), FAST_LAUNCHED(c);
+            medium_launch<0, PT>(c, ea, ml, large_min, gshift, nbits, gcnt, nullptr, nullptr, nullptr, all, RegionSink{}, s);
         stage_mark(c, 18, s);
         if ((st = scan_excl(c, gcnt, goff, ng, 1, goff + ng, s))) return st;
         cudaMemcpyAsync(&S, goff + ng, 8, cudaMemcpyDeviceToHost, s);
@@ -2561,8 +2808,7 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
                     FAST_LAUNCHED(c);
                 stage_mark(c, 12, s);
                 if (nmedium)
-                    k_medium_grp<1, PT><<<mg, 256, 0, s>>>(ea, medium, scal + Scal::NMEDIUM, gshift, nbits, nullptr,
-                                                           goff, gcur, ent, gr), FAST_LAUNCHED(c);
+                    medium_launch<1, PT>(c, ea, ml, large_min, gshift, nbits, nullptr, goff, gcur, ent, gr, RegionSink{}, s);
                 stage_mark(c, 11, s);
             }
             // vote the range
@@ -2933,11 +3179,12 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
         // 32-bit entries while entry + 1 cannot wrap to the empty key
         uint64_t sp_n = 0;
         const fast_status r = gshift + nbits < 32
-                                  ? sparse_groups<uint32_t>(c, ea, medium, nmedium, gshift, nbits, sp_cnt, sp_start,
-                                                            &sp_j, &sp_v, &sp_n, long_rows, S, alloc, s, S_ub)
-                                  : sparse_groups<unsigned long long>(c, ea, medium, nmedium, gshift, nbits, sp_cnt,
-                                                                      sp_start, &sp_j, &sp_v, &sp_n, long_rows, S,
-                                                                      alloc, s, S_ub);
+                                  ? sparse_groups<uint32_t>(c, ea, medium, nmedium, large_min, gshift, nbits, sp_cnt,
+                                                            sp_start, &sp_j, &sp_v, &sp_n, long_rows, S, alloc, s,
+                                                            S_ub)
+                                  : sparse_groups<unsigned long long>(c, ea, medium, nmedium, large_min, gshift, nbits,
+                                                                      sp_cnt, sp_start, &sp_j, &sp_v, &sp_n, long_rows,
+                                                                      S, alloc, s, S_ub);
         if (r) return fail(r);
         owned.push_back({(void *)sp_j, sp_n * 4});  // freed with the search's other buffers
         owned.push_back({(void *)sp_v, sp_n});

@@ -34,21 +34,34 @@ __device__ __forceinline__ uint32_t digit_of(KT k, uint32_t shift) {
     return (uint32_t)(k >> shift) & (kRadix - 1);
 }
 
-template <typename KT, bool STD = false>
+// Segment y of a sort: the y-th of nseg rows of `len` keys or, with several
+// stations, row y / nst's keys of station y % nst: positions soff[x] ..
+// soff[x + 1] of the row, whose generated ids start at soff[x].  Sorting
+// every station's part of a table on its own leaves the table ordered by
+// (station, key, id).
+struct Seg {
+    uint64_t base, n, id0;
+};
+__device__ __forceinline__ Seg seg_of(uint32_t y, uint64_t len, const Stations &S) {
+    if (S.nst <= 1) return Seg{(uint64_t)y * len, len, 0};
+    const uint32_t t = y / S.nst, x = y % S.nst;
+    const uint64_t a = S.soff[x];
+    return Seg{(uint64_t)t * len + a, S.soff[x + 1] - a, a};
+}
+
+template <typename KT>
 __global__ void __launch_bounds__(kThreads) k_hist(const KT *__restrict__ keys, uint64_t len, uint32_t nchunks,
                                                    uint32_t shift, uint32_t *__restrict__ counts,
-                                                   const uint32_t *__restrict__ vals = nullptr,
                                                    Stations S = Stations{nullptr, 1}) {
     __shared__ uint32_t h[kWarps][kRadix];
     const uint32_t seg = blockIdx.y, chunk = blockIdx.x;
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&h[0][0])[i] = 0;
     __syncthreads();
-    const KT *k = keys + (uint64_t)seg * len;
-    const uint64_t lo = (uint64_t)chunk * kChunk, hi = std::min<uint64_t>(lo + kChunk, len);
+    const Seg g = seg_of(seg, len, S);
+    const KT *k = keys + g.base;
+    const uint64_t lo = (uint64_t)chunk * kChunk, hi = std::min<uint64_t>(lo + kChunk, g.n);
     const int warp = threadIdx.x >> 5;
-    const uint32_t *vv = STD ? vals + (uint64_t)seg * len : nullptr;
-    for (uint64_t e = lo + threadIdx.x; e < hi; e += kThreads)
-        atomicAdd(&h[warp][STD ? station_of(S, __ldcs(vv + e)) : digit_of(__ldcs(k + e), shift)], 1u);
+    for (uint64_t e = lo + threadIdx.x; e < hi; e += kThreads) atomicAdd(&h[warp][digit_of(__ldcs(k + e), shift)], 1u);
     __syncthreads();
     uint32_t d = threadIdx.x, tot = 0;
 #pragma unroll
@@ -139,7 +152,7 @@ struct Staging {
 // Measured on GB300 this beats eight warp ballots per slot (the ballot pipe
 // is the narrow one) and the match instruction (narrower still).
 // The next sub-tile's loads are issued before the current one is ranked.
-template <typename KT, bool HAS_VAL, bool IOTA, bool STD = false>
+template <typename KT, bool HAS_VAL, bool IOTA>
 __global__ void __launch_bounds__(kThreads, 3) k_scatter(const KT *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                       KT *__restrict__ kout, uint32_t *__restrict__ vout, uint64_t len,
                                                       uint32_t nchunks, uint32_t shift,
@@ -157,12 +170,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_scatter(const KT *__restrict__ 
     const uint32_t seg = blockIdx.y, chunk = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt_mask = (1u << lane) - 1;
-    const KT *ki = kin + (uint64_t)seg * len;
-    const uint32_t *vi = HAS_VAL && !IOTA ? vin + (uint64_t)seg * len : nullptr;
-    KT *ko = kout + (uint64_t)seg * len;
-    uint32_t *vo = HAS_VAL ? vout + (uint64_t)seg * len : nullptr;
+    const Seg g = seg_of(seg, len, S);
     const uint64_t cbase = (uint64_t)chunk * kChunk;
-    const uint32_t cvalid = (uint32_t)std::min<uint64_t>(kChunk, len - cbase);
+    if (cbase >= g.n) return;  // block-uniform: a station shorter than the longest
+    const KT *ki = kin + g.base;
+    const uint32_t *vi = HAS_VAL && !IOTA ? vin + g.base : nullptr;
+    KT *ko = kout + g.base;
+    uint32_t *vo = HAS_VAL ? vout + g.base : nullptr;
+    const uint32_t cvalid = (uint32_t)std::min<uint64_t>(kChunk, g.n - cbase);
 #pragma unroll
     for (int w = 0; w < kWarps; w++) wmask[w][threadIdx.x] = 0;
     {   // the chunk's digit starts: exclusive scan of its counts over the 256 digits
@@ -190,17 +205,17 @@ __global__ void __launch_bounds__(kThreads, 3) k_scatter(const KT *__restrict__ 
 #pragma unroll
         for (int j = 0; j < kItems; j++) {
             const uint64_t e = sb + warp * (kItems * 32) + j * 32 + lane;
-            const bool valid = e < len;
+            const bool valid = e < g.n;
             // streaming loads (evict-first): the L2 keeps the write frontier of the digit runs
             k[j] = valid ? __ldcs(ki + e) : (KT)0;
-            if (HAS_VAL) v[j] = valid ? (IOTA ? (uint32_t)e : __ldcs(vi + e)) : 0u;
+            if (HAS_VAL) v[j] = valid ? (IOTA ? (uint32_t)(g.id0 + e) : __ldcs(vi + e)) : 0u;
         }
     };
 #pragma unroll
     for (int sub = 0; sub < kSubPerChunk; sub++) {
         const uint64_t sbase = cbase + (uint64_t)sub * kSub;
-        if (sbase >= len) break;  // block-uniform
-        const uint32_t nvalid = (uint32_t)std::min<uint64_t>(kSub, len - sbase);
+        if (sbase >= g.n) break;  // block-uniform
+        const uint32_t nvalid = (uint32_t)std::min<uint64_t>(kSub, g.n - sbase);
 #pragma unroll
         for (int w = 0; w < kWarps; w++) wpos[w][threadIdx.x] = 0;
         if (!PF || sub == 0) load(sbase, key, val);
@@ -214,8 +229,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_scatter(const KT *__restrict__ 
             const bool valid = e < nvalid;
             uint32_t dig = 0;
             if (valid) {
-                if constexpr (STD) dig = station_of(S, val[j]);
-                else dig = (uint32_t)(key[j] >> shift) & (kRadix - 1);
+                dig = digit_of(key[j], shift);
                 atomicOr(&wmask[warp][dig], 1u << lane);
             }
             __syncwarp();
@@ -247,9 +261,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_scatter(const KT *__restrict__ 
         for (int j = 0; j < kItems; j++) {
             const uint32_t e = warp * (kItems * 32) + j * 32 + lane;
             if (e < nvalid) {
-                uint32_t dig;
-                if constexpr (STD) dig = station_of(S, val[j]);
-                else dig = (uint32_t)(key[j] >> shift) & (kRadix - 1);
+                const uint32_t dig = digit_of(key[j], shift);
                 stage.put(wpos[warp][dig] + rnk[j], key[j], HAS_VAL ? val[j] : 0u);
             }
         }
@@ -266,10 +278,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_scatter(const KT *__restrict__ 
         KT k;
         uint32_t v;
         stage.get(i, k, v);
-        uint32_t d;
-        if constexpr (STD) d = station_of(S, v);
-        else d = (uint32_t)(k >> shift) & (kRadix - 1);
-        const uint64_t o = delta[d] + i;
+        const uint64_t o = delta[digit_of(k, shift)] + i;
         ko[o] = k;
         if (HAS_VAL) vo[o] = v;
     }
@@ -288,8 +297,6 @@ void scatter_attrs() {
                          (int)scatter_smem<uint32_t, true>());
     cudaFuncSetAttribute(k_scatter<uint32_t, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)scatter_smem<uint32_t, true>());
-    cudaFuncSetAttribute(k_scatter<uint32_t, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)scatter_smem<uint32_t, true>());
     cudaFuncSetAttribute(k_scatter<uint64_t, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)scatter_smem<uint64_t, false>());
     cudaFuncSetAttribute(k_scatter<uint64_t, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -302,7 +309,8 @@ void scatter_attrs() {
 template <typename KT, bool HAS_VAL>
 fast_status sort_impl(fast_ctx *c, uint32_t nseg, uint64_t len, const KT *keys_in, const uint32_t *vals_in,
                       KT *ka, uint32_t *va, KT *kb, uint32_t *vb, uint32_t bit0, uint32_t bit1, KT **kout,
-                      uint32_t **vout, cudaStream_t s, uint32_t *passes_out) {
+                      uint32_t **vout, cudaStream_t s, uint32_t *passes_out, Stations S = Stations{nullptr, 1},
+                      uint64_t seg_max = 0) {
     const uint32_t npass = (bit1 - bit0 + 7) / 8;
     if (passes_out) *passes_out = npass;
     if (len == 0 || nseg == 0 || npass == 0) {
@@ -310,7 +318,7 @@ fast_status sort_impl(fast_ctx *c, uint32_t nseg, uint64_t len, const KT *keys_i
         if (vout) *vout = const_cast<uint32_t *>(vals_in);
         return FAST_OK;
     }
-    const uint64_t nch64 = (len + kChunk - 1) / kChunk;
+    const uint64_t nch64 = ((S.nst > 1 ? seg_max : len) + kChunk - 1) / kChunk;
     if (nch64 > 0x7fffffffull) return set_error(c, FAST_EINVAL, "sort: segment too long");
     const uint32_t nchunks = (uint32_t)nch64;
     const size_t entries = (size_t)nseg * kRadix * nchunks;
@@ -330,17 +338,17 @@ fast_status sort_impl(fast_ctx *c, uint32_t nseg, uint64_t len, const KT *keys_i
         const uint32_t shift = bit0 + 8 * pass;
         KT *dk = (pass & 1) ? kb : ka;
         uint32_t *dv = (pass & 1) ? vb : va;
-        k_hist<KT><<<grid, kThreads, 0, s>>>(src_k, len, nchunks, shift, counts), FAST_LAUNCHED(c);
+        k_hist<KT><<<grid, kThreads, 0, s>>>(src_k, len, nchunks, shift, counts, S), FAST_LAUNCHED(c);
         if ((st = scan_excl(c, counts, offs, (uint64_t)kRadix * nchunks, nseg, nullptr, s))) break;
         if (HAS_VAL && pass == 0 && src_v == nullptr)
             k_scatter<KT, true, true><<<grid, kThreads, scatter_smem<KT, true>(), s>>>(
-                src_k, nullptr, dk, dv, len, nchunks, shift, counts, offs), FAST_LAUNCHED(c);
+                src_k, nullptr, dk, dv, len, nchunks, shift, counts, offs, S), FAST_LAUNCHED(c);
         else if (HAS_VAL)
             k_scatter<KT, true, false><<<grid, kThreads, scatter_smem<KT, true>(), s>>>(
-                src_k, src_v, dk, dv, len, nchunks, shift, counts, offs), FAST_LAUNCHED(c);
+                src_k, src_v, dk, dv, len, nchunks, shift, counts, offs, S), FAST_LAUNCHED(c);
         else
             k_scatter<KT, false, false><<<grid, kThreads, scatter_smem<KT, false>(), s>>>(
-                src_k, nullptr, dk, nullptr, len, nchunks, shift, counts, offs), FAST_LAUNCHED(c);
+                src_k, nullptr, dk, nullptr, len, nchunks, shift, counts, offs, S), FAST_LAUNCHED(c);
         src_k = dk;
         src_v = dv;
     }
@@ -358,36 +366,11 @@ fast_status sort_impl(fast_ctx *c, uint32_t nseg, uint64_t len, const KT *keys_i
 
 fast_status sort_u32(fast_ctx *c, uint32_t nseg, uint64_t len, const uint32_t *keys_in, const uint32_t *vals_in,
                      uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, uint32_t bit0,
-                     uint32_t bit1, uint32_t **keys_out, uint32_t **vals_out, cudaStream_t s, uint32_t *passes) {
-    return sort_impl<uint32_t, true>(c, nseg, len, keys_in, vals_in, keys_a, vals_a, keys_b, vals_b, bit0, bit1,
-                                     keys_out, vals_out, s, passes);
-}
-
-fast_status sort_station_pass(fast_ctx *c, uint32_t nseg, uint64_t len, const uint32_t *keys_in, const uint32_t *vals_in,
-                              uint32_t *keys_out, uint32_t *vals_out, Stations S, cudaStream_t s) {
-    if (len == 0 || nseg == 0) return FAST_OK;
-    const uint32_t nchunks = (uint32_t)((len + kChunk - 1) / kChunk);
-    const size_t entries = (size_t)nseg * kRadix * nchunks;
-    uint32_t *counts = nullptr;
-    uint64_t *offs = nullptr;
-    fast_status st;
-    if ((st = dalloc_t(c, &counts, entries, s))) return st;
-    if ((st = dalloc_t(c, &offs, entries, s))) {
-        dfree(c, counts, entries * 4, s);
-        return st;
-    }
-    const dim3 grid(nchunks, nseg);
-    scatter_attrs();
-    k_hist<uint32_t, true><<<grid, kThreads, 0, s>>>(keys_in, len, nchunks, 0, counts, vals_in, S), FAST_LAUNCHED(c);
-    st = scan_excl(c, counts, offs, (uint64_t)kRadix * nchunks, nseg, nullptr, s);
-    if (!st)
-        k_scatter<uint32_t, true, false, true><<<grid, kThreads, scatter_smem<uint32_t, true>(), s>>>(
-            keys_in, vals_in, keys_out, vals_out, len, nchunks, 0, counts, offs, S), FAST_LAUNCHED(c);
-    dfree(c, counts, entries * 4, s);
-    dfree(c, offs, entries * 8, s);
-    if (st) return st;
-    cudaError_t e = cudaGetLastError();
-    return e ? cuda_fail(c, e, "station pass") : FAST_OK;
+                     uint32_t bit1, uint32_t **keys_out, uint32_t **vals_out, cudaStream_t s, uint32_t *passes,
+                     Stations S, uint64_t seg_max) {
+    if (S.nst > 1 && (uint64_t)nseg * S.nst > 65535) return set_error(c, FAST_EINVAL, "sort: too many segments");
+    return sort_impl<uint32_t, true>(c, S.nst > 1 ? nseg * S.nst : nseg, len, keys_in, vals_in, keys_a, vals_a,
+                                     keys_b, vals_b, bit0, bit1, keys_out, vals_out, s, passes, S, seg_max);
 }
 
 fast_status sort_u64(fast_ctx *c, uint64_t len, uint64_t *keys_a, uint64_t *keys_b, uint32_t bit0, uint32_t bit1,

@@ -114,6 +114,10 @@ DETECT_CASES = [
     # imbalanced, co-occurring bits (§6.3): large background buckets
     ("c1", 30_000, dict(skew=0.6, corr=0.3), dict()),
     ("c1", 30_000, dict(skew=0.3, r=8, v=3), dict()),
+    # a 4 s source without the filter: sparse buckets of up to 4,437 live
+    # windows, more than the 4,096 a medium-bucket CTA holds by default
+    ("c1", 28_000, dict(occ_num=0, b=20, v=2, periods=(4,)), dict(large_min=10**9)),
+    ("c1", 28_000, dict(occ_num=0, b=20, v=2, periods=(4,)), dict(large_min=4500)),
 ]
 
 
