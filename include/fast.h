@@ -136,7 +136,12 @@ typedef struct {
     float ms_k_medium, ms_k_vote_block, ms_k_count_small, ms_k_count_medium;
     uint32_t dense_fallback;  /* 1 when the cluster-mask scratch did not fit and every
                                  dense group was voted by direct key comparison   */
-    uint32_t large_min;       /* the dense-group threshold the search used         */
+    uint32_t large_min;       /* the dense-group threshold the search used (a batch
+                                 with the automatic threshold: its largest station
+                                 threshold)                                         */
+    uint32_t group_shift;     /* sparse row groups hold 2^group_shift rows           */
+    uint32_t region_slots;    /* single-pass slots per row group (0: pairs counted
+                                 first, then written)                               */
 } fast_stats;
 
 /*

@@ -45,7 +45,8 @@ class fast_stats(ctypes.Structure):
                 ("n_overflow", ctypes.c_uint64), ("max_group", ctypes.c_uint64)] + \
                [(n, ctypes.c_float) for n in ("ms_k_medium", "ms_k_vote_block", "ms_k_count_small",
                                               "ms_k_count_medium")] + \
-               [("dense_fallback", ctypes.c_uint32), ("large_min", ctypes.c_uint32)]
+               [("dense_fallback", ctypes.c_uint32), ("large_min", ctypes.c_uint32),
+                ("group_shift", ctypes.c_uint32), ("region_slots", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -243,14 +243,18 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *wsum, 
 
 // Classifies big buckets by live size: >= large_min -> large list (dense
 // path), otherwise medium list; counts medium pairs per query partition
-// (each live member i pairs with the live members after it).
+// (each live member i pairs with the live members after it).  With lm_st,
+// a batch's station x has threshold lm_st[x] and its largest live bucket
+// goes to lmax_st[x].
 __global__ void __launch_bounds__(256) k_big_classify(EnumArgs a, uint4 *__restrict__ big,
                                                       const unsigned long long *__restrict__ nbig, uint64_t big_cap,
                                                       uint32_t large_min, uint4 *__restrict__ large,
                                                       unsigned long long *__restrict__ nlarge, uint4 *__restrict__ medium,
                                                       unsigned long long *__restrict__ nmedium,
                                                       unsigned long long *__restrict__ part_cnt,
-                                                      unsigned long long *__restrict__ lmax = nullptr) {
+                                                      unsigned long long *__restrict__ lmax = nullptr,
+                                                      const uint32_t *__restrict__ lm_st = nullptr,
+                                                      unsigned long long *__restrict__ lmax_st = nullptr) {
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t s_live;
     __shared__ unsigned long long s_cnt[64];
@@ -275,14 +279,20 @@ __global__ void __launch_bounds__(256) k_big_classify(EnumArgs a, uint4 *__restr
             nl = s_live;
             if (threadIdx.x == 0) big[bi].w = nl + 1;
         }
+        uint32_t large_min_b = large_min;
+        if (lm_st) {  // block-uniform
+            const uint32_t x = station_of(a.st, e.y);
+            large_min_b = lm_st[x];
+            if (threadIdx.x == 0 && lmax_st) atomicMax(lmax_st + x, (unsigned long long)nl);
+        }
         if (threadIdx.x == 0 && lmax) atomicMax(lmax, (unsigned long long)nl);
         if (threadIdx.x == 0 && nl >= 2) {
-            if (nl >= large_min) large[atomicAdd(nlarge, 1ull)] = make_uint4(e.x, e.y, e.z, nl);
+            if (nl >= large_min_b) large[atomicAdd(nlarge, 1ull)] = make_uint4(e.x, e.y, e.z, nl);
             else medium[atomicAdd(nmedium, 1ull)] = make_uint4(e.x, e.y, e.z, nl);
         }
         if (a.nparts == 1) {  // one partition: the bucket's pairs are C(nl, 2)
-            if (threadIdx.x == 0 && nl >= 2 && nl < large_min) s_cnt[0] += (unsigned long long)nl * (nl - 1) / 2;
-        } else if (nl >= 2 && nl < large_min) {
+            if (threadIdx.x == 0 && nl >= 2 && nl < large_min_b) s_cnt[0] += (unsigned long long)nl * (nl - 1) / 2;
+        } else if (nl >= 2 && nl < large_min_b) {
             uint32_t rank0 = 0;
             for (uint32_t q0 = e.y; q0 < e.z; q0 += blockDim.x) {
                 const uint32_t q = q0 + threadIdx.x;
@@ -2543,7 +2553,7 @@ static void medium_launch(fast_ctx *c, const EnumArgs &ea, const MedLists &ml, u
 
 template <typename PT, typename Alloc>
 static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *medium, uint64_t nmedium,
-                                 uint32_t large_min, uint32_t gshift, uint32_t nbits, uint32_t *sp_cnt, uint64_t *sp_start,
+                                 uint32_t large_min, double dens, uint32_t gshift, uint32_t nbits, uint32_t *sp_cnt, uint64_t *sp_start,
                                  uint32_t **sp_j_out, uint8_t **sp_v_out, uint64_t *sp_n_out, uint2 *long_rows,
                                  uint64_t &S_out, Alloc &alloc, cudaStream_t s, uint64_t S_ub) {
     const fast_params &p = c->p;
@@ -2608,16 +2618,24 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     uint32_t rcap = 0;
     const unsigned long long *ovf_sorted = nullptr;
     uint64_t *ostart = nullptr;
+    c->stats.group_shift = gshift;
     if (sizeof(PT) == 4 && p.query_part <= 1 && c->single_pass) {
-        // about twice the expected group size, plus one 128-byte line so that
-        // region starts do not all fall on the same DRAM channels
-        uint32_t cap = 256;
-        while ((uint64_t)cap < 2 * (S_ub / ng + 1) && cap < (1u << 16)) cap <<= 1;
-        cap += 32;
-        if (c->group_slots) cap = c->group_slots;
+        // 2.5, 2 or 1.75 times the expected group size of the densest
+        // station (`dens` times the mean; the most that fits) in whole
+        // 128-byte lines -- not the power of two above twice the mean, which
+        // jumps from 2x to 4x the mean as the mean crosses a power of two --
+        // plus one line so that region starts do not all fall on the same
+        // DRAM channels
         const uint64_t ovf_cap = c->group_slots ? S_ub + (1 << 20) : std::max<uint64_t>(1 << 20, S_ub / 8);
-        const uint64_t need = ng * cap * 4 + ovf_cap * 16;
         const uint64_t room = pair_room(c, vote_extra);
+        uint32_t cap = 0;
+        for (const uint64_t quarters : {10u, 8u, 7u}) {
+            const uint64_t want = ((uint64_t)(dens * quarters * (S_ub / ng + 1)) / 4 + 31) / 32 * 32;
+            cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(want, 256), 1u << 16) + 32;
+            if (c->group_slots) cap = c->group_slots;
+            if (ng * cap * 4 + ovf_cap * 16 <= room) break;
+        }
+        const uint64_t need = ng * cap * 4 + ovf_cap * 16;
         uint32_t *region = nullptr;
         unsigned long long *ovf = nullptr;
         if (need <= room && !(st = lalloc(&region, ng * cap)) && !(st = lalloc(&ovf, ovf_cap))) {
@@ -2644,6 +2662,7 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
             c->stats.n_overflow = novf;
             if (novf <= ovf_cap) {  // the vote reads the regions and the sorted overflow list in place
                 single = true;
+                c->stats.region_slots = cap;
                 ent = reinterpret_cast<PT *>(region);
                 rcap = cap;
                 if (novf) {
@@ -2921,8 +2940,25 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
     c->stats.n_long_rows = c->stats.n_huge_rows = c->stats.max_row = 0;
     c->stats.query_parts = 1;
     c->stats.dense_fallback = 0;
+    c->stats.group_shift = c->stats.region_slots = 0;
     uint32_t large_min = large_min_for(c, N);
     const unsigned blocksN = std::max(1u, std::min<unsigned>(ceil_div(N, 256), c->num_sms * 8));
+    // A batch with the automatic threshold: one threshold per station, from
+    // the station's own size and largest bucket (the batch's total would
+    // turn a station's dense buckets into medium ones).  large_min is then
+    // the largest of them.
+    const uint32_t nst = tb->nst;
+    const bool per_st = nst > 1 && !c->large_min;
+    std::vector<uint32_t> lm_h;
+    uint32_t *d_lm = nullptr;
+    unsigned long long *d_lmax = nullptr;
+    auto station_host = [&](uint64_t pos) {
+        return (uint32_t)(std::upper_bound(tb->soff.begin(), tb->soff.end(), pos) - tb->soff.begin() - 1);
+    };
+    auto upload_lm = [&]() {
+        cudaMemcpyAsync(d_lm, lm_h.data(), nst * 4, cudaMemcpyHostToDevice, s);
+        large_min = *std::max_element(lm_h.begin(), lm_h.end());
+    };
 
     // ---- big buckets
     stage_mark(c, 3, s);
@@ -2937,24 +2973,50 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
     const uint64_t nbig = c->h_scal[Scal::NBIG];
     if ((st = alloc(&large, nbig)) || (st = alloc(&medium, nbig))) return fail(st);
     const unsigned cg = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(nbig, c->num_sms * 8));
+    if (per_st) {
+        lm_h.resize(nst);
+        for (uint32_t x = 0; x < nst; x++) lm_h[x] = large_min_for(c, tb->soff[x + 1] - tb->soff[x]);
+        if ((st = alloc(&d_lm, nst)) || (st = alloc(&d_lmax, nst))) return fail(st);
+        upload_lm();
+        cudaMemsetAsync(d_lmax, 0, nst * 8, s);
+    }
     k_big_classify<<<cg, 256, 0, s>>>(ea, big, scal + Scal::NBIG, big_cap, large_min, large, scal + Scal::NLARGE,
-                                      medium, scal + Scal::NMEDIUM, scal + Scal::PART0, scal + Scal::LMAX),
+                                      medium, scal + Scal::NMEDIUM, scal + Scal::PART0, scal + Scal::LMAX, d_lm,
+                                      d_lmax),
         FAST_LAUNCHED(c);
     if ((st = read_scal(c, s, "bucket classify"))) return fail(st);
+    auto reclassify = [&]() {
+        cudaMemsetAsync(scal + Scal::NLARGE, 0, 8, s);
+        cudaMemsetAsync(scal + Scal::NMEDIUM, 0, 8, s);
+        cudaMemsetAsync(scal + Scal::PART0, 0, 8 * (kScal - Scal::PART0), s);
+        k_big_classify<<<cg, 256, 0, s>>>(ea, big, scal + Scal::NBIG, big_cap, large_min, large,
+                                          scal + Scal::NLARGE, medium, scal + Scal::NMEDIUM, scal + Scal::PART0,
+                                          nullptr, d_lm),
+            FAST_LAUNCHED(c);
+        return read_scal(c, s, "bucket classify");
+    };
     // Automatic threshold, second bound: a dense group pays when its buckets
     // are a sizeable part of the largest one.  Buckets far below it only chain
     // windows that rarely reach v votes into one group whose pairs are all
     // compared (measured: a 31,104,000-window station 4.3 s -> 1.6 s, the
     // 7,776,000-window one 75.1 -> 73.8 ms, with identical lists).
-    if (!c->large_min && c->h_scal[Scal::LMAX] / kLargeRel > large_min) {
+    if (per_st) {
+        std::vector<unsigned long long> lmx(nst);
+        cudaMemcpyAsync(lmx.data(), d_lmax, nst * 8, cudaMemcpyDeviceToHost, s);
+        if ((st = sync_check(c, s, "largest buckets"))) return fail(st);
+        bool raised = false;
+        for (uint32_t x = 0; x < nst; x++)
+            if (lmx[x] / kLargeRel > lm_h[x]) {
+                lm_h[x] = (uint32_t)(lmx[x] / kLargeRel);
+                raised = true;
+            }
+        if (raised) {
+            upload_lm();
+            if ((st = reclassify())) return fail(st);
+        }
+    } else if (!c->large_min && c->h_scal[Scal::LMAX] / kLargeRel > large_min) {
         large_min = (uint32_t)(c->h_scal[Scal::LMAX] / kLargeRel);
-        cudaMemsetAsync(scal + Scal::NLARGE, 0, 8, s);
-        cudaMemsetAsync(scal + Scal::NMEDIUM, 0, 8, s);
-        cudaMemsetAsync(scal + Scal::PART0, 0, 8 * (kScal - Scal::PART0), s);
-        k_big_classify<<<cg, 256, 0, s>>>(ea, big, scal + Scal::NBIG, big_cap, large_min, large,
-                                          scal + Scal::NLARGE, medium, scal + Scal::NMEDIUM, scal + Scal::PART0),
-            FAST_LAUNCHED(c);
-        if ((st = read_scal(c, s, "bucket classify"))) return fail(st);
+        if ((st = reclassify())) return fail(st);
     }
     uint64_t nlarge = c->h_scal[Scal::NLARGE], nmedium = c->h_scal[Scal::NMEDIUM];
 
@@ -3024,22 +3086,26 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
         cudaMemcpyAsync(hl.data(), large, nlarge * sizeof(uint4), cudaMemcpyDeviceToHost, s);
         if ((st = sync_check(c, s, "group members copy"))) return fail(st);
         if (c->large_min || round >= 8) break;
-        uint64_t gp = 0, lp = 0;  // member pairs of the groups, pairs of the large buckets
+        // member pairs of the groups, pairs of the large buckets (per station
+        // in a batch: groups never cross stations)
+        std::vector<uint64_t> gp(per_st ? nst : 1, 0), lp(per_st ? nst : 1, 0);
         for (uint64_t g0 = 0, g1; g0 < nm; g0 = g1) {
             for (g1 = g0 + 1; g1 < nm && (hm[g1] >> 32) == (hm[g0] >> 32); g1++) {
             }
-            gp += (g1 - g0) * (g1 - g0 - 1) / 2;
+            gp[per_st ? station_host((uint32_t)hm[g0]) : 0] += (g1 - g0) * (g1 - g0 - 1) / 2;
         }
-        for (const uint4 &e : hl) lp += (uint64_t)e.w * (e.w - 1) / 2;
-        if (gp <= lp) break;
-        large_min = large_min < (1u << 30) ? 2 * large_min : large_min + 1;  // and classify again
-        cudaMemsetAsync(scal + Scal::NLARGE, 0, 8, s);
-        cudaMemsetAsync(scal + Scal::NMEDIUM, 0, 8, s);
-        cudaMemsetAsync(scal + Scal::PART0, 0, 8 * (kScal - Scal::PART0), s);
-        k_big_classify<<<cg, 256, 0, s>>>(ea, big, scal + Scal::NBIG, big_cap, large_min, large,
-                                          scal + Scal::NLARGE, medium, scal + Scal::NMEDIUM, scal + Scal::PART0),
-            FAST_LAUNCHED(c);
-        if ((st = read_scal(c, s, "bucket classify"))) return fail(st);
+        for (const uint4 &e : hl) lp[per_st ? station_host(e.y) : 0] += (uint64_t)e.w * (e.w - 1) / 2;
+        auto twice = [](uint32_t m) { return m < (1u << 30) ? 2 * m : m + 1; };
+        bool raised = false;
+        for (size_t x = 0; x < gp.size(); x++)
+            if (gp[x] > lp[x]) {  // and classify again
+                if (per_st) lm_h[x] = twice(lm_h[x]);
+                else large_min = twice(large_min);
+                raised = true;
+            }
+        if (!raised) break;
+        if (per_st) upload_lm();
+        if ((st = reclassify())) return fail(st);
         nlarge = c->h_scal[Scal::NLARGE];
         nmedium = c->h_scal[Scal::NMEDIUM];
     }
@@ -3176,15 +3242,23 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
         uint32_t gshift = 0;
         const uint32_t target = c->group_pairs ? c->group_pairs : kVTargetDefault;
         while (gshift < 12 && (double)(2ull << gshift) * avg <= target) gshift++;
+        // a batch's rows are not equally dense: background pairs per row grow
+        // with the station's length, so station x expects N_x N / sum N_y^2
+        // times the mean
+        double dens = 1.0, sq = 0.0;
+        for (uint32_t x = 0; x < nst; x++) sq += std::pow((double)(tb->soff[x + 1] - tb->soff[x]), 2);
+        if (nst > 1 && sq > 0)
+            for (uint32_t x = 0; x < nst; x++)
+                dens = std::max(dens, (double)(tb->soff[x + 1] - tb->soff[x]) * (double)N / sq);
         // 32-bit entries while entry + 1 cannot wrap to the empty key
         uint64_t sp_n = 0;
         const fast_status r = gshift + nbits < 32
-                                  ? sparse_groups<uint32_t>(c, ea, medium, nmedium, large_min, gshift, nbits, sp_cnt,
-                                                            sp_start, &sp_j, &sp_v, &sp_n, long_rows, S, alloc, s,
-                                                            S_ub)
-                                  : sparse_groups<unsigned long long>(c, ea, medium, nmedium, large_min, gshift, nbits,
-                                                                      sp_cnt, sp_start, &sp_j, &sp_v, &sp_n, long_rows,
-                                                                      S, alloc, s, S_ub);
+                                  ? sparse_groups<uint32_t>(c, ea, medium, nmedium, large_min, dens, gshift, nbits,
+                                                            sp_cnt, sp_start, &sp_j, &sp_v, &sp_n, long_rows, S,
+                                                            alloc, s, S_ub)
+                                  : sparse_groups<unsigned long long>(c, ea, medium, nmedium, large_min, dens, gshift,
+                                                                      nbits, sp_cnt, sp_start, &sp_j, &sp_v, &sp_n,
+                                                                      long_rows, S, alloc, s, S_ub);
         if (r) return fail(r);
         owned.push_back({(void *)sp_j, sp_n * 4});  // freed with the search's other buffers
         owned.push_back({(void *)sp_v, sp_n});

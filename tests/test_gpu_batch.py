@@ -46,6 +46,37 @@ def test_uneven_stations_equal_single_station_runs(opts):
     s.close()
 
 
+def test_batch_thresholds_are_per_station():
+    # with the automatic dense threshold every station of a batch keeps its
+    # own: station a's buckets of 520..775 windows are dense alone, and stay
+    # dense next to station b, whose largest bucket (~15,500) would lift one
+    # batch-wide threshold above them
+    from dataclasses import replace
+
+    from paper_1803_09835_gb300 import Searcher
+    a = replace(synth.scaled("c2", 40_000, station=0, D=2048, K=100, b=30, occ_num=0), periods=(40,))
+    b = replace(synth.scaled("c2", 40_000, station=1, D=2048, K=100, b=30, occ_num=0), periods=(2,))
+    ia, ib = (synth.generate(w, ld=104) for w in (a, b))
+    s = Searcher(a.params())
+    keys = ("n_dense_pairs", "n_emissions", "n_groups", "n_detections")
+    alone = []
+    for x in (ia, ib):
+        r = s.detect(torch.from_numpy(x).cuda())
+        st = s.stats()
+        alone.append((r.numpy(), {k: st[k] for k in keys}, st["large_min"]))
+        r.free()
+    assert alone[0][1]["n_groups"] > 0 and alone[1][1]["n_groups"] > 0
+    batch = s.detect_batch(torch.from_numpy(np.concatenate([ia, ib])).cuda(), [a.N, b.N])
+    st = s.stats()
+    for x in range(2):
+        assert _eq(batch[x].numpy(), alone[x][0]), f"station {x}"
+        batch[x].free()
+    for k in keys:
+        assert st[k] == alone[0][1][k] + alone[1][1][k], k
+    assert st["large_min"] == max(alone[0][2], alone[1][2])
+    s.close()
+
+
 def test_equal_keys_across_a_station_boundary():
     # station 1 repeats station 0 window for window: the last keys of one
     # station equal the first keys of the next, and buckets must not merge
