@@ -836,13 +836,15 @@ struct MedLists {
 
 // Splits the medium list into the warp list and the CTA list (warp-aggregated
 // appends; the order inside each class does not matter).
+// With count_only, the classes are only counted (the lists are then
+// allocated at their sizes).
 __global__ void __launch_bounds__(256) k_med_split(const uint4 *__restrict__ medium,
                                                    const unsigned long long *__restrict__ nmedium,
                                                    uint4 *__restrict__ wl, unsigned long long *__restrict__ nw,
                                                    uint4 *__restrict__ cl, uint64_t cap,
                                                    unsigned long long *__restrict__ nf,
                                                    unsigned long long *__restrict__ nb, uint4 *__restrict__ hl,
-                                                   unsigned long long *__restrict__ nh) {
+                                                   unsigned long long *__restrict__ nh, bool count_only) {
     const uint64_t n = *nmedium;
     const uint32_t lane = threadIdx.x & 31, lt = (1u << lane) - 1;
     const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
@@ -865,7 +867,7 @@ __global__ void __launch_bounds__(256) k_med_split(const uint4 *__restrict__ med
             if ((int)lane == leader)
                 b0 = atomicAdd(k == 0 ? nw : k == 1 ? nf : k == 2 ? nb : nh, (unsigned long long)__popc(m));
             b0 = __shfl_sync(~0u, b0, leader);
-            if (cls == k) {
+            if (cls == k && !count_only) {
                 const uint64_t q = b0 + __popc(m & lt);
                 if (k == 0) wl[q] = e;
                 else if (k == 1) cl[q] = e;
@@ -2595,18 +2597,28 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     const uint64_t nwarps = (ntiles + tpw - 1) / tpw;
     const dim3 eg((unsigned)std::max<uint64_t>(1, (nwarps + 7) / 8), p.b);
     // medium buckets: the warp list and the CTA list (largest first)
+    // (counted first, then allocated at their sizes)
     uint4 *med_w = nullptr, *med_c = nullptr, *med_h = nullptr;
-    if ((st = lalloc(&med_w, nmedium)) || (st = lalloc(&med_c, nmedium)) ||
-        (large_min > kMedCap + 1 && (st = lalloc(&med_h, nmedium))))
-        return st;
+    uint64_t n_cta = 0;
+    const unsigned sg = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(nmedium, 256), c->num_sms * 8));
     cudaMemsetAsync(scal + Scal::NMEDW, 0, 8 * 4, s);
-    if (nmedium)
-        k_med_split<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(nmedium, 256), c->num_sms * 8)),
-                      256, 0, s>>>(medium, scal + Scal::NMEDIUM, med_w, scal + Scal::NMEDW, med_c, nmedium,
-                                   scal + Scal::NMEDF, scal + Scal::NMEDB, med_h ? med_h : med_c,
-                                   scal + Scal::NMEDH), FAST_LAUNCHED(c);
+    if (nmedium) {
+        k_med_split<<<sg, 256, 0, s>>>(medium, scal + Scal::NMEDIUM, nullptr, scal + Scal::NMEDW, nullptr, 0,
+                                       scal + Scal::NMEDF, scal + Scal::NMEDB, nullptr, scal + Scal::NMEDH, true),
+            FAST_LAUNCHED(c);
+        cudaMemcpyAsync(c->h_scal + Scal::NMEDW, scal + Scal::NMEDW, 8 * 4, cudaMemcpyDeviceToHost, s);
+        if ((st = sync_check(c, s, "medium classes"))) return st;
+        n_cta = c->h_scal[Scal::NMEDF] + c->h_scal[Scal::NMEDB];
+        if ((st = lalloc(&med_w, c->h_scal[Scal::NMEDW])) || (st = lalloc(&med_c, n_cta)) ||
+            (st = lalloc(&med_h, c->h_scal[Scal::NMEDH])))
+            return st;
+        cudaMemsetAsync(scal + Scal::NMEDW, 0, 8 * 4, s);
+        k_med_split<<<sg, 256, 0, s>>>(medium, scal + Scal::NMEDIUM, med_w, scal + Scal::NMEDW, med_c, n_cta,
+                                       scal + Scal::NMEDF, scal + Scal::NMEDB, med_h, scal + Scal::NMEDH, false),
+            FAST_LAUNCHED(c);
+    }
     const MedLists ml{med_w, med_c, med_h, scal + Scal::NMEDW, scal + Scal::NMEDF, scal + Scal::NMEDB,
-                      scal + Scal::NMEDH, nmedium, scal + Scal::MEDNEXT, scal + Scal::MEDNEXTH};
+                      scal + Scal::NMEDH, n_cta, scal + Scal::MEDNEXT, scal + Scal::MEDNEXTH};
     cudaMemsetAsync(scal + Scal::NSMALLEMIT, 0, 8, s);
     const GroupRange all{0, ng, 0};
     uint64_t S = 0;
@@ -2860,30 +2872,39 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
                 // rows too long for a shared-memory hash use one in global
                 // memory; their scratch is handed out chunk by chunk of rows,
                 // at most kHugeWords words per launch (or one row's need)
+                // (halved while the device cannot hold that much)
                 constexpr uint64_t kHugeWords = 1ull << 29;
-                std::vector<uint64_t> gofs(nlong), chunk{0};
-                uint64_t gtot = 0, gmax = 0;
-                for (uint64_t r = 0; r < nlong; r++) {
-                    uint64_t slots = 32;
-                    while (slots < 2ull * hl[r].y) slots <<= 1;
-                    c->stats.max_row = std::max<uint64_t>(c->stats.max_row, hl[r].y);
-                    const uint64_t need = slots > kRowBlockSlots ? 2 * slots : 0;
-                    if (need && gtot + need > kHugeWords && gtot) {  // the next chunk starts here
-                        chunk.push_back(r);
-                        gtot = 0;
+                std::vector<uint64_t> gofs(nlong), chunk;
+                for (uint64_t r = 0; r < nlong; r++) c->stats.max_row = std::max<uint64_t>(c->stats.max_row, hl[r].y);
+                for (uint64_t lim = kHugeWords, first = 1;; lim /= 2, first = 0) {
+                    chunk.assign(1, 0);
+                    uint64_t gtot = 0, gmax = 0, rmax = 0;
+                    for (uint64_t r = 0; r < nlong; r++) {
+                        uint64_t slots = 32;
+                        while (slots < 2ull * hl[r].y) slots <<= 1;
+                        const uint64_t need = slots > kRowBlockSlots ? 2 * slots : 0;
+                        if (need && gtot + need > lim && gtot) {  // the next chunk starts here
+                            chunk.push_back(r);
+                            gtot = 0;
+                        }
+                        gofs[r] = gtot;
+                        gtot += need;
+                        gmax = std::max(gmax, gtot);
+                        rmax = std::max(rmax, need);
+                        if (first) c->stats.n_huge_rows += need != 0;
                     }
-                    gofs[r] = gtot;
-                    gtot += need;
-                    gmax = std::max(gmax, gtot);
-                    c->stats.n_huge_rows += need != 0;
-                }
-                chunk.push_back(nlong);
-                if (gmax > gscr_cap) {  // one scratch for every partition, grown only when a row needs more
+                    chunk.push_back(nlong);
+                    if (gmax <= gscr_cap) break;  // one scratch for every partition, grown only when needed
                     dfree(c, gscr, gscr_cap * 4, s);
                     gscr = nullptr;
                     gscr_cap = 0;
-                    if ((st = dalloc_t(c, &gscr, gmax, s))) return st;
-                    gscr_cap = gmax;
+                    if (!(st = dalloc_t(c, &gscr, gmax, s))) {
+                        gscr_cap = gmax;
+                        break;
+                    }
+                    if ((st != FAST_ENOMEM && st != FAST_EBUDGET) || lim <= rmax) return st;
+                    st = FAST_OK;
+                    c->err.clear();
                 }
                 cudaMemcpyAsync(d_gofs, gofs.data(), nlong * 8, cudaMemcpyHostToDevice, s);
                 for (size_t k = 0; k + 1 < chunk.size(); k++) {
