@@ -693,6 +693,23 @@ struct RegionSink {
     }
 };
 
+// Slots for cnt new pairs of row group g: the single pass counts from 0 in
+// gcur (its regions are fixed); the counted pass takes them from the
+// group's cursor gpos, which starts at the group's offset in the pass's
+// buffer (one atomic, no offset lookup).
+template <int MODE>
+__device__ __forceinline__ uint64_t reserve(uint32_t *gcur, unsigned long long *gpos, uint64_t g, uint32_t cnt) {
+    if (MODE == 2) return atomicAdd(gcur + g, cnt);
+    return atomicAdd(gpos + g, (unsigned long long)cnt);
+}
+
+// gpos[g] = goff[g] - ebase for the groups of one pass.
+__global__ void k_init_pos(const uint64_t *__restrict__ goff, GroupRange gr, unsigned long long *__restrict__ gpos) {
+    for (uint64_t g = gr.g_lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < gr.g_hi;
+         g += (uint64_t)gridDim.x * blockDim.x)
+        gpos[g] = goff[g] - gr.ebase;
+}
+
 struct PairSmem {  // one warp's tile window and its pair bookkeeping
     uint32_t id[64], lab[64], pre[32];
     uint64_t keep[32];  // per row: window positions of its kept partners
@@ -701,7 +718,7 @@ struct PairSmem {  // one warp's tile window and its pair bookkeeping
 
 template <int MODE, typename PT>
 __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, uint32_t nbits, uint32_t tiles_per_warp,
-                                                   uint32_t *__restrict__ gcnt, const uint64_t *__restrict__ goff,
+                                                   uint32_t *__restrict__ gcnt, unsigned long long *__restrict__ gpos,
                                                    uint32_t *__restrict__ gcur, PT *__restrict__ ent,
                                                    unsigned long long *__restrict__ n_emit, GroupRange gr,
                                                    RegionSink rs = RegionSink{}) {
@@ -782,7 +799,7 @@ __global__ void __launch_bounds__(256) k_pairs_grp(EnumArgs a, uint32_t gshift, 
                 if (cnt) atomicAdd(gcnt + g, cnt);
             } else if (__any_sync(~0u, cnt != 0)) {
                 W.keep[lane] = keep;
-                W.base[lane] = !cnt ? 0 : MODE == 2 ? atomicAdd(gcur + g, cnt) : goff[g] - gr.ebase + atomicAdd(gcur + g, cnt);
+                W.base[lane] = !cnt ? 0 : reserve<MODE>(gcur, gpos, g, cnt);
                 __syncwarp();
                 for (uint32_t k = lane; k < P; k += 32) {
                     uint32_t L = 0;
@@ -888,7 +905,7 @@ __global__ void __launch_bounds__(256) k_med_split(const uint4 *__restrict__ med
 template <int MODE, typename PT>
 __global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, MedLists ml, bool huge, uint32_t mcap,
                                                     uint32_t gshift, uint32_t nbits, uint32_t *__restrict__ gcnt,
-                                                    const uint64_t *__restrict__ goff, uint32_t *__restrict__ gcur,
+                                                    unsigned long long *__restrict__ gpos, uint32_t *__restrict__ gcur,
                                                     PT *__restrict__ ent, GroupRange gr,
                                                     RegionSink rs = RegionSink{}) {
     extern __shared__ uint32_t med_dyn[];
@@ -921,7 +938,7 @@ __global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, MedLists ml, boo
                 if (MODE == 0) {
                     atomicAdd(gcnt + g, c);
                 } else {
-                    uint64_t o = MODE == 2 ? atomicAdd(gcur + g, c) : goff[g] - gr.ebase + atomicAdd(gcur + g, c);
+                    uint64_t o = reserve<MODE>(gcur, gpos, g, c);
                     for (uint32_t y = x + 1; y < e.z; y++) {
                         const uint32_t j = s[y];
                         if (!a.drop[j] && pair_live(a, i, j)) {
@@ -999,7 +1016,7 @@ __global__ void __launch_bounds__(256) k_medium_grp(EnumArgs a, MedLists ml, boo
                     continue;
                 }
                 uint64_t base = 0;
-                if (c) base = MODE == 2 ? atomicAdd(gcur + g, c) : goff[g] - gr.ebase + atomicAdd(gcur + g, c);
+                if (c) base = reserve<MODE>(gcur, gpos, g, c);
                 for (uint32_t todo = __ballot_sync(~0u, c != 0); todo; todo &= todo - 1) {
                     const int r = __ffs(todo) - 1;
                     const uint32_t ri = __shfl_sync(~0u, i, r), rli = __shfl_sync(~0u, li, r);
@@ -1047,7 +1064,7 @@ struct MedWarpSmem {
 
 template <int MODE, typename PT>
 __global__ void __launch_bounds__(256) k_medium_warp(EnumArgs a, MedLists ml, uint32_t gshift, uint32_t nbits,
-                                                     uint32_t *__restrict__ gcnt, const uint64_t *__restrict__ goff,
+                                                     uint32_t *__restrict__ gcnt, unsigned long long *__restrict__ gpos,
                                                      uint32_t *__restrict__ gcur, PT *__restrict__ ent,
                                                      GroupRange gr, RegionSink rs = RegionSink{}) {
     __shared__ MedWarpSmem msm[8];
@@ -1116,7 +1133,7 @@ __global__ void __launch_bounds__(256) k_medium_warp(EnumArgs a, MedLists ml, ui
                 continue;
             }
             unsigned long long b = 0;
-            if (c) b = MODE == 2 ? atomicAdd(gcur + g, c) : goff[g] - gr.ebase + atomicAdd(gcur + g, c);
+            if (c) b = reserve<MODE>(gcur, gpos, g, c);
             const uint32_t cu = li == kNone ? c : 0u;
             uint32_t inc = cu;
 #pragma unroll
@@ -1770,14 +1787,18 @@ __global__ void __launch_bounds__(256) k_dense_rowcount(const DenseTile *__restr
 //
 // Inside one dense group, the members sharing a key in table t form a
 // cluster; votes(i, j) is the number of tables in which i and j fall in the
-// same cluster.  Clusters of at least kClT members get one bit column each
-// (at most kClW * 32 per group): the tables where i and j share such a
-// cluster number popc(mask_i & mask_j).  The pairs of the smaller clusters
-// are added one by one into the tile votes.  Both parts are exact, so their
-// sum is the vote; a group with too many large clusters is voted by direct
-// key comparison (k_dense_rowcount) instead.
+// same cluster.  Clusters of at least the group's threshold get one bit
+// column each (at most kClW * 32 per group): the tables where i and j share
+// such a cluster number popc(mask_i & mask_j).  The pairs of the smaller
+// clusters are added one by one into the tile votes.  Both parts are exact,
+// so their sum is the vote.  The threshold is a power of two from kClT up,
+// chosen per group from a histogram of its cluster sizes: the one with the
+// fewest mask words per member pair plus enumerated pairs (weighted
+// kClEnum), among those that leave at most kClW * 32 columns.
 constexpr uint32_t kClT = 64;
 constexpr uint32_t kClW = 32;
+constexpr uint32_t kClBins = 18;  // cluster sizes 64 * 2^k .. 64 * 2^(k+1) - 1
+constexpr double kClEnum = 64.0;  // an enumerated pair (global atomic) against one mask word of a member pair
 
 struct DenseGroup {
     uint32_t g0, n, t0, nt;  // first member, members, first tile, tiles per side
@@ -1814,6 +1835,51 @@ __global__ void k_clu_starts(const uint32_t *__restrict__ flag, const uint64_t *
     }
 }
 
+// Per group: clusters and their pairs by size class (sizes of at least kClT).
+__global__ void k_clu_hist(const unsigned long long *__restrict__ comp, const uint64_t *__restrict__ cst,
+                           const uint64_t *__restrict__ ncl, const uint32_t *__restrict__ mg,
+                           uint32_t *__restrict__ hcnt, unsigned long long *__restrict__ hpairs) {
+    const uint64_t nc = *ncl;
+    for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t sz = cst[c + 1] - cst[c];
+        if (sz < kClT) continue;
+        const uint32_t g = mg[comp[cst[c]] & 0xFFFFFF];
+        const uint32_t bin = min(kClBins - 1, (uint32_t)(63 - __clzll((long long)(sz / kClT))));
+        atomicAdd(hcnt + (uint64_t)g * kClBins + bin, 1u);
+        atomicAdd(hpairs + (uint64_t)g * kClBins + bin, (unsigned long long)(sz * (sz - 1) / 2));
+    }
+}
+
+// Per group: the mask threshold kClT * 2^k of least estimated cost (see
+// above); gover marks a group that direct key comparison votes for less (b
+// comparisons per member pair, about two thirds of a mask word each).
+__global__ void k_clu_thr(const DenseGroup *__restrict__ G, uint64_t ngroups, uint32_t nb,
+                          const uint32_t *__restrict__ hcnt, const unsigned long long *__restrict__ hpairs,
+                          uint32_t *__restrict__ gthr, uint32_t *__restrict__ gover) {
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        const double mp = (double)G[g].n * (G[g].n - 1) / 2;
+        const uint32_t *h = hcnt + g * kClBins;
+        const unsigned long long *hp = hpairs + g * kClBins;
+        double best = 0, below = 0;  // enumerated pairs of the classes under threshold k
+        uint32_t bk = kClBins + 1;
+        for (uint32_t k = 0; k <= kClBins; k++) {
+            uint64_t cols = 0;
+            for (uint32_t q = k; q < kClBins; q++) cols += h[q];
+            if (cols <= kClW * 32) {
+                const double cost = mp * (double)((cols + 31) / 32) + kClEnum * below;
+                if (bk > kClBins || cost < best) {
+                    best = cost;
+                    bk = k;
+                }
+            }
+            if (k < kClBins) below += (double)hp[k];
+        }
+        if (bk > kClBins || best > mp * nb * (2.0 / 3.0)) gover[g] = 1;
+        gthr[g] = bk >= kClBins ? 0xFFFFFFFFu : kClT << bk;
+    }
+}
+
 // One warp per cluster: a column for a large one, its pairs for a small one.
 // MB is word-major: MB[w * nm + k].  tv32 holds the tile votes as bytes
 // (each below 256: at most b tables).
@@ -1822,7 +1888,7 @@ __global__ void __launch_bounds__(256) k_clu_apply(const unsigned long long *__r
                                                    const uint32_t *__restrict__ mg, const DenseGroup *__restrict__ G,
                                                    uint64_t nm, uint32_t *__restrict__ gcol,
                                                    uint32_t *__restrict__ gover, uint32_t *__restrict__ MB,
-                                                   uint32_t *__restrict__ tv32) {
+                                                   uint32_t *__restrict__ tv32, const uint32_t *__restrict__ gthr) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t nc = *ncl;
     for (uint64_t c = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; c < nc;
@@ -1831,7 +1897,8 @@ __global__ void __launch_bounds__(256) k_clu_apply(const unsigned long long *__r
         const uint32_t sz = (uint32_t)(e1 - e0);
         if (sz < 2) continue;  // warp-uniform
         const uint32_t g = mg[comp[e0] & 0xFFFFFF];
-        if (sz >= kClT) {
+        if (gover[g]) continue;  // voted by direct comparison
+        if (sz >= gthr[g]) {
             uint32_t col = 0;
             if (lane == 0) col = atomicAdd(gcol + g, 1u);
             col = __shfl_sync(~0u, col, 0);
@@ -1843,20 +1910,17 @@ __global__ void __launch_bounds__(256) k_clu_apply(const unsigned long long *__r
                 atomicOr(MB + (uint64_t)(col / 32) * nm + (comp[x] & 0xFFFFFF), 1u << (col & 31));
         } else {
             const DenseGroup D = G[g];
-            const uint32_t np = sz * (sz - 1) / 2;
-            for (uint32_t q = lane; q < np; q += 32) {
-                uint32_t a = 0, rem = q;  // pair q = (a, b), a < b, in row-major order of the triangle
-                while (rem >= sz - 1 - a) {
-                    rem -= sz - 1 - a;
-                    a++;
+            // pairs (a, b), a < b, of the cluster's members (ascending):
+            // row a by the warp, its partners b 32 at a time
+            for (uint32_t a = 0; a + 1 < sz; a++) {
+                const uint32_t la = (uint32_t)(comp[e0 + a] & 0xFFFFFF) - D.g0, ta = la / kDT;
+                for (uint32_t bb = a + 1 + lane; bb < sz; bb += 32) {
+                    const uint32_t lb = (uint32_t)(comp[e0 + bb] & 0xFFFFFF) - D.g0;
+                    const uint32_t tb = lb / kDT;
+                    const uint64_t tn = D.t0 + (uint64_t)ta * D.nt - (uint64_t)ta * (ta - 1) / 2 + (tb - ta);
+                    const uint64_t byte = tn * (kDT * kDT) + (la % kDT) * kDT + (lb % kDT);
+                    atomicAdd(tv32 + (byte >> 2), 1u << (8 * (byte & 3)));
                 }
-                const uint32_t bb = a + 1 + rem;
-                const uint32_t la = (uint32_t)(comp[e0 + a] & 0xFFFFFF) - D.g0;
-                const uint32_t lb = (uint32_t)(comp[e0 + bb] & 0xFFFFFF) - D.g0;
-                const uint32_t ta = la / kDT, tb = lb / kDT;
-                const uint64_t tn = D.t0 + (uint64_t)ta * D.nt - (uint64_t)ta * (ta - 1) / 2 + (tb - ta);
-                const uint64_t byte = tn * (kDT * kDT) + (la % kDT) * kDT + (lb % kDT);
-                atomicAdd(tv32 + (byte >> 2), 1u << (8 * (byte & 3)));
             }
         }
     }
@@ -1942,70 +2006,63 @@ __global__ void __launch_bounds__(256) k_dense_rows(const DenseStrip *__restrict
                                                     uint32_t v, uint32_t excl, const uint64_t *__restrict__ row_off,
                                                     uint32_t *__restrict__ oi, uint32_t *__restrict__ oj,
                                                     uint8_t *__restrict__ ov) {
-    __shared__ uint32_t s_cur[kDT];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const uint32_t lane = threadIdx.x & 31;
+    // A tile's votes and column ids are staged in shared memory; warp w owns
+    // rows 8w .. 8w + 7 of the strip: for each, two ballots give the row's
+    // kept columns as a 64-bit mask and the lanes write them compacted, in
+    // column order, as one coalesced run after the row's running count.
+    __shared__ __align__(16) uint8_t s_v[kDT][kDT];
+    __shared__ uint32_t s_rid[kDT], s_jid[kDT], s_cur[kDT];
+    __shared__ uint64_t s_off[kDT];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, lt = (1u << lane) - 1;
     for (uint64_t si = blockIdx.x; si < nstrips; si += gridDim.x) {
         const DenseStrip S = strips[si];
         const uint32_t nt = (S.n + kDT - 1) / kDT;
-        __syncthreads();
-        if (threadIdx.x < kDT) s_cur[threadIdx.x] = 0;
-        uint32_t rid[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const uint32_t ga = S.ta * kDT + ty * 4 + u;
-            rid[u] = ga < S.n ? ids[S.g0 + ga] : 0;
+        __syncthreads();  // the previous strip is done with the row arrays
+        if (threadIdx.x < kDT) {
+            const uint32_t ga = S.ta * kDT + threadIdx.x;
+            const uint32_t rid = ga < S.n ? ids[S.g0 + ga] : 0u;
+            s_rid[threadIdx.x] = rid;
+            s_off[threadIdx.x] = ga < S.n ? row_off[rid] : 0;
+            s_cur[threadIdx.x] = 0;
         }
         const uint64_t trow = (uint64_t)S.t0 + (uint64_t)S.ta * nt - (uint64_t)S.ta * (S.ta - 1) / 2 - S.ta;
-        __syncthreads();
         for (uint32_t tb = S.ta; tb < nt; tb++) {
-            uint32_t acc[4][4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const uchar4 q = tv[(trow + tb) * (kDT * kDT / 4) + (ty * 4 + u) * (kDT / 4) + tx];
-                acc[u][0] = q.x;
-                acc[u][1] = q.y;
-                acc[u][2] = q.z;
-                acc[u][3] = q.w;
+            __syncthreads();  // every warp is done with the previous tile
+            const uchar4 *src = tv + (trow + tb) * (kDT * kDT / 4);
+            for (uint32_t x = threadIdx.x; x < kDT * kDT / 4; x += blockDim.x)
+                reinterpret_cast<uchar4 *>(&s_v[0][0])[x] = src[x];
+            if (threadIdx.x < kDT) {
+                const uint32_t gb = tb * kDT + threadIdx.x;
+                s_jid[threadIdx.x] = gb < S.n ? ids[S.g0 + gb] : 0u;
             }
-            uint32_t jid[4];
+            __syncthreads();
+            for (uint32_t r = warp * 8; r < warp * 8 + 8; r++) {
+                const uint32_t ga = S.ta * kDT + r;
+                if (ga >= S.n) break;  // warp-uniform
+                const uint32_t rid = s_rid[r];
+                bool keep[2];
+                uint32_t m[2];
 #pragma unroll
-            for (int w = 0; w < 4; w++) {
-                const uint32_t gb = tb * kDT + tx * 4 + w;
-                jid[w] = gb < S.n ? ids[S.g0 + gb] : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const uint32_t ga = S.ta * kDT + ty * 4 + u;
-                uint32_t keep = 0;
-#pragma unroll
-                for (int w = 0; w < 4; w++) {
-                    const uint32_t gb = tb * kDT + tx * 4 + w;
-                    if (ga < S.n && gb < S.n && ga < gb && acc[u][w] >= v && jid[w] - rid[u] > excl) keep |= 1u << w;
+                for (int h = 0; h < 2; h++) {
+                    const uint32_t col = h * 32 + lane, gb = tb * kDT + col;
+                    keep[h] = gb < S.n && ga < gb && s_v[r][col] >= v && s_jid[col] - rid > excl;
+                    m[h] = __ballot_sync(~0u, keep[h]);
                 }
-                const uint32_t c = __popc(keep);
-                // inclusive scan over the 16 lanes of this row (same ty)
-                uint32_t inc = c;
+                const uint32_t cnt = __popc(m[0]) + __popc(m[1]);
+                if (!cnt) continue;  // warp-uniform
+                const uint64_t base = s_off[r] + s_cur[r];
 #pragma unroll
-                for (int d = 1; d < 16; d <<= 1) {
-                    uint32_t y = __shfl_up_sync(~0u, inc, d, 16);
-                    if ((lane & 15) >= (uint32_t)d) inc += y;
-                }
-                const uint32_t r = ty * 4 + u;
-                if (c) {
-                    uint64_t o = row_off[rid[u]] + s_cur[r] + (inc - c);
-#pragma unroll
-                    for (int w = 0; w < 4; w++)
-                        if (keep >> w & 1) {
-                            oi[o] = rid[u];
-                            oj[o] = jid[w];
-                            ov[o] = (uint8_t)acc[u][w];
-                            ++o;
-                        }
-                }
-                const uint32_t row_tot = __shfl_sync(~0u, inc, (lane & 16) | 15);
-                __syncthreads();
-                if (tx == 0) s_cur[r] += row_tot;
+                for (int h = 0; h < 2; h++)
+                    if (keep[h]) {
+                        const uint32_t col = h * 32 + lane;
+                        const uint64_t o = base + (h ? __popc(m[0]) : 0u) + __popc(m[h] & lt);
+                        oi[o] = rid;
+                        oj[o] = s_jid[col];
+                        ov[o] = s_v[r][col];
+                    }
+                __syncwarp();
+                if (lane == 0) s_cur[r] += cnt;  // row r belongs to this warp alone
+                __syncwarp();
             }
         }
     }
@@ -2019,17 +2076,31 @@ __global__ void k_sparse_place(uint64_t N, const uint32_t *__restrict__ sp_cnt, 
                                uint32_t *__restrict__ oi, uint32_t *__restrict__ oj, uint8_t *__restrict__ ov,
                                uint32_t *__restrict__ merge_rows, uint64_t *__restrict__ merge_ofs,
                                unsigned long long *__restrict__ n_merge, unsigned long long *__restrict__ merge_tot) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t n = sp_cnt[i];
-        if (!n) continue;
-        const uint32_t d = dense_cnt ? dense_cnt[i] : 0;
-        const uint64_t o = row_off[i] + d, s = sp_start[i];
-        for (uint32_t k = 0; k < n; k++) {
-            oi[o + k] = (uint32_t)i;
-            oj[o + k] = sp_j[s + k];
-            ov[o + k] = sp_v[s + k];
+    // a warp takes 32 consecutive rows (coalesced counts and offsets) and
+    // copies each non-empty one with all lanes (coalesced runs)
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    for (uint64_t base = ((uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32) * 32; base < N;
+         base += nwarps * 32) {
+        const uint64_t i = base + lane;
+        uint32_t n = 0, d = 0;
+        uint64_t o = 0, s = 0;
+        if (i < N && (n = sp_cnt[i]) != 0) {
+            d = dense_cnt ? dense_cnt[i] : 0;
+            o = row_off[i] + d;
+            s = sp_start[i];
         }
-        if (d) {
+        for (uint32_t todo = __ballot_sync(~0u, n != 0); todo; todo &= todo - 1) {
+            const int r = __ffs(todo) - 1;
+            const uint32_t rn = __shfl_sync(~0u, n, r), ri = (uint32_t)(base + r);
+            const uint64_t ro = __shfl_sync(~0u, o, r), rs = __shfl_sync(~0u, s, r);
+            for (uint32_t k = lane; k < rn; k += 32) {
+                oi[ro + k] = ri;
+                oj[ro + k] = sp_j[rs + k];
+                ov[ro + k] = sp_v[rs + k];
+            }
+        }
+        if (n && d) {
             const unsigned long long q = atomicAdd(n_merge, 1ull);
             merge_rows[q] = (uint32_t)i;
             merge_ofs[q] = atomicAdd(merge_tot, (unsigned long long)(d + n));
@@ -2525,7 +2596,7 @@ __global__ void k_part_cuts(const uint64_t *__restrict__ goff, uint64_t ng, uint
 // resident CTA takes work until the lists are done).
 template <int MODE, typename PT>
 static void medium_launch(fast_ctx *c, const EnumArgs &ea, const MedLists &ml, uint32_t large_min, uint32_t gshift,
-                          uint32_t nbits, uint32_t *gcnt, const uint64_t *goff, uint32_t *gcur, PT *ent,
+                          uint32_t nbits, uint32_t *gcnt, unsigned long long *gpos, uint32_t *gcur, PT *ent,
                           GroupRange gr, RegionSink rs, cudaStream_t s) {
     static int occ_w = 0, occ_c = 0;
     const size_t csm = (size_t)2 * kMedCap * 4;
@@ -2537,7 +2608,7 @@ static void medium_launch(fast_ctx *c, const EnumArgs &ea, const MedLists &ml, u
         occ_w = std::max(occ_w, 1);
         occ_c = std::max(occ_c, 1);
     }
-    k_medium_warp<MODE, PT><<<c->num_sms * occ_w, 256, 0, s>>>(ea, ml, gshift, nbits, gcnt, goff, gcur, ent, gr,
+    k_medium_warp<MODE, PT><<<c->num_sms * occ_w, 256, 0, s>>>(ea, ml, gshift, nbits, gcnt, gpos, gcur, ent, gr,
                                                                  rs), FAST_LAUNCHED(c);
     if (large_min > kMedCap + 1) {  // live members of a medium bucket stay below large_min
         const uint32_t hcap = std::min(large_min, kMedHugeCap);
@@ -2546,10 +2617,10 @@ static void medium_launch(fast_ctx *c, const EnumArgs &ea, const MedLists &ml, u
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_h, k_medium_grp<MODE, PT>, 256, hsm);
         cudaMemsetAsync(ml.next_h, 0, 8, s);
         k_medium_grp<MODE, PT><<<c->num_sms * std::max(occ_h, 1), 256, hsm, s>>>(
-            ea, ml, true, hcap, gshift, nbits, gcnt, goff, gcur, ent, gr, rs), FAST_LAUNCHED(c);
+            ea, ml, true, hcap, gshift, nbits, gcnt, gpos, gcur, ent, gr, rs), FAST_LAUNCHED(c);
     }
     cudaMemsetAsync(ml.next, 0, 8, s);
-    k_medium_grp<MODE, PT><<<c->num_sms * occ_c, 256, csm, s>>>(ea, ml, false, kMedCap, gshift, nbits, gcnt, goff,
+    k_medium_grp<MODE, PT><<<c->num_sms * occ_c, 256, csm, s>>>(ea, ml, false, kMedCap, gshift, nbits, gcnt, gpos,
                                                                   gcur, ent, gr, rs), FAST_LAUNCHED(c);
 }
 
@@ -2717,6 +2788,8 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
     }
     S_out = S;
     c->stats.n_pairs_small = c->h_scal[Scal::NSMALLEMIT];
+    unsigned long long *gpos = nullptr;  // the counted pass's group cursors
+    if (!single && (st = lalloc(&gpos, ng))) return st;
 
     // Query partitions (§6.4): consecutive row-group ranges of about equal
     // pair counts, each written and voted in turn, so the pair buffer holds
@@ -2831,15 +2904,18 @@ static fast_status sparse_groups(fast_ctx *c, const EnumArgs &ea, const uint4 *m
             va.g_lo = gr.g_lo;
             va.g_hi = gr.g_hi;
             va.ebase = gr.ebase;
-            // write the range's pairs (gcur restarts per range: every group is in exactly one)
+            // write the range's pairs (each group's cursor starts at its offset in the range's buffer)
             if (!single) {
-                if (cut.size() > 2 || attempt > 0) cudaMemsetAsync(gcur + gr.g_lo, 0, (gr.g_hi - gr.g_lo) * 4, s);
+                k_init_pos<<<(unsigned)std::max<uint64_t>(
+                                 1, std::min<uint64_t>(ceil_div(gr.g_hi - gr.g_lo, 256), c->num_sms * 8)),
+                             256, 0, s>>>(goff, gr, gpos), FAST_LAUNCHED(c);
                 stage_mark(c, 10, s);
-                k_pairs_grp<1, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, tpw, nullptr, goff, gcur, ent, nullptr, gr),
+                k_pairs_grp<1, PT><<<eg, 256, 0, s>>>(ea, gshift, nbits, tpw, nullptr, gpos, gcur, ent, nullptr, gr),
                     FAST_LAUNCHED(c);
                 stage_mark(c, 12, s);
                 if (nmedium)
-                    medium_launch<1, PT>(c, ea, ml, large_min, gshift, nbits, nullptr, goff, gcur, ent, gr, RegionSink{}, s);
+                    medium_launch<1, PT>(c, ea, ml, large_min, gshift, nbits, nullptr, gpos, gcur, ent, gr,
+                                         RegionSink{}, s);
                 stage_mark(c, 11, s);
             }
             // vote the range
@@ -3204,8 +3280,19 @@ static fast_status search_rows(fast_ctx *c, const fast_tables *tb, const uint32_
             k_clu_mark<<<eg, 256, 0, s>>>(sc, ne, d_mg, flag), FAST_LAUNCHED(c);
             if ((r = scan_excl(c, flag, cid, ne, 1, cid + ne, s))) return r;
             k_clu_starts<<<eg, 256, 0, s>>>(flag, cid, ne, cid + ne, cst), FAST_LAUNCHED(c);
+            uint32_t *hcnt = nullptr, *gthr = nullptr;
+            unsigned long long *hpairs = nullptr;
+            if ((r = alloc(&hcnt, ngroups * kClBins)) || (r = alloc(&hpairs, ngroups * kClBins)) ||
+                (r = alloc(&gthr, ngroups)))
+                return r;
+            cudaMemsetAsync(hcnt, 0, ngroups * kClBins * 4, s);
+            cudaMemsetAsync(hpairs, 0, ngroups * kClBins * 8, s);
+            k_clu_hist<<<eg, 256, 0, s>>>(sc, cst, cid + ne, d_mg, hcnt, hpairs), FAST_LAUNCHED(c);
+            k_clu_thr<<<(unsigned)std::max<uint64_t>(1, ceil_div(ngroups, 128)), 128, 0, s>>>(d_grp, ngroups, nb,
+                                                                                            hcnt, hpairs, gthr, gover),
+                FAST_LAUNCHED(c);
             k_clu_apply<<<c->num_sms * 8, 256, 0, s>>>(sc, cst, cid + ne, d_mg, d_grp, nm, gcol, gover, MB,
-                                                       reinterpret_cast<uint32_t *>(tvotes)), FAST_LAUNCHED(c);
+                                                       reinterpret_cast<uint32_t *>(tvotes), gthr), FAST_LAUNCHED(c);
             return FAST_OK;
         };
         // only a lack of memory (or a group too large for the masks) falls
