@@ -234,18 +234,20 @@ def _kernel_source_hash(rel: str) -> str:
     return hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest()[:16]
 
 
-def _traffic(kernel: str, units: dict):
-    """DRAM bytes of a kernel over a step, from the committed ncu record of
-    that kernel (profiles/dram_traffic.json: bytes per unit of its work,
-    scaled to the step's units), or None when there is none or the kernel's
-    source changed since."""
+def _traffic(kernel: str, key: str):
+    """DRAM bytes of a kernel in one step (one search of every station of the
+    workload), from the committed ncu record of that kernel on this workload
+    (profiles/dram_traffic.json, keyed by workload and windows), or None when
+    there is none or the kernel's source changed since.  Records are not
+    carried across workload sizes: the pair kernels' misses grow faster than
+    their work once their buffers outgrow L2."""
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))[kernel]
-    except (OSError, ValueError, KeyError):
+        rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))[key][kernel]
+    except (OSError, ValueError, KeyError, TypeError):
         return None
-    if _kernel_source_hash(rec["source"]) != rec["source_sha256_16"] or rec.get("unit") not in units:
+    if _kernel_source_hash(rec["source"]) != rec["source_sha256_16"]:
         return None
-    return rec["bytes_per_unit"] * units[rec["unit"]]
+    return rec["bytes_per_run"]
 
 
 def _peaks():
@@ -291,11 +293,11 @@ KERNEL_MS = {"k_sig_walk": "sig", "radix sort": "sort", "k_pairs_grp": "k_pairs"
 SINGLE = {"k_sig_walk", "k_pairs_grp", "k_medium_grp", "k_pairs_grp count", "k_warp_vote"}
 
 
-def kernel_rooflines(kb, per, steps, peaks):
+def kernel_rooflines(kb, per, steps, peaks, key=""):
     """Per heavy kernel: live ms per step (CUDA events on the launching
     stream, summed over the step's launches), algorithmic bytes per step and
-    the HBM roofline fraction they reach; ``traffic`` is DRAM bytes from the
-    committed ncu record of that kernel (scaled to the step's units), or None."""
+    the HBM roofline fraction they reach; ``traffic`` is DRAM bytes per step
+    from the committed ncu record of that kernel on this workload, or None."""
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     src = "measured" if "hbm_gbs" in peaks else "fallback"
     out = {}
@@ -304,8 +306,7 @@ def kernel_rooflines(kb, per, steps, peaks):
         nbytes = kb.b[name] / steps
         ach = nbytes / (ms / 1000) / 1e9 if ms > 0 else 0.0
         out[name] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                     "traffic": (lambda t: t / steps if t is not None else None)(
-                         _traffic(name, kb.units)), "peak_source": f"{src} ({hbm:g} GB/s)",
+                     "traffic": _traffic(name, key), "peak_source": f"{src} ({hbm:g} GB/s)",
                      "algorithmic_bytes": nbytes, "ms": ms, "single_kernel": name in SINGLE}
     return out
 
@@ -334,14 +335,16 @@ class Meter:
         self.kb = KernelBytes(w)
         self.last = {}
 
-    def add(self, N, st):
+    def add(self, N, st, key=None):
+        """One search of N windows; `key` names it in the line's counters
+        (default N: batches of equal length need their own keys)."""
         if not self.on:
             return
         for k in STAGES:
             self.acc[k] += st["ms_" + k]
         self.launches += st["n_launches"]
         self.kb.add(N, st)
-        self.last[N] = {k: st[k] for k in COUNTERS}
+        self.last[N if key is None else key] = {**{k: st[k] for k in COUNTERS}, "windows": N}
 
 
 def _sample_line(w, n, label):
@@ -417,7 +420,7 @@ def station_arm(args, rank, world, local_rank, w, steps, warmup, e2e=True):
         line["e2e"] = {"value": n_total / (e2e_ms / 1000), "unit": UNIT, "ms_per_step": e2e_ms,
                        "h2d_bytes_per_step": w.N * ld * 2, "d2h_bytes_per_step": M * 9}
     per = {k: meter.acc[k] / steps for k in STAGES}
-    kernels = kernel_rooflines(meter.kb, per, steps, _peaks())
+    kernels = kernel_rooflines(meter.kb, per, steps, _peaks(), traffic_key(w.name, w.N))
     line["roofline"] = dominant(kernels)
     line["kernels"] = {k: {kk: v[kk] for kk in ("ms", "bound", "achieved", "frac", "unit")} for k, v in kernels.items()}
     line["stage_ms"] = per
@@ -481,7 +484,7 @@ def c2_arm(args, rank, world, local_rank):
         tot = 0
         for grp, d, lens in bufs:
             res = s.detect_batch(d, lens)
-            meter.add(sum(lens), s.stats())
+            meter.add(sum(lens), s.stats(), "+".join(str(m) for m in grp))
             for m, r in zip(grp, res):
                 last_M[m] = r.M
                 tot += r.M
@@ -576,7 +579,7 @@ def c2_arm(args, rank, world, local_rank):
     torch.cuda.empty_cache()
 
     per = {k: meter.acc[k] / args.steps for k in STAGES}
-    kernels = kernel_rooflines(meter.kb, per, args.steps, _peaks())
+    kernels = kernel_rooflines(meter.kb, per, args.steps, _peaks(), traffic_key("c2", N_all))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
@@ -636,10 +639,18 @@ TRAFFIC_KERNELS = {  # kernel-name prefix in the ncu list -> (roofline name, sou
     "k_sig_walk": ("k_sig_walk", "paper_1803_09835_gb300/csrc/k_sig.cu", "fingerprint"),
     "k_pairs_grp<2": ("k_pairs_grp", "paper_1803_09835_gb300/csrc/k_search.cu", "small-bucket pair"),
     "k_pairs_grp<1": ("k_pairs_grp", "paper_1803_09835_gb300/csrc/k_search.cu", "small-bucket pair"),
+    "k_pairs_grp<0": ("k_pairs_grp count", "paper_1803_09835_gb300/csrc/k_search.cu", "small-bucket pair"),
     "k_medium_grp<2": ("k_medium_grp", "paper_1803_09835_gb300/csrc/k_search.cu", "medium-bucket pair"),
     "k_medium_grp<1": ("k_medium_grp", "paper_1803_09835_gb300/csrc/k_search.cu", "medium-bucket pair"),
+    "k_medium_warp<2": ("k_medium_grp", "paper_1803_09835_gb300/csrc/k_search.cu", "medium-bucket pair"),
+    "k_medium_warp<1": ("k_medium_grp", "paper_1803_09835_gb300/csrc/k_search.cu", "medium-bucket pair"),
     "k_warp_vote": ("k_warp_vote", "paper_1803_09835_gb300/csrc/k_search.cu", "emission"),
 }
+
+
+def traffic_key(name: str, windows: int) -> str:
+    """Key of a workload's DRAM record: its name and windows per step."""
+    return f"{name}/{windows}"
 
 
 def units_of(st: dict, N: int) -> dict:
@@ -660,8 +671,20 @@ def record_traffic(csv_path: str, line_path: str, command: str, out_path: str | 
     bytes follow the pairs they write."""
     import csv
     line = json.loads([x for x in open(line_path) if x.startswith("{")][-1])
-    N = line["config"]["N_per_station"]
-    units = {k: v * runs for k, v in units_of(line["counters"], N).items()}
+    if "counters_by_batch" in line:  # the 12-station step: its batches' units
+        N = line["config"]["windows_per_step"]
+        wkey = traffic_key("c2", N)
+        units = {}
+        batches = line["counters_by_batch"]
+        for n, cnt in batches.items():
+            for k, v in units_of(cnt, cnt.get("windows", int(n) if n.isdigit() else 0)).items():
+                units[k] = units.get(k, 0) + v * runs
+        if sum(c.get("windows", int(n) if n.isdigit() else 0) for n, c in batches.items()) != N:
+            units = {}  # counters of some batches missing: bytes per search only
+    else:
+        N = line["config"]["N_per_station"]
+        wkey = traffic_key(line["config"]["workload"].split(":")[0], N)
+        units = {k: v * runs for k, v in units_of(line["counters"], N).items()}
     scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
     rows = list(csv.reader(open(csv_path)))
     hdr = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
@@ -687,14 +710,23 @@ def record_traffic(csv_path: str, line_path: str, command: str, out_path: str | 
     out = {}
     for name, rec in seen.items():
         _, src, unit = TRAFFIC_KERNELS[rec["key"]]
-        n = max(1, units[unit])
+        tot = rec["read"] + rec["write"]
+        n = units.get(unit, 0)
         out[name] = {"source": src, "source_sha256_16": _kernel_source_hash(src),
-                     "bytes_per_unit": (rec["read"] + rec["write"]) / n, "unit": unit,
-                     "captured_on": f"{N:,} windows, {runs} search(es), {len(rec['ids'])} launch(es), "
-                                    f"{n:,} {unit}s",
+                     "bytes_per_run": tot / runs, "bytes_per_unit": tot / n if n else None,
+                     "unit": unit if n else None,
+                     "captured_on": f"{N:,} windows, {runs} search(es), {len(rec['ids'])} launch(es)"
+                                    + (f", {n:,} {unit}s" if n else ""),
                      "dram_read_bytes": rec["read"], "dram_write_bytes": rec["write"], "command": command}
-    with open(out_path or os.path.join(ROOT, "profiles", "dram_traffic.json"), "w") as f:
-        json.dump(out, f, indent=1)
+    path = out_path or os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        every = json.load(open(path))
+        every = {k: v for k, v in every.items() if "/" in k}  # records of other workloads stay
+    except (OSError, ValueError):
+        every = {}
+    every[wkey] = out
+    with open(path, "w") as f:
+        json.dump(every, f, indent=1)
         f.write("\n")
     return out
 

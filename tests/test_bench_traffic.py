@@ -43,7 +43,8 @@ def test_record_traffic(tmp_path):
     line = tmp_path / "line.log"
     _write_csv(src, launches)
     counters = {"n_pairs_small": 2_000_000, "n_emissions": 2_500_000}
-    line.write_text("noise\n" + json.dumps({"config": {"N_per_station": 1_000_000}, "counters": counters}) + "\n")
+    line.write_text("noise\n" + json.dumps({"config": {"workload": "c1@1000000: ...", "N_per_station": 1_000_000},
+                                            "counters": counters}) + "\n")
     rec = bench.record_traffic(str(src), str(line), "cmd", str(out))
     assert set(rec) == {"k_sig_walk", "k_pairs_grp", "k_medium_grp", "k_warp_vote"}
     assert rec["k_sig_walk"]["dram_read_bytes"] == 6.2e9 and rec["k_sig_walk"]["unit"] == "fingerprint"
@@ -55,16 +56,40 @@ def test_record_traffic(tmp_path):
     assert abs(rec["k_medium_grp"]["bytes_per_unit"] - (4e9 + 1500e6) / 5e5) < 1e-6
     assert abs(rec["k_warp_vote"]["bytes_per_unit"] - (5.4e9 + 2e6) / 2.5e6) < 1e-6
     on_disk = json.load(open(out))
-    assert on_disk == json.loads(json.dumps(rec))
+    assert on_disk == {"c1@1000000/1000000": json.loads(json.dumps(rec))}
     for name, r in rec.items():
         assert r["source_sha256_16"] == bench._kernel_source_hash(r["source"]), name
+    # a second workload is kept beside the first; the 12-station line sums
+    # its batches' units (two runs: warm-up and timed step)
+    line2 = tmp_path / "line2.log"
+    batches = {"2+1": {"n_pairs_small": 1_000_000, "n_emissions": 1_500_000, "windows": 3_000_000},
+               "1": {"n_pairs_small": 1_000_000, "n_emissions": 1_000_000, "windows": 1_000_000}}
+    line2.write_text(json.dumps({"config": {"workload": "c2: ...", "windows_per_step": 4_000_000},
+                                 "counters_by_batch": batches}) + "\n")
+    rec2 = bench.record_traffic(str(src), str(line2), "cmd", str(out), runs=2)
+    assert abs(rec2["k_sig_walk"]["bytes_per_unit"] - (6.2e9 + 3000.5e6) / 8e6) < 1e-6
+    assert abs(rec2["k_pairs_grp"]["bytes_per_unit"] - (17.0e9 + 12800e6) / 4e6) < 1e-6
+    assert abs(rec2["k_medium_grp"]["bytes_per_unit"] - (4e9 + 1500e6) / 1e6) < 1e-6
+    assert abs(rec2["k_pairs_grp"]["bytes_per_run"] - (17.0e9 + 12800e6) / 2) < 1e-3
+    assert set(json.load(open(out))) == {"c1@1000000/1000000", "c2/4000000"}
+    # a line whose batches do not add up to the step records bytes per search only
+    batches.pop("1")
+    line2.write_text(json.dumps({"config": {"workload": "c2: ...", "windows_per_step": 4_000_000},
+                                 "counters_by_batch": batches}) + "\n")
+    rec3 = bench.record_traffic(str(src), str(line2), "cmd", str(out), runs=2)
+    assert rec3["k_pairs_grp"]["bytes_per_unit"] is None and rec3["k_pairs_grp"]["bytes_per_run"] > 0
 
 
 def test_committed_traffic_matches_its_sources():
-    # every committed record names a source file of this repository, a unit
-    # the roofline knows and the hash format it checks against
-    rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
-    for name, r in rec.items():
-        assert os.path.exists(os.path.join(ROOT, r["source"])), name
-        assert len(r["source_sha256_16"]) == 16 and r["bytes_per_unit"] > 0
-        assert r["unit"] in ("fingerprint", "small-bucket pair", "medium-bucket pair", "emission")
+    # every committed record names a workload (name/windows), a source file
+    # of this repository, a unit the roofline knows and the hash format it
+    # checks against
+    every = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
+    for key, rec in every.items():
+        name, windows = key.split("/")
+        assert name and int(windows) > 0
+        for kernel, r in rec.items():
+            assert os.path.exists(os.path.join(ROOT, r["source"])), kernel
+            assert len(r["source_sha256_16"]) == 16 and r["bytes_per_run"] > 0
+            assert r["unit"] in (None, "fingerprint", "small-bucket pair", "medium-bucket pair", "emission")
+            assert (r["unit"] is None) == (r["bytes_per_unit"] is None)
