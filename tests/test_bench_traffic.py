@@ -93,3 +93,19 @@ def test_committed_traffic_matches_its_sources():
             assert len(r["source_sha256_16"]) == 16 and r["bytes_per_run"] > 0
             assert r["unit"] in (None, "fingerprint", "small-bucket pair", "medium-bucket pair", "emission")
             assert (r["unit"] is None) == (r["bytes_per_unit"] is None)
+
+
+def test_meter_keeps_batches_of_equal_length_apart():
+    # batches of the same total length (7 months: 7, 6+1, 5+2, 4+3) each keep
+    # their own counters, with their window count, in the line
+    st = {k: 1.0 for k in ("ms_" + s for s in bench.STAGES)}
+    st.update({k: 3 for k in bench.COUNTERS}, n_launches=5, n_fingerprints=7)
+    import synth
+    m = bench.Meter(synth.scaled("c2", 1000))
+    m.on = True
+    for key in ("7", "6+1", "5+2", "4+3"):
+        m.add(18_144_000, dict(st, n_emissions=len(key)), key)
+    assert set(m.last) == {"7", "6+1", "5+2", "4+3"}
+    assert all(c["windows"] == 18_144_000 for c in m.last.values())
+    assert [m.last[k]["n_emissions"] for k in ("7", "6+1", "5+2", "4+3")] == [1, 3, 3, 3]
+    assert m.launches == 20
