@@ -292,6 +292,37 @@ KERNEL_MS = {"k_sig_walk": "sig", "radix sort": "sort", "k_pairs_grp": "k_pairs"
              "k_pairs_grp count": "k_count_small", "k_warp_vote": "k_vote", "output": "output"}
 SINGLE = {"k_sig_walk", "k_pairs_grp", "k_medium_grp", "k_pairs_grp count", "k_warp_vote"}
 
+WALK_TILE, WALK_BATCH = 32, 8  # fingerprints per walk tile, ranking steps read per batch (k_sig_walk)
+SMEM_LOOKUPS_PER_CLK = 32      # conflict-free shared-memory reads per SM and clock (one warp-wide load)
+
+
+def walk_steps(D: int, K: int, tile: int = WALK_TILE, batch: int = WALK_BATCH) -> float:
+    """Expected ranking steps of one k_sig_walk walk, for fingerprints of K
+    set bits drawn uniformly from D: a walk over one function's ranking of
+    [0, D) stops at the batch of `batch` steps in which the last of the
+    tile's `tile` fingerprints is hit.  P(a fingerprint is missed by the
+    first s elements) = C(D - K, s) / C(D, s); the walk's length is the
+    maximum over the tile of the first-hit positions."""
+    miss, m = [1.0], 1.0
+    for s in range(1, D + 1):
+        m *= max(0.0, D - K - (s - 1)) / (D - (s - 1))
+        miss.append(m)
+    return batch * sum(1.0 - (1.0 - miss[min(D, x)]) ** tile for x in range(0, D + batch, batch))
+
+
+def walk_bound(w, ms: float, n_fp: float, sms: int = 152, clk_ghz: float = 2.07) -> dict:
+    """k_sig_walk against its own work: shared-memory membership lookups
+    (one per walk step: every function's min walk and, for Min-Max, its max
+    walk, over each tile of 32 fingerprints) per second, against the SMs'
+    conflict-free lookup rate at the nominal clock."""
+    nf = w.b * w.r if w.kind == 0 else w.b * ((w.r + 1) // 2)
+    walks = nf if w.kind == 0 else 2 * nf
+    per_fp = walks * walk_steps(w.D, w.K) / WALK_TILE
+    rate = n_fp * per_fp / (ms / 1000) if ms > 0 else 0.0
+    peak = sms * SMEM_LOOKUPS_PER_CLK * clk_ghz * 1e9
+    return {"bound": "smem lookups", "lookups_per_fingerprint": per_fp, "achieved": rate, "peak": peak,
+            "unit": "lookups/s", "frac": rate / peak}
+
 
 def kernel_rooflines(kb, per, steps, peaks, key=""):
     """Per heavy kernel: live ms per step (CUDA events on the launching
@@ -308,6 +339,8 @@ def kernel_rooflines(kb, per, steps, peaks, key=""):
         out[name] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                      "traffic": _traffic(name, key), "peak_source": f"{src} ({hbm:g} GB/s)",
                      "algorithmic_bytes": nbytes, "ms": ms, "single_kernel": name in SINGLE}
+    if kb.units.get("fingerprint") and kb.w.K * kb.w.K >= kb.w.D:  # the walk kernel against its own work
+        out["k_sig_walk"]["walk"] = walk_bound(kb.w, out["k_sig_walk"]["ms"], kb.units["fingerprint"] / steps)
     return out
 
 
@@ -422,7 +455,8 @@ def station_arm(args, rank, world, local_rank, w, steps, warmup, e2e=True):
     per = {k: meter.acc[k] / steps for k in STAGES}
     kernels = kernel_rooflines(meter.kb, per, steps, _peaks(), traffic_key(w.name, w.N))
     line["roofline"] = dominant(kernels)
-    line["kernels"] = {k: {kk: v[kk] for kk in ("ms", "bound", "achieved", "frac", "unit")} for k, v in kernels.items()}
+    line["kernels"] = {k: {kk: v[kk] for kk in ("ms", "bound", "achieved", "frac", "unit", "walk") if kk in v}
+                       for k, v in kernels.items()}
     line["stage_ms"] = per
     line["counters"] = meter.last.get(w.N, {})
     s.close()
@@ -606,7 +640,8 @@ def c2_arm(args, rank, world, local_rank):
                       "how": "the same stations, one fast_detect per station, inputs resident",
                       "same_counts_as_batched": plain_M == last_M},
             "plan": plan_info,
-            "kernels": {k: {kk: v[kk] for kk in ("ms", "bound", "achieved", "frac", "unit", "algorithmic_bytes")}
+            "kernels": {k: {kk: v[kk] for kk in ("ms", "bound", "achieved", "frac", "unit", "algorithmic_bytes", "walk")
+                            if kk in v}
                         for k, v in kernels.items()},
             "stage_ms": per,
             "counters_by_batch": {str(n): c for n, c in meter.last.items()},

@@ -109,3 +109,35 @@ def test_meter_keeps_batches_of_equal_length_apart():
     assert all(c["windows"] == 18_144_000 for c in m.last.values())
     assert [m.last[k]["n_emissions"] for k in ("7", "6+1", "5+2", "4+3")] == [1, 3, 3, 3]
     assert m.launches == 20
+
+
+def test_walk_steps_matches_simulated_walks():
+    # the expected walk length of k_sig_walk's bound against walks simulated
+    # on uniformly drawn fingerprints: a random ranking of [0, D), a tile of
+    # 32 fingerprints of K bits, the walk read 8 steps at a time until every
+    # fingerprint is hit
+    import numpy as np
+    rng = np.random.default_rng(7)
+    for D, K in ((512, 40), (2048, 100)):
+        lens = []
+        for _ in range(3000):
+            rank = rng.permutation(D)
+            pos = np.empty(D, np.int64)
+            pos[rank] = np.arange(D)
+            first = [pos[rng.choice(D, K, replace=False)].min() + 1 for _ in range(32)]
+            lens.append(-(-max(first) // 8) * 8)
+        want = float(np.mean(lens))
+        got = bench.walk_steps(D, K)
+        assert abs(got - want) < 4 * np.std(lens) / np.sqrt(len(lens)) + 0.05, (D, K, got, want)
+    # more set bits, shorter walks; one fingerprint per tile, shorter still
+    assert bench.walk_steps(8192, 800) < bench.walk_steps(8192, 400)
+    assert bench.walk_steps(8192, 400, tile=1) < bench.walk_steps(8192, 400)
+
+
+def test_walk_bound_counts_both_walks_of_min_max():
+    import synth
+    w = synth.scaled("c1", 1000)  # Min-Max, b = 100 tables of r = 4: 200 functions, 400 walks
+    wb = bench.walk_bound(w, 10.0, 1_000_000)
+    assert abs(wb["lookups_per_fingerprint"] - 400 * bench.walk_steps(w.D, w.K) / 32) < 1e-9
+    assert abs(wb["achieved"] - 1e6 * wb["lookups_per_fingerprint"] / 0.01) < 1e-3 * wb["achieved"]
+    assert wb["unit"] == "lookups/s" and 0 < wb["frac"] < 1
